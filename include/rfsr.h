@@ -1,0 +1,203 @@
+/*
+ * rfsr.h -- C ABI of the GB300 library for recursive frequency-selective reconstruction (R-FSR)
+ * of quarter-sampled video (Grosche, Seiler, Kaup, ICIP 2021, arXiv 2203.09200).
+ *
+ * Per frame t of a stream the library runs, on the GPU and without a host round trip
+ * (the processing chain of Fig. 1):
+ *   ingest ... the sensor data: one measured pixel per 2x2 block (quarter sampling, Sec. 1) as a
+ *              sample plane f_sub = f * b and a binary mask b (Sec. 2.1)
+ *   ME ....... pixel-wise template matching of the measured pixels of frame t against each of the
+ *              K previously reconstructed frames (Sec. 2.2; K = 3, Sec. 4)
+ *   CC ....... consistency checks of the motion vectors: RME (Sec. 2.2), RMC / FRMC (Sec. 3.1.1),
+ *              NNC (Sec. 3.1.2, Eq. (1)) and the proposed NNC + FRMC combination
+ *   PR ....... projection of measured past pixels along accepted vectors, averaged over the
+ *              past frames that project (Sec. 2.2)
+ *   FSR ...... block-wise frequency selective reconstruction with the projected pixels as extra
+ *              known pixels and the D-FSR overwrite rule (Sec. 2.1, 3.2), concealed weighting 0
+ *              so all blocks are independent (Sec. 4)
+ * and keeps the 8-bit reconstruction as the reference of the next frames.
+ *
+ * Conventions shared by all calls:
+ *   - frames are H x W row-major 8-bit luma, H and W even, 16 <= H, W <= 8192;
+ *   - a mask is H x W bytes, 1 = measured, 0 = not measured, with exactly one 1 per 2x2 block;
+ *   - a motion vector is two int8 (vertical, horizontal) per pixel; it points from the current
+ *     frame t into the past frame t-k;
+ *   - every call returns RFSR_OK (0) or a negative RFSR_E* code; rfsr_last_error() gives a
+ *     message for the calling thread; no C++ exception crosses this interface;
+ *   - the engine is thread-safe; one stream must be used by one thread at a time;
+ *   - device pointers are CUDA device addresses on the engine's device; host pointers are plain
+ *     process memory.  The library never takes ownership of caller buffers.
+ */
+#ifndef RFSR_H
+#define RFSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RFSR_ABI_VERSION 1
+
+/* ---- status codes ---------------------------------------------------------------------- */
+enum {
+    RFSR_OK = 0,
+    RFSR_EINVAL = -1,     /* bad argument: NULL pointer, size, parameter out of range       */
+    RFSR_EMASK = -2,      /* mask is not a quarter-sampling mask (one 1 per 2x2, values 0/1) */
+    RFSR_ENOMEM = -3,     /* device or pinned host memory could not be allocated            */
+    RFSR_EAGAIN = -4,     /* stream queued by memory admission, not live yet                */
+    RFSR_EBUSY = -5,      /* in-flight frame limit reached: collect frames first            */
+    RFSR_ETIMEDOUT = -6,  /* nothing ready within the timeout                               */
+    RFSR_EDEVICE = -7,    /* CUDA error; the message names the call                         */
+    RFSR_ESTATE = -8      /* call not valid in the current state (e.g. get before push)     */
+};
+
+/* ---- consistency-check modes (Table 3 rows, plus no check and NNC alone) ---------------- */
+enum {
+    RFSR_CC_NONE = 0,      /* every projectable vector accepted                              */
+    RFSR_CC_RME = 1,       /* reverse motion estimation, accept iff vectors coincide (Sec. 2.2) */
+    RFSR_CC_RMC = 2,       /* reverse motion check, (2Rc+1)^2 reverse vectors (Sec. 3.1.1)   */
+    RFSR_CC_FRMC = 3,      /* fast RMC, offsets {-7,-3,-1,0,1,3,7}^2 (Sec. 3.1.1)           */
+    RFSR_CC_NNC = 4,       /* nearest neighbour check alone (Sec. 3.1.2)                     */
+    RFSR_CC_NNC_FRMC = 5   /* NNC, then FRMC for NNC survivors: the paper's proposal         */
+};
+
+/* ---- per-pixel decision labels (debug plane RFSR_DBG_DECISION) -------------------------- */
+enum {
+    RFSR_DEC_MEASURED = 0,         /* pixel measured in frame t: nothing to project          */
+    RFSR_DEC_NOT_PROJECTABLE = 1,  /* p+v outside the frame or not measured in frame t-k    */
+    RFSR_DEC_NNC_REJECT = 2,       /* rejected by the nearest neighbour check               */
+    RFSR_DEC_CHECK_REJECT = 3,     /* rejected by RME / RMC / FRMC                           */
+    RFSR_DEC_ACCEPT = 4            /* projected                                              */
+};
+
+enum { RFSR_MASK_FIXED = 0, RFSR_MASK_DYNAMIC = 1 };
+
+/* ---- configuration ---------------------------------------------------------------------- */
+typedef struct rfsr_engine rfsr_engine;
+typedef struct rfsr_stream rfsr_stream;
+
+typedef struct {
+    int device;            /* CUDA device ordinal                                                */
+    size_t memory_budget;  /* bytes of device memory for stream state; 0 = 80% of free memory    */
+    void *cuda_stream;     /* cudaStream_t to run on; NULL = the engine creates its own          */
+    int max_inflight;      /* frames per stream pushed and not yet collected; 0 = 4             */
+    int batched;           /* 0: each push launches its frame step at once; 1: pushes are staged
+                              and rfsr_engine_step() runs one batched step over all streams      */
+} rfsr_engine_config;
+
+typedef struct {
+    int height, width;     /* HR frame size (even, >= 16)                                        */
+    int mask_type;         /* RFSR_MASK_FIXED / RFSR_MASK_DYNAMIC (informational)                 */
+    int cc_mode;           /* RFSR_CC_*                                                          */
+    int num_refs;          /* K, number of past frames for ME and projection, 0..3 (Sec. 4: 3)   */
+    int template_size;     /* T, odd, 1..11 (default 9)                                          */
+    int search_radius;     /* R, ME search window [-R, R]^2, 1..9 (default 8)                     */
+    int check_radius;      /* Rc, RMC window [-Rc, Rc]^2, 1..9 (default = R)                     */
+    int fsr_iterations;    /* FSR model iterations (default 100)                                 */
+    float fsr_rho;         /* FSR spatial weighting decay (default 0.7)                          */
+    float fsr_gamma;       /* FSR orthogonality deficiency compensation (default 0.5)            */
+    float fsr_proj_weight; /* weight factor of projected pixels (default 1: same as measured)     */
+    int fsr_overwrite_projected; /* 0: D-FSR (Sec. 3.2, default); 1: R-FSR overwrite          */
+    int keep_f32;          /* 1: keep the FP32 FSR output of every frame for rfsr_get_frame      */
+} rfsr_stream_config;
+
+/* Fill a config with the defaults above (1280x720, NNC_FRMC, K=3, T=9, R=8). */
+void rfsr_engine_config_default(rfsr_engine_config *cfg);
+void rfsr_stream_config_default(rfsr_stream_config *cfg);
+
+/* ---- engine ----------------------------------------------------------------------------- */
+/* Create an engine on cfg->device.  *out is owned by the library until rfsr_engine_destroy.
+ * Errors: EINVAL (NULL / bad field), EDEVICE (no such device, stream creation failed). */
+int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out);
+/* Waits for all work, destroys all streams of the engine and frees everything. */
+int rfsr_engine_destroy(rfsr_engine *eng);
+/* Batched engines: one frame step (Fig. 1) over every live stream that has a staged frame,
+ * launched as one batch.  Returns the number of frames launched (>= 0) or an error. */
+int rfsr_engine_step(rfsr_engine *eng);
+/* Wait (bounded) until all launched work of the engine is done.  ETIMEDOUT on timeout. */
+int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
+
+/* ---- streams (the four calls of the serving interface) ---------------------------------- */
+/* Create a video stream.  The stream owns its device state: K+1 ring slots of reconstruction,
+ * sample plane and mask, the motion fields, decisions, projection sums and FSR output.
+ * Errors: EINVAL (sizes / parameters), ENOMEM (device memory, or the engine budget would be
+ * exceeded), EDEVICE.  *out is owned by the library until rfsr_destroy. */
+int rfsr_create_stream(rfsr_engine *eng, const rfsr_stream_config *cfg, rfsr_stream **out);
+
+/* Push frame t: samples = f_sub (H x W, unmeasured bytes ignored), mask = b (H x W, 0/1, one 1
+ * per 2x2 block), both HOST memory owned by the caller and copied before return, so the caller
+ * may reuse them at once.  The frame step runs asynchronously on the GPU.
+ * Errors: EINVAL, EMASK (checked on the host before anything is enqueued; the stream state is
+ * unchanged), EBUSY (max_inflight frames not yet collected), EDEVICE. */
+int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask);
+
+/* As rfsr_push_frame, but samples and mask are DEVICE buffers (2-byte aligned, else EINVAL) that
+ * must stay unchanged until the
+ * frame has been collected (rfsr_get_frame / rfsr_get_frame_device returned it).  The mask is
+ * validated on the GPU; a bad mask is reported as EMASK by the call that collects the frame, and
+ * the frame then leaves the stream's history unchanged. */
+int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask);
+
+/* Collect the oldest uncollected frame (FIFO): out_u8 = 8-bit reconstruction (H x W host),
+ * out_f32 = FSR output on the [0, 1] scale before quantisation (H x W host, may be NULL; needs
+ * keep_f32).  Waits at most timeout_ms (< 0: no limit) and never hangs beyond that.
+ * Errors: ESTATE (nothing pushed), ETIMEDOUT, EMASK (frame had a bad device mask), EINVAL. */
+int rfsr_get_frame(rfsr_stream *s, uint8_t *out_u8, float *out_f32, int timeout_ms);
+
+/* As rfsr_get_frame, into DEVICE buffers (either may be NULL). */
+int rfsr_get_frame_device(rfsr_stream *s, uint8_t *d_out_u8, float *d_out_f32, int timeout_ms);
+
+/* Destroy a stream.  Waits for its frames in flight, then frees its device and host state. */
+int rfsr_destroy(rfsr_stream *s);
+
+/* ---- state, history injection and debug planes (parity tests, checkpointing) ------------ */
+typedef struct {
+    int height, width;
+    int live;              /* 1 when admitted (0 while queued by memory admission)               */
+    long long frames_pushed, frames_collected;
+    int history_frames;    /* past frames available to the next frame (0..K)                      */
+    size_t device_bytes;   /* device memory held by this stream                                   */
+} rfsr_stream_info;
+int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info);
+
+/* Replace the history seen by the next pushed frame: for k = 1..nrefs, rec[k-1], smp[k-1] and
+ * msk[k-1] are the reconstruction, sample plane and 0/1 mask of frame t-k (HOST buffers, H x W,
+ * copied before return).  nrefs <= K.  Waits for the stream's frames in flight first. */
+int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
+                     const uint8_t *const *smp, const uint8_t *const *msk);
+
+/* Debug planes of the most recently completed frame (waits for it), copied to HOST memory dst:
+ *   RFSR_DBG_MV        k in 1..K_eff: raw ME field, H*W*2 int8 (vertical, horizontal)
+ *   RFSR_DBG_FMV       k: vector used by checks and projection (NNC median when NNC is on)
+ *   RFSR_DBG_DECISION  k: H*W uint8 RFSR_DEC_* labels
+ *   RFSR_DBG_PSUM      projection sums, H*W uint16;  RFSR_DBG_PCNT counts, H*W uint8
+ *   RFSR_DBG_FSR       FSR output, H*W float;        RFSR_DBG_REC reconstruction, H*W uint8
+ *   RFSR_DBG_RMV       k: reverse ME field at every past-frame pixel (RME mode only)
+ * Errors: ESTATE (no frame done yet or k > K_eff of that frame), EINVAL. */
+enum { RFSR_DBG_MV = 0, RFSR_DBG_FMV = 1, RFSR_DBG_DECISION = 2, RFSR_DBG_PSUM = 3,
+       RFSR_DBG_PCNT = 4, RFSR_DBG_FSR = 5, RFSR_DBG_REC = 6, RFSR_DBG_RMV = 7 };
+int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst);
+
+/* ---- stand-alone FSR (Sec. 2.1, 3.2) on device buffers ---------------------------------- */
+/* Reconstruct every 4x4 block of an H x W frame from its 32x32 support.  d_smp: sample plane
+ * (H*W uint8), d_msk: 0/1 mask (H*W uint8), d_psum / d_pcnt: projection sums and counts (H*W
+ * uint16 / uint8, both NULL for single-frame FSR; d_psum 2-byte aligned).  Outputs: d_out_f32
+ * (H*W float, [0,1] scale, 4-byte aligned, may be NULL) and d_out_u8 (H*W uint8, may be NULL).  cfg supplies the fsr_* fields and
+ * height / width.  Runs on cuda_stream (cudaStream_t, NULL = legacy default stream) and returns
+ * without waiting.  Errors: EINVAL, EDEVICE. */
+int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
+                    const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
+                    uint8_t *d_out_u8, void *cuda_stream);
+
+/* Kernel launches made by this process so far (all engines), for launch accounting. */
+long long rfsr_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rfsr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFSR_H */

@@ -1,0 +1,55 @@
+// ingest.cu -- takes the sensor data of frame t into the stream's ring slot.
+//
+// Quarter sampling (Sec. 1, Fig. 1): per 2x2 block exactly one pixel is measured; the sampled
+// image is f_sub = f * b with the binary mask b (Sec. 2.1).  The kernel checks that the mask is a
+// quarter-sampling mask (values 0/1, one 1 per block), writes the sample plane with unmeasured
+// bytes zeroed and the mask as 0x00/0xFF bytes (the form the ME kernel ANDs with), and flags a
+// bad mask in the frame status word so that the remaining kernels of the step do nothing.
+#include <atomic>
+
+#include "rfsr_internal.h"
+
+namespace rfsr {
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void count_launch(int n) { g_launches += n; }
+long long launches() { return g_launches.load(); }
+
+__global__ void ingest_kernel(FrameTask t)
+{
+    const int bw = t.W >> 1, bh = t.H >> 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && t.prev_status != nullptr && *t.prev_status != 0)
+        atomicOr(t.status, kStatusPoisoned);
+    if (i >= bw * bh) return;
+    const int by = i / bw, bx = i - by * bw;
+    const size_t o0 = (size_t)(2 * by) * t.W + 2 * bx, o1 = o0 + t.W;
+    // two aligned 16-bit loads per plane (x is even)
+    const uint16_t m0 = *reinterpret_cast<const uint16_t *>(t.in_msk + o0);
+    const uint16_t m1 = *reinterpret_cast<const uint16_t *>(t.in_msk + o1);
+    const uint16_t s0 = *reinterpret_cast<const uint16_t *>(t.in_smp + o0);
+    const uint16_t s1 = *reinterpret_cast<const uint16_t *>(t.in_smp + o1);
+    const int a = m0 & 0xff, b = m0 >> 8, c = m1 & 0xff, d = m1 >> 8;
+    const bool ok = ((a | b | c | d) <= 1) && (a + b + c + d == 1);
+    if (!ok) atomicOr(t.status, kStatusBadMask);
+    // byte masks 0x00 / 0xff (an invalid byte still yields a well-formed plane)
+    const uint16_t bm0 = (uint16_t)((a ? 0x00ff : 0) | (b ? 0xff00 : 0));
+    const uint16_t bm1 = (uint16_t)((c ? 0x00ff : 0) | (d ? 0xff00 : 0));
+    *reinterpret_cast<uint16_t *>(t.cur_msk + o0) = bm0;
+    *reinterpret_cast<uint16_t *>(t.cur_msk + o1) = bm1;
+    *reinterpret_cast<uint16_t *>(t.cur_smp + o0) = (uint16_t)(s0 & bm0);
+    *reinterpret_cast<uint16_t *>(t.cur_smp + o1) = (uint16_t)(s1 & bm1);
+}
+
+cudaError_t launch_ingest(const FrameTask &t, cudaStream_t st)
+{
+    const int nb = (t.H / 2) * (t.W / 2);
+    ingest_kernel<<<(nb + 255) / 256, 256, 0, st>>>(t);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace rfsr

@@ -1,0 +1,727 @@
+// rfsr_api.cpp -- the C ABI declared in include/rfsr.h: engines, streams with their device-
+// resident state, the asynchronous frame step and its host <-> device staging.
+//
+// A stream keeps everything the recursion needs on the device (Sec. 2.2 / Fig. 1): a ring of
+// K+1 slots holding the reconstruction, sample plane and mask of the current and the K previous
+// frames, the per-reference motion fields, decisions, projection sums and the FSR output.  A
+// frame step is one sequence of kernels on the engine's CUDA stream:
+//     ingest -> ME (all K references in one launch) -> [RME reverse field] -> checks + projection
+//     -> FSR + 8-bit reconstruction
+// preceded (host push) by one pinned host->device copy of the frame and followed by one
+// device->host copy of the result into a pinned slot, so the frame loop never leaves the device.
+#include "rfsr.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rfsr_internal.h"
+
+using namespace rfsr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return RFSR_EDEVICE;
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+// host-side quarter-sampling check (Sec. 1): values 0/1 and exactly one 1 per 2x2 block
+bool mask_ok(const uint8_t *m, int H, int W)
+{
+    for (int y = 0; y < H; y += 2) {
+        const uint8_t *r0 = m + (size_t)y * W, *r1 = r0 + W;
+        unsigned bad = 0;
+        for (int x = 0; x < W; x += 2) {
+            const unsigned a = r0[x], b = r0[x + 1], c = r1[x], d = r1[x + 1];
+            bad |= (a | b | c | d) & ~1u;
+            bad |= (a + b + c + d) ^ 1u;
+        }
+        if (bad) return false;
+    }
+    return true;
+}
+
+// FSR tables (Sec. 2.1 model): rho^d over the support, frequency weights, DFT twiddles.
+void fill_fsr_tables(FsrTables &tb, double rho)
+{
+    const int N = kFsrN;
+    const double c = (N - 1) / 2.0;
+    for (int m = 0; m < N; ++m)
+        for (int n = 0; n < N; ++n)
+            tb.wsp[m * N + n] = (float)std::pow(rho, std::sqrt((m - c) * (m - c) + (n - c) * (n - c)));
+    for (int k = 0; k < N; ++k)
+        for (int l = 0; l < kFsrHalf; ++l) {
+            const double kn = std::min(k, N - k) / (N / 2.0), ln = std::min(l, N - l) / (N / 2.0);
+            const double v = 1.0 - std::sqrt(2.0) / 2.0 * std::sqrt(kn * kn + ln * ln);
+            tb.wf[k * kFsrHalf + l] = (float)(v * v);
+        }
+    for (int j = 0; j < N; ++j) {
+        tb.cs[j] = (float)std::cos(2.0 * M_PI * j / N);
+        tb.sn[j] = (float)std::sin(2.0 * M_PI * j / N);
+    }
+}
+
+int wait_event(cudaEvent_t ev, int timeout_ms)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return RFSR_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+        if (timeout_ms >= 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(RFSR_ETIMEDOUT, "frame not ready within timeout");
+        }
+        if (++spins < 2000) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+struct Slot {
+    uint8_t *h_in = nullptr;    // pinned samples | mask
+    uint8_t *d_in = nullptr;    // device samples | mask
+    uint8_t *h_out = nullptr;   // pinned reconstruction
+    float *h_out32 = nullptr;   // pinned FSR output (keep_f32)
+    uint8_t *d_out = nullptr;   // device reconstruction
+    float *d_out32 = nullptr;   // device FSR output (keep_f32)
+    int *d_status = nullptr;
+    int *h_status = nullptr;
+    cudaEvent_t done = nullptr;
+    bool host_push = false;
+};
+
+struct rfsr_engine {
+    rfsr_engine_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, used = 0;
+    std::mutex mu;
+    std::vector<rfsr_stream *> streams;
+};
+
+struct rfsr_stream {
+    rfsr_engine *eng = nullptr;
+    rfsr_stream_config cfg{};
+    int H = 0, W = 0, K = 0;
+    size_t bytes = 0;
+    std::vector<void *> dev_allocs;
+    std::vector<void *> host_allocs;
+    uint8_t *ring_rec[kMaxRefs + 1] = {}, *ring_smp[kMaxRefs + 1] = {}, *ring_msk[kMaxRefs + 1] = {};
+    int8_t *mv[kMaxRefs] = {}, *fmv[kMaxRefs] = {}, *rmv[kMaxRefs] = {};
+    uint8_t *dec[kMaxRefs] = {};
+    uint16_t *psum = nullptr;
+    uint8_t *pcnt = nullptr;
+    float *fsr = nullptr;
+    float *tables = nullptr;
+    int *d_zero = nullptr;
+    std::vector<Slot> slots;
+    long long pushed = 0, collected = 0;
+    int hist = 0;          // history frames available to the next frame
+    int ring_head = 0;     // ring index of the next frame
+    int last_slot = -1, last_ring = -1, last_K = 0;
+    bool poisoned = false;
+
+    int dev_alloc(void **p, size_t n)
+    {
+        cudaError_t e = cudaMalloc(p, n);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        dev_allocs.push_back(*p);
+        bytes += n;
+        return RFSR_OK;
+    }
+    int host_alloc(void **p, size_t n)
+    {
+        cudaError_t e = cudaMallocHost(p, n);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+        host_allocs.push_back(*p);
+        return RFSR_OK;
+    }
+    void release()
+    {
+        for (auto &s : slots)
+            if (s.done) cudaEventDestroy(s.done);
+        for (void *p : dev_allocs) cudaFree(p);
+        for (void *p : host_allocs) cudaFreeHost(p);
+        dev_allocs.clear();
+        host_allocs.clear();
+        slots.clear();
+    }
+};
+
+extern "C" {
+
+void rfsr_engine_config_default(rfsr_engine_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->device = 0;
+    c->max_inflight = 4;
+}
+
+void rfsr_stream_config_default(rfsr_stream_config *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->height = 720;
+    c->width = 1280;
+    c->mask_type = RFSR_MASK_DYNAMIC;
+    c->cc_mode = RFSR_CC_NNC_FRMC;
+    c->num_refs = 3;
+    c->template_size = 9;
+    c->search_radius = 8;
+    c->check_radius = 8;
+    c->fsr_iterations = 100;
+    c->fsr_rho = 0.7f;
+    c->fsr_gamma = 0.5f;
+    c->fsr_proj_weight = 1.0f;
+    c->fsr_overwrite_projected = 0;
+    c->keep_f32 = 0;
+}
+
+const char *rfsr_last_error(void) { return g_err.c_str(); }
+
+long long rfsr_kernel_launches(void) { return rfsr::launches(); }
+
+int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
+{
+    if (!cfg || !out) return fail(RFSR_EINVAL, "engine_create: NULL argument");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(RFSR_EINVAL, "engine_create: no such device");
+    if (cfg->max_inflight < 0 || cfg->max_inflight > 64)
+        return fail(RFSR_EINVAL, "engine_create: max_inflight out of range");
+    if (cfg->batched) return fail(RFSR_EINVAL, "engine_create: batched mode is not available");
+    CK(cudaSetDevice(cfg->device));
+    auto *e = new rfsr_engine();
+    e->cfg = *cfg;
+    if (e->cfg.max_inflight == 0) e->cfg.max_inflight = 4;
+    if (cfg->cuda_stream) {
+        e->stream = (cudaStream_t)cfg->cuda_stream;
+    } else {
+        cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) {
+            delete e;
+            return cuda_fail(err, "cudaStreamCreateWithFlags");
+        }
+        e->own_stream = true;
+    }
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    e->budget = cfg->memory_budget ? cfg->memory_budget : (size_t)(0.8 * (double)fr);
+    *out = e;
+    return RFSR_OK;
+}
+
+int rfsr_engine_sync(rfsr_engine *e, int timeout_ms)
+{
+    if (!e) return fail(RFSR_EINVAL, "engine_sync: NULL engine");
+    CK(cudaSetDevice(e->cfg.device));
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(ev, e->stream);
+    if (err != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return cuda_fail(err, "cudaEventRecord");
+    }
+    int rc = wait_event(ev, timeout_ms);
+    cudaEventDestroy(ev);
+    return rc;
+}
+
+int rfsr_destroy(rfsr_stream *s);
+
+int rfsr_engine_destroy(rfsr_engine *e)
+{
+    if (!e) return fail(RFSR_EINVAL, "engine_destroy: NULL engine");
+    cudaSetDevice(e->cfg.device);
+    cudaStreamSynchronize(e->stream);
+    std::vector<rfsr_stream *> ss;
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        ss = e->streams;
+    }
+    for (auto *s : ss) rfsr_destroy(s);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    delete e;
+    return RFSR_OK;
+}
+
+int rfsr_engine_step(rfsr_engine *e)
+{
+    if (!e) return fail(RFSR_EINVAL, "engine_step: NULL engine");
+    return fail(RFSR_ESTATE, "engine_step: engine is not batched");
+}
+
+static int check_stream_config(const rfsr_stream_config *c)
+{
+    if (c->height < 16 || c->width < 16 || c->height > 8192 || c->width > 8192 ||
+        (c->height & 1) || (c->width & 1))
+        return fail(RFSR_EINVAL, "stream config: height / width must be even, in [16, 8192]");
+    if (c->cc_mode < 0 || c->cc_mode > 5) return fail(RFSR_EINVAL, "stream config: cc_mode");
+    if (c->num_refs < 0 || c->num_refs > kMaxRefs) return fail(RFSR_EINVAL, "stream config: num_refs");
+    if (c->template_size < 1 || c->template_size > 2 * kMaxHalf + 1 || !(c->template_size & 1))
+        return fail(RFSR_EINVAL, "stream config: template_size must be odd, 1..11");
+    if (c->search_radius < 1 || c->search_radius > kMaxRadius)
+        return fail(RFSR_EINVAL, "stream config: search_radius must be 1..9");
+    if (c->check_radius < 1 || c->check_radius > kMaxRadius)
+        return fail(RFSR_EINVAL, "stream config: check_radius must be 1..9");
+    if (c->fsr_iterations < 0 || c->fsr_iterations > 100000)
+        return fail(RFSR_EINVAL, "stream config: fsr_iterations");
+    if (!(c->fsr_rho > 0.f && c->fsr_rho <= 1.f)) return fail(RFSR_EINVAL, "stream config: fsr_rho");
+    if (!(c->fsr_gamma > 0.f && c->fsr_gamma <= 2.f)) return fail(RFSR_EINVAL, "stream config: fsr_gamma");
+    if (!(c->fsr_proj_weight >= 0.f)) return fail(RFSR_EINVAL, "stream config: fsr_proj_weight");
+    return RFSR_OK;
+}
+
+int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_stream **out)
+{
+    if (!e || !cfg || !out) return fail(RFSR_EINVAL, "create_stream: NULL argument");
+    int rc = check_stream_config(cfg);
+    if (rc) return rc;
+    CK(cudaSetDevice(e->cfg.device));
+    auto *s = new rfsr_stream();
+    s->eng = e;
+    s->cfg = *cfg;
+    s->H = cfg->height;
+    s->W = cfg->width;
+    s->K = cfg->num_refs;
+    const size_t HW = (size_t)s->H * s->W;
+    const int M = e->cfg.max_inflight;
+    const bool rme = cfg->cc_mode == RFSR_CC_RME;
+    // device bytes this stream will hold (admission against the engine budget)
+    size_t need = (size_t)(s->K + 1) * 3 * HW + (size_t)s->K * (2 * HW * (rme ? 3 : 2) + HW) +
+                  3 * HW + 4 * HW + sizeof(FsrTables) + 64 +
+                  (size_t)M * (3 * HW + (cfg->keep_f32 ? 4 * HW : 0) + 4);
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        if (e->used + need > e->budget) {
+            delete s;
+            return fail(RFSR_ENOMEM, "create_stream: engine memory budget exceeded");
+        }
+        e->used += need;
+    }
+    auto bail = [&](int code) {
+        s->release();
+        {
+            std::lock_guard<std::mutex> g(e->mu);
+            e->used -= need;
+        }
+        delete s;
+        return code;
+    };
+#define AL(ptr, n)                                                 \
+    do {                                                           \
+        int r_ = s->dev_alloc((void **)&(ptr), (n));               \
+        if (r_) return bail(r_);                                   \
+    } while (0)
+    for (int r = 0; r <= s->K; ++r) {
+        AL(s->ring_rec[r], HW);
+        AL(s->ring_smp[r], HW);
+        AL(s->ring_msk[r], HW);
+    }
+    for (int k = 0; k < s->K; ++k) {
+        AL(s->mv[k], 2 * HW);
+        AL(s->fmv[k], 2 * HW);
+        AL(s->dec[k], HW);
+        if (rme) AL(s->rmv[k], 2 * HW);
+    }
+    AL(s->psum, 2 * HW);
+    AL(s->pcnt, HW);
+    AL(s->fsr, 4 * HW);
+    AL(s->tables, sizeof(FsrTables));
+    AL(s->d_zero, 64);
+    if (cudaMemset(s->d_zero, 0, 64) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
+    {
+        FsrTables tb;
+        fill_fsr_tables(tb, cfg->fsr_rho);
+        cudaError_t er = cudaMemcpy(s->tables, &tb, sizeof(tb), cudaMemcpyHostToDevice);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemcpy tables"));
+    }
+    s->slots.resize(M);
+    for (int i = 0; i < M; ++i) {
+        Slot &sl = s->slots[i];
+        AL(sl.d_in, 2 * HW);
+        AL(sl.d_out, HW);
+        AL(sl.d_status, 4);
+        if (cfg->keep_f32) AL(sl.d_out32, 4 * HW);
+        int r_ = s->host_alloc((void **)&sl.h_in, 2 * HW);
+        if (!r_) r_ = s->host_alloc((void **)&sl.h_out, HW);
+        if (!r_) r_ = s->host_alloc((void **)&sl.h_status, sizeof(int));
+        if (!r_ && cfg->keep_f32) r_ = s->host_alloc((void **)&sl.h_out32, 4 * HW);
+        if (r_) return bail(r_);
+        cudaError_t er = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
+    }
+#undef AL
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        e->streams.push_back(s);
+    }
+    *out = s;
+    return RFSR_OK;
+}
+
+static void fill_task(rfsr_stream *s, Slot &sl, FrameTask &t, const uint8_t *in_smp,
+                      const uint8_t *in_msk, const int *prev_status)
+{
+    std::memset(&t, 0, sizeof(t));
+    const int R1 = s->K + 1;
+    const int r = s->ring_head;
+    t.H = s->H;
+    t.W = s->W;
+    t.K = s->hist;
+    t.T = s->cfg.template_size;
+    t.R = s->cfg.search_radius;
+    t.Rc = s->cfg.check_radius;
+    t.cc_mode = s->cfg.cc_mode;
+    t.fsr_iters = s->cfg.fsr_iterations;
+    t.fsr_gamma = s->cfg.fsr_gamma;
+    t.fsr_proj_weight = s->cfg.fsr_proj_weight;
+    t.fsr_overwrite_projected = s->cfg.fsr_overwrite_projected;
+    t.fsr_tables = s->tables;
+    t.in_smp = in_smp;
+    t.in_msk = in_msk;
+    t.cur_smp = s->ring_smp[r];
+    t.cur_msk = s->ring_msk[r];
+    t.cur_rec = s->ring_rec[r];
+    for (int k = 1; k <= t.K; ++k) {
+        const int rr = ((r - k) % R1 + R1) % R1;
+        t.ref_rec[k - 1] = s->ring_rec[rr];
+        t.ref_smp[k - 1] = s->ring_smp[rr];
+        t.ref_msk[k - 1] = s->ring_msk[rr];
+        t.mv[k - 1] = s->mv[k - 1];
+        t.fmv[k - 1] = s->fmv[k - 1];
+        t.dec[k - 1] = s->dec[k - 1];
+        t.rmv[k - 1] = s->rmv[k - 1];
+    }
+    t.psum = s->psum;
+    t.pcnt = s->pcnt;
+    t.fsr_out = sl.d_out32 ? sl.d_out32 : s->fsr;
+    t.out_u8 = sl.d_out;
+    t.status = sl.d_status;
+    t.prev_status = prev_status;
+}
+
+static int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint8_t *in_msk)
+{
+    rfsr_engine *e = s->eng;
+    Slot &sl = s->slots[slot_idx];
+    const int *prev = s->last_slot >= 0 ? s->slots[s->last_slot].d_status : s->d_zero;
+    FrameTask t;
+    fill_task(s, sl, t, in_smp, in_msk, prev);
+    CK(cudaMemsetAsync(sl.d_status, 0, sizeof(int), e->stream));
+    CK(launch_ingest(t, e->stream));
+    CK(launch_me(t, e->stream));
+    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
+    CK(launch_cc_project(t, e->stream));
+    CK(launch_fsr(t, e->stream));
+    CK(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    s->last_K = t.K;
+    s->last_ring = s->ring_head;
+    s->last_slot = slot_idx;
+    s->ring_head = (s->ring_head + 1) % (s->K + 1);
+    s->hist = std::min(s->hist + 1, s->K);
+    return RFSR_OK;
+}
+
+static int push_common(rfsr_stream *s, const void *a, const void *b)
+{
+    if (!s || !a || !b) return fail(RFSR_EINVAL, "push_frame: NULL argument");
+    if (s->poisoned) return fail(RFSR_ESTATE, "push_frame: stream had a bad mask; reset it with rfsr_set_history");
+    if (s->pushed - s->collected >= (long long)s->slots.size())
+        return fail(RFSR_EBUSY, "push_frame: in-flight limit reached, collect frames first");
+    return RFSR_OK;
+}
+
+int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask)
+{
+    int rc = push_common(s, samples, mask);
+    if (rc) return rc;
+    if (!mask_ok(mask, s->H, s->W)) return fail(RFSR_EMASK, "push_frame: not a quarter-sampling mask");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    const size_t HW = (size_t)s->H * s->W;
+    const int si = (int)(s->pushed % (long long)s->slots.size());
+    Slot &sl = s->slots[si];
+    std::memcpy(sl.h_in, samples, HW);
+    std::memcpy(sl.h_in + HW, mask, HW);
+    cudaStream_t st = s->eng->stream;
+    CK(cudaMemcpyAsync(sl.d_in, sl.h_in, 2 * HW, cudaMemcpyHostToDevice, st));
+    rc = enqueue_step(s, si, sl.d_in, sl.d_in + HW);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(sl.h_out, sl.d_out, HW, cudaMemcpyDeviceToHost, st));
+    if (sl.h_out32) CK(cudaMemcpyAsync(sl.h_out32, sl.d_out32, 4 * HW, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(sl.done, st));
+    sl.host_push = true;
+    s->pushed++;
+    return RFSR_OK;
+}
+
+int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask)
+{
+    int rc = push_common(s, d_samples, d_mask);
+    if (rc) return rc;
+    if (((uintptr_t)d_samples | (uintptr_t)d_mask) & 1u)
+        return fail(RFSR_EINVAL, "push_frame_device: buffers must be 2-byte aligned");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    const int si = (int)(s->pushed % (long long)s->slots.size());
+    Slot &sl = s->slots[si];
+    rc = enqueue_step(s, si, d_samples, d_mask);
+    if (rc) return rc;
+    CK(cudaEventRecord(sl.done, s->eng->stream));
+    sl.host_push = false;
+    s->pushed++;
+    return RFSR_OK;
+}
+
+static int collect(rfsr_stream *s, int timeout_ms, Slot **out)
+{
+    if (s->collected >= s->pushed) return fail(RFSR_ESTATE, "get_frame: no frame pushed");
+    Slot &sl = s->slots[(size_t)(s->collected % (long long)s->slots.size())];
+    int rc = wait_event(sl.done, timeout_ms);
+    if (rc) return rc;
+    s->collected++;
+    const int st = *sl.h_status;
+    if (st & kStatusBadMask) {
+        s->poisoned = true;
+        return fail(RFSR_EMASK, "get_frame: the frame's device mask is not a quarter-sampling mask");
+    }
+    if (st & kStatusPoisoned) {
+        s->poisoned = true;
+        return fail(RFSR_ESTATE, "get_frame: an earlier frame of the stream had a bad mask");
+    }
+    *out = &sl;
+    return RFSR_OK;
+}
+
+int rfsr_get_frame(rfsr_stream *s, uint8_t *out_u8, float *out_f32, int timeout_ms)
+{
+    if (!s) return fail(RFSR_EINVAL, "get_frame: NULL stream");
+    if (out_f32 && !s->cfg.keep_f32) return fail(RFSR_EINVAL, "get_frame: out_f32 needs keep_f32");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    Slot *sl = nullptr;
+    int rc = collect(s, timeout_ms, &sl);
+    if (rc) return rc;
+    const size_t HW = (size_t)s->H * s->W;
+    if (sl->host_push) {
+        if (out_u8) std::memcpy(out_u8, sl->h_out, HW);
+        if (out_f32) std::memcpy(out_f32, sl->h_out32, 4 * HW);
+    } else {
+        if (out_u8) CK(cudaMemcpy(out_u8, sl->d_out, HW, cudaMemcpyDeviceToHost));
+        if (out_f32) CK(cudaMemcpy(out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToHost));
+    }
+    return RFSR_OK;
+}
+
+int rfsr_get_frame_device(rfsr_stream *s, uint8_t *d_out_u8, float *d_out_f32, int timeout_ms)
+{
+    if (!s) return fail(RFSR_EINVAL, "get_frame_device: NULL stream");
+    if (d_out_f32 && !s->cfg.keep_f32) return fail(RFSR_EINVAL, "get_frame_device: out_f32 needs keep_f32");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    Slot *sl = nullptr;
+    int rc = collect(s, timeout_ms, &sl);
+    if (rc) return rc;
+    const size_t HW = (size_t)s->H * s->W;
+    cudaStream_t st = s->eng->stream;
+    if (d_out_u8) CK(cudaMemcpyAsync(d_out_u8, sl->d_out, HW, cudaMemcpyDeviceToDevice, st));
+    if (d_out_f32) CK(cudaMemcpyAsync(d_out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(sl->done, st));
+    return wait_event(sl->done, -1);
+}
+
+int rfsr_destroy(rfsr_stream *s)
+{
+    if (!s) return fail(RFSR_EINVAL, "destroy: NULL stream");
+    rfsr_engine *e = s->eng;
+    cudaSetDevice(e->cfg.device);
+    for (auto &sl : s->slots)
+        if (sl.done) cudaEventSynchronize(sl.done);
+    s->release();
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        e->streams.erase(std::remove(e->streams.begin(), e->streams.end(), s), e->streams.end());
+    }
+    // return the admission bytes (recomputed as in create)
+    {
+        const size_t HW = (size_t)s->H * s->W;
+        const int M = e->cfg.max_inflight;
+        const bool rme = s->cfg.cc_mode == RFSR_CC_RME;
+        size_t n = (size_t)(s->K + 1) * 3 * HW + (size_t)s->K * (2 * HW * (rme ? 3 : 2) + HW) +
+                   3 * HW + 4 * HW + sizeof(FsrTables) + 64 +
+                   (size_t)M * (3 * HW + (s->cfg.keep_f32 ? 4 * HW : 0) + 4);
+        std::lock_guard<std::mutex> g(e->mu);
+        e->used -= std::min(e->used, n);
+    }
+    delete s;
+    return RFSR_OK;
+}
+
+int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info)
+{
+    if (!s || !info) return fail(RFSR_EINVAL, "stream_get_info: NULL argument");
+    info->height = s->H;
+    info->width = s->W;
+    info->live = 1;
+    info->frames_pushed = s->pushed;
+    info->frames_collected = s->collected;
+    info->history_frames = s->hist;
+    info->device_bytes = s->bytes;
+    return RFSR_OK;
+}
+
+static int wait_all(rfsr_stream *s)
+{
+    for (auto &sl : s->slots) CK(cudaEventSynchronize(sl.done));
+    return RFSR_OK;
+}
+
+int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
+                     const uint8_t *const *smp, const uint8_t *const *msk)
+{
+    if (!s) return fail(RFSR_EINVAL, "set_history: NULL stream");
+    if (nrefs < 0 || nrefs > s->K) return fail(RFSR_EINVAL, "set_history: nrefs must be in [0, K]");
+    if (nrefs > 0 && (!rec || !smp || !msk)) return fail(RFSR_EINVAL, "set_history: NULL arrays");
+    for (int k = 0; k < nrefs; ++k)
+        if (!rec[k] || !smp[k] || !msk[k]) return fail(RFSR_EINVAL, "set_history: NULL plane");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    int rc = wait_all(s);
+    if (rc) return rc;
+    const size_t HW = (size_t)s->H * s->W;
+    std::vector<uint8_t> bm(HW), sm(HW);
+    const int R1 = s->K + 1;
+    for (int k = 1; k <= nrefs; ++k) {
+        if (!mask_ok(msk[k - 1], s->H, s->W))
+            return fail(RFSR_EMASK, "set_history: not a quarter-sampling mask");
+        for (size_t i = 0; i < HW; ++i) {
+            bm[i] = msk[k - 1][i] ? 0xff : 0;
+            sm[i] = smp[k - 1][i] & bm[i];
+        }
+        const int rr = ((s->ring_head - k) % R1 + R1) % R1;
+        CK(cudaMemcpy(s->ring_rec[rr], rec[k - 1], HW, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->ring_smp[rr], sm.data(), HW, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(s->ring_msk[rr], bm.data(), HW, cudaMemcpyHostToDevice));
+    }
+    s->hist = nrefs;
+    s->poisoned = false;
+    s->last_slot = -1;      // the poison chain restarts
+    return RFSR_OK;
+}
+
+int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
+{
+    if (!s || !dst) return fail(RFSR_EINVAL, "debug_get: NULL argument");
+    if (s->last_slot < 0 || s->pushed == 0) return fail(RFSR_ESTATE, "debug_get: no frame processed");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    int rc = wait_all(s);
+    if (rc) return rc;
+    const size_t HW = (size_t)s->H * s->W;
+    const bool per_ref = what == RFSR_DBG_MV || what == RFSR_DBG_FMV || what == RFSR_DBG_DECISION ||
+                         what == RFSR_DBG_RMV;
+    if (per_ref && (k < 1 || k > s->last_K)) return fail(RFSR_ESTATE, "debug_get: k outside 1..K of that frame");
+    const void *src = nullptr;
+    size_t n = 0;
+    switch (what) {
+    case RFSR_DBG_MV: src = s->mv[k - 1]; n = 2 * HW; break;
+    case RFSR_DBG_FMV: src = s->fmv[k - 1]; n = 2 * HW; break;
+    case RFSR_DBG_DECISION: src = s->dec[k - 1]; n = HW; break;
+    case RFSR_DBG_RMV:
+        if (!s->rmv[k - 1]) return fail(RFSR_ESTATE, "debug_get: reverse field exists in RME mode only");
+        src = s->rmv[k - 1]; n = 2 * HW; break;
+    case RFSR_DBG_PSUM: src = s->psum; n = 2 * HW; break;
+    case RFSR_DBG_PCNT: src = s->pcnt; n = HW; break;
+    case RFSR_DBG_FSR: {
+        const Slot &sl = s->slots[s->last_slot];
+        src = sl.d_out32 ? (const void *)sl.d_out32 : (const void *)s->fsr;
+        n = 4 * HW;
+        break;
+    }
+    case RFSR_DBG_REC: src = s->ring_rec[s->last_ring]; n = HW; break;
+    default: return fail(RFSR_EINVAL, "debug_get: unknown plane");
+    }
+    CK(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+    return RFSR_OK;
+}
+
+int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
+                    const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
+                    uint8_t *d_out_u8, void *cuda_stream)
+{
+    if (!cfg || !d_smp || !d_msk) return fail(RFSR_EINVAL, "fsr_device: NULL argument");
+    if ((d_psum == nullptr) != (d_pcnt == nullptr))
+        return fail(RFSR_EINVAL, "fsr_device: psum and pcnt must both be given or both be NULL");
+    if (((uintptr_t)d_psum & 1u) || ((uintptr_t)d_out_f32 & 3u))
+        return fail(RFSR_EINVAL, "fsr_device: psum must be 2-byte and out_f32 4-byte aligned");
+    int rc = check_stream_config(cfg);
+    if (rc) return rc;
+    // tables and a zero status word, cached per (device, rho)
+    static std::mutex mu;
+    static std::map<std::pair<int, float>, std::pair<float *, int *>> cache;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    float *tables = nullptr;
+    int *zero = nullptr;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto key = std::make_pair(dev, cfg->fsr_rho);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            FsrTables tb;
+            fill_fsr_tables(tb, cfg->fsr_rho);
+            CK(cudaMalloc((void **)&tables, sizeof(tb)));
+            CK(cudaMemcpy(tables, &tb, sizeof(tb), cudaMemcpyHostToDevice));
+            CK(cudaMalloc((void **)&zero, 64));
+            CK(cudaMemset(zero, 0, 64));
+            cache[key] = std::make_pair(tables, zero);
+        } else {
+            tables = it->second.first;
+            zero = it->second.second;
+        }
+    }
+    FrameTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.H = cfg->height;
+    t.W = cfg->width;
+    t.fsr_iters = cfg->fsr_iterations;
+    t.fsr_gamma = cfg->fsr_gamma;
+    t.fsr_proj_weight = cfg->fsr_proj_weight;
+    t.fsr_overwrite_projected = cfg->fsr_overwrite_projected;
+    t.fsr_tables = tables;
+    t.cur_smp = const_cast<uint8_t *>(d_smp);
+    t.cur_msk = const_cast<uint8_t *>(d_msk);
+    t.psum = const_cast<uint16_t *>(d_psum);
+    t.pcnt = const_cast<uint8_t *>(d_pcnt);
+    t.fsr_out = d_out_f32;
+    t.cur_rec = nullptr;
+    t.out_u8 = d_out_u8;
+    t.status = zero;
+    CK(launch_fsr(t, (cudaStream_t)cuda_stream));
+    return RFSR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+"""ctypes binding of the C ABI in include/rfsr.h (argument marshalling only).
+
+Every step of the frame path runs in the CUDA library ``librfsr.so``; there is no Python or CPU
+fallback: if the library is missing, ``load()`` raises.  Device buffers may be given as torch
+CUDA tensors (their ``data_ptr()`` is passed) or as integer device addresses.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librfsr.so")
+
+RFSR_OK, RFSR_EINVAL, RFSR_EMASK, RFSR_ENOMEM, RFSR_EAGAIN, RFSR_EBUSY, RFSR_ETIMEDOUT, \
+    RFSR_EDEVICE, RFSR_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+CC_MODES = {"none": 0, "rme": 1, "rmc": 2, "frmc": 3, "nnc": 4, "nnc_frmc": 5}
+DEC_MEASURED, DEC_NOT_PROJECTABLE, DEC_NNC_REJECT, DEC_CHECK_REJECT, DEC_ACCEPT = range(5)
+MASK_FIXED, MASK_DYNAMIC = 0, 1
+DBG_MV, DBG_FMV, DBG_DECISION, DBG_PSUM, DBG_PCNT, DBG_FSR, DBG_REC, DBG_RMV = range(8)
+
+_ERRNAMES = {RFSR_EINVAL: "EINVAL", RFSR_EMASK: "EMASK", RFSR_ENOMEM: "ENOMEM",
+             RFSR_EAGAIN: "EAGAIN", RFSR_EBUSY: "EBUSY", RFSR_ETIMEDOUT: "ETIMEDOUT",
+             RFSR_EDEVICE: "EDEVICE", RFSR_ESTATE: "ESTATE"}
+
+
+class RfsrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rfsr_engine_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
+                ("max_inflight", C.c_int), ("batched", C.c_int)]
+
+
+class rfsr_stream_config(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("mask_type", C.c_int),
+                ("cc_mode", C.c_int), ("num_refs", C.c_int), ("template_size", C.c_int),
+                ("search_radius", C.c_int), ("check_radius", C.c_int),
+                ("fsr_iterations", C.c_int), ("fsr_rho", C.c_float), ("fsr_gamma", C.c_float),
+                ("fsr_proj_weight", C.c_float), ("fsr_overwrite_projected", C.c_int),
+                ("keep_f32", C.c_int)]
+
+
+class rfsr_stream_info(C.Structure):
+    _fields_ = [("height", C.c_int), ("width", C.c_int), ("live", C.c_int),
+                ("frames_pushed", C.c_longlong), ("frames_collected", C.c_longlong),
+                ("history_frames", C.c_int), ("device_bytes", C.c_size_t)]
+
+
+# exported symbols with their argument types (also used by the export test)
+_VP, _I = C.c_void_p, C.c_int
+SYMBOLS = {
+    "rfsr_engine_config_default": ([C.POINTER(rfsr_engine_config)], None),
+    "rfsr_stream_config_default": ([C.POINTER(rfsr_stream_config)], None),
+    "rfsr_engine_create": ([C.POINTER(rfsr_engine_config), C.POINTER(_VP)], _I),
+    "rfsr_engine_destroy": ([_VP], _I),
+    "rfsr_engine_step": ([_VP], _I),
+    "rfsr_engine_sync": ([_VP, _I], _I),
+    "rfsr_create_stream": ([_VP, C.POINTER(rfsr_stream_config), C.POINTER(_VP)], _I),
+    "rfsr_push_frame": ([_VP, _VP, _VP], _I),
+    "rfsr_push_frame_device": ([_VP, _VP, _VP], _I),
+    "rfsr_get_frame": ([_VP, _VP, _VP, _I], _I),
+    "rfsr_get_frame_device": ([_VP, _VP, _VP, _I], _I),
+    "rfsr_destroy": ([_VP], _I),
+    "rfsr_stream_get_info": ([_VP, C.POINTER(rfsr_stream_info)], _I),
+    "rfsr_set_history": ([_VP, _I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP)], _I),
+    "rfsr_debug_get": ([_VP, _I, _I, _VP], _I),
+    "rfsr_fsr_device": ([C.POINTER(rfsr_stream_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "rfsr_kernel_launches": ([], C.c_longlong),
+    "rfsr_last_error": ([], C.c_char_p),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``librfsr.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run __graft_entry__.build())")
+        lib = C.CDLL(path)
+        for name, (args, res) in SYMBOLS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise RfsrError(rc, load().rfsr_last_error().decode())
+    return rc
+
+
+def _ptr(x) -> Optional[int]:
+    """Device / host address of a torch tensor, numpy array, or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = MASK_DYNAMIC,
+                  num_refs: int = 3, template_size: int = 9, search_radius: int = 8,
+                  check_radius: Optional[int] = None, fsr_iterations: int = 100,
+                  fsr_rho: float = 0.7, fsr_gamma: float = 0.5, fsr_proj_weight: float = 1.0,
+                  fsr_overwrite_projected: bool = False, keep_f32: bool = False
+                  ) -> rfsr_stream_config:
+    c = rfsr_stream_config()
+    load().rfsr_stream_config_default(C.byref(c))
+    c.height, c.width = height, width
+    c.cc_mode = CC_MODES[cc_mode] if isinstance(cc_mode, str) else int(cc_mode)
+    c.mask_type = mask_type
+    c.num_refs = num_refs
+    c.template_size = template_size
+    c.search_radius = search_radius
+    c.check_radius = search_radius if check_radius is None else check_radius
+    c.fsr_iterations = fsr_iterations
+    c.fsr_rho, c.fsr_gamma, c.fsr_proj_weight = fsr_rho, fsr_gamma, fsr_proj_weight
+    c.fsr_overwrite_projected = int(bool(fsr_overwrite_projected))
+    c.keep_f32 = int(bool(keep_f32))
+    return c
+
+
+class Engine:
+    """rfsr_engine_create / rfsr_engine_destroy."""
+
+    def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
+                 max_inflight: int = 4, batched: bool = False):
+        lib = load()
+        cfg = rfsr_engine_config()
+        lib.rfsr_engine_config_default(C.byref(cfg))
+        cfg.device, cfg.memory_budget = device, memory_budget
+        cfg.cuda_stream = cuda_stream
+        cfg.max_inflight, cfg.batched = max_inflight, int(batched)
+        h = C.c_void_p()
+        _check(lib.rfsr_engine_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self.streams = []
+
+    def create_stream(self, **kw) -> "Stream":
+        cfg = stream_config(**kw)
+        h = C.c_void_p()
+        _check(load().rfsr_create_stream(self.handle, C.byref(cfg), C.byref(h)))
+        s = Stream(self, h, cfg)
+        self.streams.append(s)
+        return s
+
+    def step(self) -> int:
+        return _check(load().rfsr_engine_step(self.handle))
+
+    def sync(self, timeout_ms: int = -1):
+        _check(load().rfsr_engine_sync(self.handle, timeout_ms))
+
+    def destroy(self):
+        if self.handle:
+            for s in self.streams:
+                s.handle = None
+            _check(load().rfsr_engine_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+
+class Stream:
+    """rfsr_create_stream / rfsr_push_frame / rfsr_get_frame / rfsr_destroy and the debug calls."""
+
+    def __init__(self, engine: Engine, handle, cfg: rfsr_stream_config):
+        self.engine, self.handle, self.cfg = engine, handle, cfg
+        self.H, self.W = cfg.height, cfg.width
+
+    def push_frame(self, samples: np.ndarray, mask: np.ndarray):
+        s = np.ascontiguousarray(samples, np.uint8)
+        m = np.ascontiguousarray(mask, np.uint8)
+        assert s.shape == (self.H, self.W) and m.shape == (self.H, self.W)
+        _check(load().rfsr_push_frame(self.handle, s.ctypes.data, m.ctypes.data))
+
+    def push_frame_device(self, d_samples, d_mask):
+        _check(load().rfsr_push_frame_device(self.handle, _ptr(d_samples), _ptr(d_mask)))
+
+    def get_frame(self, timeout_ms: int = -1, f32: bool = False):
+        out = np.empty((self.H, self.W), np.uint8)
+        o32 = np.empty((self.H, self.W), np.float32) if f32 else None
+        _check(load().rfsr_get_frame(self.handle, out.ctypes.data,
+                                     None if o32 is None else o32.ctypes.data, timeout_ms))
+        return (out, o32) if f32 else out
+
+    def get_frame_device(self, d_out_u8=None, d_out_f32=None, timeout_ms: int = -1):
+        _check(load().rfsr_get_frame_device(self.handle, _ptr(d_out_u8), _ptr(d_out_f32),
+                                            timeout_ms))
+
+    def set_history(self, history: Sequence[Tuple[np.ndarray, np.ndarray, np.ndarray]]):
+        """history[k-1] = (reconstruction, samples, 0/1 mask) of frame t-k."""
+        n = len(history)
+        keep = [tuple(np.ascontiguousarray(a, np.uint8) for a in h) for h in history]
+        arr = C.c_void_p * max(1, n)
+        rec = arr(*[h[0].ctypes.data for h in keep])
+        smp = arr(*[h[1].ctypes.data for h in keep])
+        msk = arr(*[h[2].ctypes.data for h in keep])
+        _check(load().rfsr_set_history(self.handle, n, rec, smp, msk))
+
+    def debug_get(self, what: int, k: int = 0) -> np.ndarray:
+        H, W = self.H, self.W
+        shape, dt = {DBG_MV: ((H, W, 2), np.int8), DBG_FMV: ((H, W, 2), np.int8),
+                     DBG_RMV: ((H, W, 2), np.int8), DBG_DECISION: ((H, W), np.uint8),
+                     DBG_PSUM: ((H, W), np.uint16), DBG_PCNT: ((H, W), np.uint8),
+                     DBG_FSR: ((H, W), np.float32), DBG_REC: ((H, W), np.uint8)}[what]
+        out = np.empty(shape, dt)
+        _check(load().rfsr_debug_get(self.handle, what, k, out.ctypes.data))
+        return out
+
+    def info(self) -> rfsr_stream_info:
+        i = rfsr_stream_info()
+        _check(load().rfsr_stream_get_info(self.handle, C.byref(i)))
+        return i
+
+    def destroy(self):
+        if self.handle:
+            _check(load().rfsr_destroy(self.handle))
+            self.handle = None
+            if self in self.engine.streams:
+                self.engine.streams.remove(self)
+
+
+def fsr_device(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, height: int, width: int,
+               cuda_stream: Optional[int] = None, **fsr_kw):
+    """rfsr_fsr_device: stand-alone FSR over device buffers."""
+    cfg = stream_config(height, width, **fsr_kw)
+    _check(load().rfsr_fsr_device(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
+                                  _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8), cuda_stream))
+
+
+def kernel_launches() -> int:
+    return int(load().rfsr_kernel_launches())
+
+
+# C-ABI names, for callers who prefer the flat interface
+rfsr_fsr_device = fsr_device
+rfsr_kernel_launches = kernel_launches
