@@ -85,6 +85,8 @@ typedef struct {
     int max_inflight;      /* frames per stream pushed and not yet collected; 0 = 4             */
     int batched;           /* 0: each push launches its frame step at once; 1: pushes are staged
                               and rfsr_engine_step() runs one batched step over all streams      */
+    int profile;           /* 1: record CUDA events between the phases of every frame step
+                              (read with rfsr_stream_phase_ms)                                   */
 } rfsr_engine_config;
 
 typedef struct {
@@ -190,6 +192,20 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst);
 int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
                     const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
                     uint8_t *d_out_u8, void *cuda_stream);
+
+/* Device time of the phases of the most recently pushed frame of s (waits for it), measured with
+ * CUDA events on the engine's stream around each kernel: ms[0] ingest, ms[1] motion estimation
+ * (and the RME reverse field), ms[2] checks + projection, ms[3] FSR + 8-bit reconstruction.
+ * Needs an engine created with profile = 1 (else ESTATE). */
+int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4]);
+
+/* Throughput probe for roofline denominators (not part of the method): runs a chain of one
+ * instruction kind on every SM of `device` and returns instructions per second and per clock per
+ * SM.  kind: 0 3-input add, 1 3-input logic, 2 byte permute, 3 byte |a-b| (__vabsdiffu4),
+ * 4 byte SAD (__vsadu4) + add, 5 16-bit x2 3-way max, 6 16-bit x2 3-way min, 7 integer multiply-add,
+ * 8 |a-b|+c (__sad), 9 32-bit min, 10 xor, 11 FP32 fused multiply-add.  Synchronous; allocates
+ * and frees its own small buffers.  Errors: EINVAL, EDEVICE. */
+int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_sec, double *ops_per_clk_sm);
 
 /* Kernel launches made by this process so far (all engines), for launch accounting. */
 long long rfsr_kernel_launches(void);

@@ -93,6 +93,8 @@ def _load():
         lib.orc_cc_pixel.restype = I
         lib.orc_fsr_block_ex.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I, I,
                                          dp, dp, dp, dp, dp, dp, ip, dp]
+        lib.orc_fsr_block_alt.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I,
+                                          I, dp, dp, dp, dp, dp, dp, ip, dp, dp, I]
         lib.orc_fsr_frame.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, dp, dp]
         lib.orc_quantize.argtypes = [dp, u8p, u8p, I, I, u8p]
         _lib = lib
@@ -241,9 +243,12 @@ class FsrTrace:
     R: np.ndarray            # (N, N) complex final residual spectrum
     selected: np.ndarray     # (iterations,) linear bin index per iteration
     min_gap: float
+    gaps: np.ndarray         # (iterations,) relative best / second-best gap per iteration
 
 
-def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx) -> FsrTrace:
+def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx, second_at: int = -1) -> FsrTrace:
+    """FSR of block (by, bx).  second_at >= 0 resolves the selection at that iteration the other
+    way (second best bin): the alternative continuation at a near tie."""
     lib = _load()
     smp, msk = _u8(smp), _u8(msk)
     H, W = smp.shape
@@ -254,14 +259,35 @@ def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx) -> FsrTrace:
     w, f, g = np.zeros((N, N)), np.zeros((N, N)), np.zeros((N, N))
     rre, rim = np.zeros((N, N)), np.zeros((N, N))
     sel = np.zeros(max(1, params.iterations), np.int32)
+    gaps = np.zeros(max(1, params.iterations))
     gap = C.c_double()
     cp = params._c()
-    lib.orc_fsr_block_ex(C.byref(cp), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
-                         _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, by, bx,
-                         _p(out, C.c_double), _p(w, C.c_double), _p(f, C.c_double),
-                         _p(g, C.c_double), _p(rre, C.c_double), _p(rim, C.c_double),
-                         sel.ctypes.data_as(C.POINTER(C.c_int)), C.byref(gap))
-    return FsrTrace(out, w, f, g, rre + 1j * rim, sel[:params.iterations], gap.value)
+    lib.orc_fsr_block_alt(C.byref(cp), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
+                          _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, by, bx,
+                          _p(out, C.c_double), _p(w, C.c_double), _p(f, C.c_double),
+                          _p(g, C.c_double), _p(rre, C.c_double), _p(rim, C.c_double),
+                          sel.ctypes.data_as(C.POINTER(C.c_int)), C.byref(gap),
+                          _p(gaps, C.c_double), int(second_at))
+    return FsrTrace(out, w, f, g, rre + 1j * rim, sel[:params.iterations], gap.value,
+                    gaps[:params.iterations])
+
+
+def fsr_block_valid(params: FsrParams, smp, msk, psum, pcnt, by, bx, got, tol: float = 1e-4,
+                    near: float = 1e-3, tries: int = 12):
+    """Is ``got`` (B x B) a result of the method for this block?  Either within ``tol`` of the
+    argmax continuation, or -- where the selection had a near tie (relative gap < ``near``) --
+    within ``tol`` of the continuation that resolves one of those near ties the other way.
+    Returns (ok, error of the plain continuation, iteration used or -1)."""
+    tr = fsr_block(params, smp, msk, psum, pcnt, by, bx)
+    e0 = float(np.abs(np.asarray(got, np.float64) - tr.out).max())
+    if e0 <= tol:
+        return True, e0, -1
+    order = [int(i) for i in np.argsort(tr.gaps) if tr.gaps[i] < near][:tries]
+    for i in order:
+        alt = fsr_block(params, smp, msk, psum, pcnt, by, bx, second_at=i)
+        if float(np.abs(np.asarray(got, np.float64) - alt.out).max()) <= tol:
+            return True, e0, i
+    return False, e0, -1
 
 
 def fsr_frame(params: FsrParams, smp, msk, psum=None, pcnt=None):

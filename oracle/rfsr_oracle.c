@@ -456,13 +456,16 @@ static void dft2_real(const double *a, int N, const double *tc, const double *ts
 }
 
 /* Extended form for tests: besides the B*B block output it can return the support weights and
- * values, the model g over the whole support, the final residual spectrum, the selected bins and
- * the smallest relative gap between the best and second best selection criterion seen over the
- * iterations (a near tie there means that a different rounding may select a different bin). */
-void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
-                      const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
-                      double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
-                      double *rim_out, int *sel_out, double *min_gap_out)
+ * values, the model g over the whole support, the final residual spectrum, the selected bins, the
+ * relative gap between the best and second best selection criterion at every iteration and their
+ * minimum.  A near tie (tiny gap) means that another rounding of the same arithmetic may select
+ * the other bin; both continuations are results of the method.  second_at >= 0 takes the second
+ * best bin at that one iteration (the other resolution of a near tie); -1 = plain argmax. */
+void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
+                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
+                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
+                       double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
+                       int second_at)
 {
     const int N = P->N, B = P->B, o = (P->N - P->B) / 2;
     static double w[ORC_NMAX * ORC_NMAX], f[ORC_NMAX * ORC_NMAX], wf[ORC_NMAX * ORC_NMAX];
@@ -498,20 +501,20 @@ void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t
     double min_gap = INFINITY;
     const double W0 = Wre[0];
     for (int it = 0; it < P->iterations && W0 > 0.0; ++it) {
-        int best = -1;
+        int best = -1, best2 = -1;
         double bv = -1.0, second = -1.0;
         for (int k = 0; k < N; ++k)
             for (int l = 0; l < N; ++l) {
                 int lin = k * N + l, conj_lin = ((N - k) % N) * N + (N - l) % N;
                 if (lin > conj_lin) continue;                 /* canonical member of the pair */
                 double e = wf[lin] * (Rre[lin] * Rre[lin] + Rim[lin] * Rim[lin]);
-                if (e > bv) { second = bv; bv = e; best = lin; }
-                else if (e > second) second = e;
+                if (e > bv) { second = bv; best2 = best; bv = e; best = lin; }
+                else if (e > second) { second = e; best2 = lin; }
             }
-        if (bv > 0.0 && second >= 0.0) {
-            double gap = (bv - second) / bv;
-            if (gap < min_gap) min_gap = gap;
-        }
+        double gap = (bv > 0.0 && second >= 0.0) ? (bv - second) / bv : INFINITY;
+        if (gap < min_gap) min_gap = gap;
+        if (gaps_out) gaps_out[it] = gap;
+        if (it == second_at && best2 >= 0) best = best2;
         int uk = best / N, ul = best % N;
         int self = (((N - uk) % N) == uk) && (((N - ul) % N) == ul);
         double dre = P->gamma * Rre[best] / W0, dim = P->gamma * Rim[best] / W0;
@@ -557,6 +560,15 @@ void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t
     if (rre_out) memcpy(rre_out, Rre, sizeof(double) * N * N);
     if (rim_out) memcpy(rim_out, Rim, sizeof(double) * N * N);
     if (min_gap_out) *min_gap_out = min_gap;
+}
+
+void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
+                      const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
+                      double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
+                      double *rim_out, int *sel_out, double *min_gap_out)
+{
+    orc_fsr_block_alt(P, smp, msk, psum, pcnt, H, W, by, bx, out, w_out, f_out, g_out, rre_out,
+                      rim_out, sel_out, min_gap_out, 0, -1);
 }
 
 void orc_fsr_block(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,

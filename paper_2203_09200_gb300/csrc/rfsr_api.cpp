@@ -114,6 +114,7 @@ struct Slot {
     int *d_status = nullptr;
     int *h_status = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t phase[5] = {};  // profile: before ingest, after ingest / ME / checks / FSR
     bool host_push = false;
 };
 
@@ -165,8 +166,11 @@ struct rfsr_stream {
     }
     void release()
     {
-        for (auto &s : slots)
+        for (auto &s : slots) {
             if (s.done) cudaEventDestroy(s.done);
+            for (auto &ev : s.phase)
+                if (ev) cudaEventDestroy(ev);
+        }
         for (void *p : dev_allocs) cudaFree(p);
         for (void *p : host_allocs) cudaFreeHost(p);
         dev_allocs.clear();
@@ -378,6 +382,11 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
         if (r_) return bail(r_);
         cudaError_t er = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
+        if (e->cfg.profile)
+            for (auto &ev : sl.phase) {
+                er = cudaEventCreate(&ev);
+                if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
+            }
     }
 #undef AL
     {
@@ -436,12 +445,18 @@ static int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, con
     const int *prev = s->last_slot >= 0 ? s->slots[s->last_slot].d_status : s->d_zero;
     FrameTask t;
     fill_task(s, sl, t, in_smp, in_msk, prev);
+    const bool prof = e->cfg.profile != 0;
     CK(cudaMemsetAsync(sl.d_status, 0, sizeof(int), e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[0], e->stream));
     CK(launch_ingest(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[1], e->stream));
     CK(launch_me(t, e->stream));
     if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
     CK(launch_cc_project(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[3], e->stream));
     CK(launch_fsr(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[4], e->stream));
     CK(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     s->last_K = t.K;
     s->last_ring = s->ring_head;
@@ -665,6 +680,18 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
     default: return fail(RFSR_EINVAL, "debug_get: unknown plane");
     }
     CK(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
+    return RFSR_OK;
+}
+
+int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4])
+{
+    if (!s || !ms) return fail(RFSR_EINVAL, "stream_phase_ms: NULL argument");
+    if (!s->eng->cfg.profile) return fail(RFSR_ESTATE, "stream_phase_ms: engine not created with profile = 1");
+    if (s->last_slot < 0) return fail(RFSR_ESTATE, "stream_phase_ms: no frame pushed");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    Slot &sl = s->slots[s->last_slot];
+    CK(cudaEventSynchronize(sl.phase[4]));
+    for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&ms[i], sl.phase[i], sl.phase[i + 1]));
     return RFSR_OK;
 }
 

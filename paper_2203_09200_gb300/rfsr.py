@@ -35,7 +35,7 @@ class RfsrError(RuntimeError):
 
 class rfsr_engine_config(C.Structure):
     _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
-                ("max_inflight", C.c_int), ("batched", C.c_int)]
+                ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int)]
 
 
 class rfsr_stream_config(C.Structure):
@@ -72,6 +72,8 @@ SYMBOLS = {
     "rfsr_set_history": ([_VP, _I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP)], _I),
     "rfsr_debug_get": ([_VP, _I, _I, _VP], _I),
     "rfsr_fsr_device": ([C.POINTER(rfsr_stream_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "rfsr_stream_phase_ms": ([_VP, C.POINTER(C.c_float)], _I),
+    "rfsr_alu_peak": ([_I, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_double)], _I),
     "rfsr_kernel_launches": ([], C.c_longlong),
     "rfsr_last_error": ([], C.c_char_p),
 }
@@ -141,13 +143,13 @@ class Engine:
     """rfsr_engine_create / rfsr_engine_destroy."""
 
     def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
-                 max_inflight: int = 4, batched: bool = False):
+                 max_inflight: int = 4, batched: bool = False, profile: bool = False):
         lib = load()
         cfg = rfsr_engine_config()
         lib.rfsr_engine_config_default(C.byref(cfg))
         cfg.device, cfg.memory_budget = device, memory_budget
         cfg.cuda_stream = cuda_stream
-        cfg.max_inflight, cfg.batched = max_inflight, int(batched)
+        cfg.max_inflight, cfg.batched, cfg.profile = max_inflight, int(batched), int(profile)
         h = C.c_void_p()
         _check(lib.rfsr_engine_create(C.byref(cfg), C.byref(h)))
         self.handle = h
@@ -228,6 +230,12 @@ class Stream:
         _check(load().rfsr_debug_get(self.handle, what, k, out.ctypes.data))
         return out
 
+    def phase_ms(self):
+        """(ingest, ME, checks + projection, FSR) device ms of the last pushed frame."""
+        a = (C.c_float * 4)()
+        _check(load().rfsr_stream_phase_ms(self.handle, a))
+        return tuple(float(x) for x in a)
+
     def info(self) -> rfsr_stream_info:
         i = rfsr_stream_info()
         _check(load().rfsr_stream_get_info(self.handle, C.byref(i)))
@@ -247,6 +255,17 @@ def fsr_device(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, height: int, w
     cfg = stream_config(height, width, **fsr_kw)
     _check(load().rfsr_fsr_device(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
                                   _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8), cuda_stream))
+
+
+ALU_KINDS = ["iadd3", "lop3", "prmt", "vabsdiffu4", "vsadu4+add", "vimax3_u16x2",
+             "vimin3_u16x2", "imad", "sad", "imin", "xor", "ffma"]
+
+
+def alu_peak(kind: str, device: int = 0, iters: int = 2000):
+    """rfsr_alu_peak: (instructions per second, per clock per SM) of one instruction kind."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().rfsr_alu_peak(device, ALU_KINDS.index(kind), iters, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def kernel_launches() -> int:

@@ -1,10 +1,12 @@
 """GPU parity: the CUDA frame step through the C ABI against the CPU oracle.
 
 Integer results (motion fields, NNC-filtered fields, decision labels, projection sums and
-counts) must match bit-exactly; the FSR output (FP32 on the GPU, FP64 in the oracle, [0, 1]
-scale) within 1e-4 max abs.  A block may exceed 1e-4 only where the oracle's own selection
-sequence had a near tie (relative gap < 1e-3 between the best and second-best bin), where both
-selections are correct; such blocks must stay below 1 % and within 1e-2.
+counts) must match bit-exactly.  The FSR output (FP32 on the GPU, FP64 in the oracle, [0, 1]
+scale) must be within 1e-4 max abs of the oracle, block by block.  FSR selects one basis pair per
+iteration by an argmax; where the oracle's selection had a near tie (relative gap < 1e-3), FP32
+rounding may resolve it the other way, and both continuations are results of the method: such a
+block must then be within 1e-4 of the oracle's own FP64 continuation that resolves one of those
+near ties the other way (oracle.fsr_block_valid), and such blocks must stay rare.
 
 Past frames are injected with rfsr_set_history from the generator (ground-truth frames), so
 both sides see identical inputs; no oracle input ever comes from the GPU.
@@ -53,18 +55,32 @@ def gpu_step(eng, smp, msk, hist, **cfg):
     return out
 
 
-def assert_fsr_close(got, ref, gap, B=4):
-    err = np.abs(got.astype(np.float64) - ref)
+def assert_fsr_close(got, smp, msk, psum, pcnt, ref_out, params=None, B=4, max_frac=0.05):
+    """Every block within FSR_TOL of the oracle, or a valid near-tie continuation."""
+    params = params or oracle.FsrParams()
+    H, W = got.shape
+    err = np.abs(got.astype(np.float64) - ref_out)
     if err.max() <= FSR_TOL:
-        return
-    H, W = err.shape
+        return 0
     nby, nbx = -(-H // B), -(-W // B)
     pad = np.zeros((nby * B, nbx * B))
     pad[:H, :W] = err
     eb = pad.reshape(nby, B, nbx, B).max(axis=(1, 3))
-    bad = eb > FSR_TOL
-    assert (gap[bad] < 1e-3).all(), f"FSR error {eb[bad].max()} in blocks without a near tie"
-    assert bad.mean() < 0.01 and eb.max() < 1e-2, (bad.sum(), eb.max())
+    bad = np.argwhere(eb > FSR_TOL)
+    for by, bx in bad:
+        blk = got[B * by:B * by + B, B * bx:B * bx + B]
+        ok, e0, it = oracle.fsr_block_valid(params, smp, msk, psum, pcnt, int(by), int(bx), blk)
+        assert ok, f"FSR block ({by},{bx}) off by {e0} and not a near-tie continuation"
+    assert len(bad) <= max(2, max_frac * nby * nbx), f"{len(bad)} near-tie blocks"
+    return len(bad)
+
+
+def assert_rec_consistent(rec, f32, smp, msk):
+    """8-bit output: measured samples exact; elsewhere the half-to-even rounding of 255 x."""
+    m = msk == 1
+    np.testing.assert_array_equal(rec[m], smp[m])
+    q = np.clip(np.rint(np.float32(255.0) * f32), 0, 255).astype(np.uint8)
+    np.testing.assert_array_equal(rec[~m], q[~m])
 
 
 def compare(got, ref, msk, smp):
@@ -74,13 +90,8 @@ def compare(got, ref, msk, smp):
         np.testing.assert_array_equal(got["dec"][k], ref.dec[k], err_msg=f"dec k={k + 1}")
     np.testing.assert_array_equal(got["psum"], ref.psum)
     np.testing.assert_array_equal(got["pcnt"], ref.pcnt)
-    assert_fsr_close(got["fsr"], ref.fsr, ref.min_gap)
-    # 8-bit reconstruction: measured pixels exact, others within rounding of the oracle value
-    m = msk == 1
-    np.testing.assert_array_equal(got["rec"][m], smp[m])
-    lim = 0.5 + 255 * FSR_TOL + 1e-9
-    assert (np.abs(got["rec"][~m].astype(np.float64) -
-                   np.clip(255 * ref.fsr[~m], 0, 255)) <= lim + 0.5).all()
+    assert_fsr_close(got["fsr"], smp, msk, ref.psum, ref.pcnt, ref.fsr)
+    assert_rec_consistent(got["rec"], got["fsr"], smp, msk)
 
 
 # --------------------------------------------------------------------------------------------
@@ -206,13 +217,11 @@ def test_fsr_device_full_hd_sampled(engine):
     blocks += [(int(rng.integers(0, nby)), int(rng.integers(0, nbx))) for _ in range(60)]
     near = 0
     for by, bx in blocks:
-        tr = oracle.fsr_block(P, smp, msk, psum, pcnt, by, bx)
-        g = got[4 * by:4 * by + 4, 4 * bx:4 * bx + 4].astype(np.float64)
-        e = np.abs(g - tr.out).max()
-        if e > FSR_TOL:
-            assert tr.min_gap < 1e-3 and e < 1e-2, (by, bx, e, tr.min_gap)
-            near += 1
-    assert near <= 2
+        g = got[4 * by:4 * by + 4, 4 * bx:4 * bx + 4]
+        ok, e0, it = oracle.fsr_block_valid(P, smp, msk, psum, pcnt, by, bx, g)
+        assert ok, (by, bx, e0)
+        near += e0 > FSR_TOL
+    assert near <= 4
     m = msk == 1
     np.testing.assert_array_equal(got8[m], smp[m])
     np.testing.assert_allclose(got[m], smp[m] / 255.0, atol=1e-7)
@@ -249,7 +258,8 @@ def test_single_frame_is_fsr_only(engine):
     got = gpu_step(engine, seq.samples[0], seq.masks[0], [])
     ref = oracle.frame_step(seq.samples[0], seq.masks[0], [])
     assert not got["pcnt"].any()
-    assert_fsr_close(got["fsr"], ref.fsr, ref.min_gap)
+    assert_fsr_close(got["fsr"], seq.samples[0], seq.masks[0], ref.psum, ref.pcnt, ref.fsr)
+    assert_rec_consistent(got["rec"], got["fsr"], seq.samples[0], seq.masks[0])
 
 
 def test_errors(engine):
