@@ -199,6 +199,39 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
  * Needs an engine created with profile = 1 (else ESTATE). */
 int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4]);
 
+/* ---- one frame of ME + checks + projection without allocating device memory ------------- */
+/* The paper has no counterpart to this call; it exists for callers that cannot allocate device
+ * memory while they run -- a real-time loop that must keep allocator locks and driver
+ * allocations out of its latency, a plugin inside an application that owns all of the GPU's
+ * memory and hands out only buffers it created, or code that may not allocate after start-up.
+ * It computes what one frame step computes up to the projection (ingest, motion estimation
+ * against nrefs past frames, the checks of cfg->cc_mode, projection sums and counts), writing
+ * only the caller's outputs, and calls no cudaMalloc / cudaFree or any allocating routine.
+ * Every intermediate plane lives in one fixed array of 8 MiB in the library's static device
+ * memory, which each GPU that loads the library holds until the process exits.  A frame fits if
+ *     256 + 2*A(H*W) + nrefs*(2*A(2*H*W) + A(H*W)) [+ nrefs*A(2*H*W) in RME mode] <= 8 MiB,
+ * A(n) = n rounded up to a multiple of 256 (e.g. 640x480 with three past frames in any mode);
+ * larger frames are rejected with EINVAL and a message giving the bytes needed.
+ *   cfg: height, width, cc_mode, template_size, search_radius, check_radius (FSR fields unused)
+ *   d_smp, d_msk: current sample plane and 0/1 mask (H*W uint8, device, 2-byte aligned)
+ *   d_ref_rec[k], d_ref_smp[k], d_ref_msk[k] (k < nrefs <= 3): HOST arrays of DEVICE pointers
+ *       to the reconstruction, sample plane and 0/1 mask of frame t-1-k (H*W uint8 each)
+ *   d_psum, d_pcnt: outputs, projection sums (H*W uint16, 2-byte aligned) and counts (H*W uint8)
+ *   d_dec: optional output, nrefs*H*W RFSR_DEC_* labels (k-major); d_status: optional output,
+ *       one int (4-byte aligned) set to 0 when d_msk is a quarter-sampling mask and to 1 when it
+ *       is not (the other outputs are then left unwritten)
+ *   cuda_stream: cudaStream_t to run on (NULL = legacy default stream); returns without waiting.
+ * It runs on the calling thread's current device.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last call's contents, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race: serialise them.
+ * Errors: EINVAL (NULL / misaligned / out-of-range arguments, frame too large), EDEVICE. */
+int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const uint8_t *d_smp,
+                               const uint8_t *d_msk, int nrefs, const uint8_t *const *d_ref_rec,
+                               const uint8_t *const *d_ref_smp, const uint8_t *const *d_ref_msk,
+                               uint16_t *d_psum, uint8_t *d_pcnt, uint8_t *d_dec, int *d_status,
+                               void *cuda_stream);
+
 /* Throughput probe for roofline denominators (not part of the method): runs a chain of one
  * instruction kind on every SM of `device` and returns instructions per second and per clock per
  * SM.  kind: 0 3-input add, 1 3-input logic, 2 byte permute, 3 byte |a-b| (__vabsdiffu4),

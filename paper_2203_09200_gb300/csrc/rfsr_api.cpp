@@ -104,6 +104,8 @@ int wait_event(cudaEvent_t ev, int timeout_ms)
 
 }  // namespace
 
+int rfsr::set_error(int code, const std::string &msg) { return fail(code, msg); }
+
 struct Slot {
     uint8_t *h_in = nullptr;    // pinned samples | mask
     uint8_t *d_in = nullptr;    // device samples | mask

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 #include <cuda_runtime.h>
 
@@ -73,6 +74,9 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st);
+
+// set the calling thread's rfsr_last_error() message; returns code
+int set_error(int code, const std::string &msg);
 
 // number of kernel launches issued by this process (all launchers count)
 void count_launch(int n = 1);

@@ -73,6 +73,8 @@ SYMBOLS = {
     "rfsr_debug_get": ([_VP, _I, _I, _VP], _I),
     "rfsr_fsr_device": ([C.POINTER(rfsr_stream_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "rfsr_stream_phase_ms": ([_VP, C.POINTER(C.c_float)], _I),
+    "rfsr_me_cc_project_noalloc": ([C.POINTER(rfsr_stream_config), _VP, _VP, _I, C.POINTER(_VP),
+                                    C.POINTER(_VP), C.POINTER(_VP), _VP, _VP, _VP, _VP, _VP], _I),
     "rfsr_alu_peak": ([_I, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_double)], _I),
     "rfsr_kernel_launches": ([], C.c_longlong),
     "rfsr_last_error": ([], C.c_char_p),
@@ -255,6 +257,22 @@ def fsr_device(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, height: int, w
     cfg = stream_config(height, width, **fsr_kw)
     _check(load().rfsr_fsr_device(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
                                   _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8), cuda_stream))
+
+
+def me_cc_project_noalloc(d_smp, d_msk, refs, d_psum, d_pcnt, height: int, width: int,
+                          d_dec=None, d_status=None, cuda_stream: Optional[int] = None, **cfg_kw):
+    """rfsr_me_cc_project_noalloc: ME + checks + projection of one frame for callers that cannot
+    allocate device memory; every intermediate lives in the library's fixed static scratch.
+    refs[k] = (reconstruction, samples, 0/1 mask) of frame t-1-k as device buffers."""
+    cfg = stream_config(height, width, **cfg_kw)
+    n = len(refs)
+    arr = C.c_void_p * max(1, n)
+    rec = arr(*[_ptr(r[0]) for r in refs])
+    smp = arr(*[_ptr(r[1]) for r in refs])
+    msk = arr(*[_ptr(r[2]) for r in refs])
+    _check(load().rfsr_me_cc_project_noalloc(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), n, rec, smp,
+                                             msk, _ptr(d_psum), _ptr(d_pcnt), _ptr(d_dec),
+                                             _ptr(d_status), cuda_stream))
 
 
 ALU_KINDS = ["iadd3", "lop3", "prmt", "vabsdiffu4", "vsadu4+add", "vimax3_u16x2",
