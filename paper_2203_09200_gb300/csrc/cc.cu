@@ -19,18 +19,327 @@
 //   ACCEPT          otherwise: psum(p) += f_sub_{t-k}(q), pcnt(p) += 1
 // The projected value psum/pcnt is the average over the past frames that project (Sec. 2.2).
 // NNC runs first and the reverse check only for NNC survivors (the combination of Sec. 3.1.2).
+//
+// GB300 design: one CTA per 32x32 pixel tile, all past frames in one launch.  The current frame
+// around the tile (template + check halo) is staged once in shared memory as masked samples and
+// byte masks, each in four byte-shifted copies so that a template row at any column is three
+// aligned 32-bit words; the template counts n are computed once per tile.  Per past frame the
+// CTA stages the ME field with a 2-pixel halo and the past frame around the tile, computes the
+// median field once, decides every pixel, and compacts the pixels that need a reverse check into
+// a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
+// registers, lane 0 scores d = 0 and the other lanes split the remaining offsets, each costing T
+// rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.
 #include "rfsr_internal.h"
 
 namespace rfsr {
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int TP = 32;                        // tile side (pixels)
+constexpr int NT = 256;                       // threads per CTA
+constexpr int NW = NT / 32;                   // warps per CTA
+constexpr int HC = 16;                        // staged halo: |d| <= 9 plus template half <= 5,
+                                              // rounded up so the region starts word aligned
+constexpr int RS = TP + 2 * HC;               // staged region side (64)
+constexpr int RWD = RS / 4 + 1;               // words per staged row (+1 feeds the shifted copies)
+constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +- 9)
+constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
+constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
+constexpr int PPT = TP * TP / NT;             // pixels owned per thread
+
+struct Smem {
+    uint32_t cs[4][RS][RWD];      // masked samples, byte-shifted copies
+    uint32_t cm[4][RS][RWD];      // byte masks, byte-shifted copies
+    uint32_t rf[4][RS][RWD];      // past frame (clamped coordinates), byte-shifted copies
+    uint8_t nsrc[NS][NS];         // measured pixels in the template around each source
+    char2 mv[MT][MT];
+    char2 md[MD][MD];
+    uint16_t list[TP * TP];       // tile pixels that need a reverse check
+    uint8_t rej[TP * TP];
+    int nlist;
+};
 
 __device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
 
-// template cost C(src, v) against the past frame: SAD over measured current-frame pixels of the
-// T x T window around src, past-frame coordinates clamped.  n = number of measured pixels.
+__device__ __forceinline__ void cswap(int &a, int &b)
+{
+    const int lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
+
+// median of nine values: sort each group of three, then the median of (largest minimum,
+// median of medians, smallest maximum) -- exact for any input, ties included
+__device__ __forceinline__ int median9(int p0, int p1, int p2, int p3, int p4, int p5, int p6,
+                                       int p7, int p8)
+{
+    cswap(p0, p1); cswap(p1, p2); cswap(p0, p1);
+    cswap(p3, p4); cswap(p4, p5); cswap(p3, p4);
+    cswap(p6, p7); cswap(p7, p8); cswap(p6, p7);
+    const int lo = max(max(p0, p3), p6);
+    const int hi = min(min(p2, p5), p8);
+    return med3(lo, med3(p1, p4, p7), hi);
+}
+
+// FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
+__device__ __forceinline__ int frmc_offset(int i)
+{
+    return i == 3 ? 0 : (i < 3 ? -((1 << (3 - i)) - 1) : (1 << (i - 3)) - 1);
+}
+
+// Stage a frame region (rows y0-HC.., cols x0-HC..) into four byte-shifted copies: copy j, word w
+// of a row holds region bytes 4w+j .. 4w+j+3.  MODE 0: masked samples and 1: byte mask (both 0
+// outside the frame); MODE 2: past frame with clamped coordinates.
+template <int MODE>
+__device__ void stage(uint32_t (&dst)[4][RS][RWD], const uint8_t *__restrict__ src, int H, int W,
+                      int y0, int x0)
+{
+    for (int i = threadIdx.x; i < RS * RWD; i += NT) {
+        const int r = i / RWD, w = i - r * RWD;
+        const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
+        uint32_t v = 0;
+        if (MODE == 2) {
+            const uint8_t *row = src + (size_t)min(max(gy, 0), H - 1) * W;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        } else if (gy >= 0 && gy < H) {
+            // 16-bit loads: W is even and gx is even, so a pixel pair never straddles the border
+            const uint8_t *row = src + (size_t)gy * W;
+#pragma unroll
+            for (int b = 0; b < 4; b += 2) {
+                const int x = gx + b;
+                if (x >= 0 && x < W)
+                    v |= (uint32_t)(*reinterpret_cast<const uint16_t *>(row + x)) << (8 * b);
+            }
+        }
+        dst[0][r][w] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * RS * (RWD - 1); i += NT) {
+        const int j = 1 + i / (RS * (RWD - 1));
+        const int rem = i - (j - 1) * RS * (RWD - 1);
+        const int r = rem / (RWD - 1), w = rem - r * (RWD - 1);
+        dst[j][r][w] = __funnelshift_r(dst[0][r][w], dst[0][r][w + 1], 8 * j);
+    }
+}
+
+// SAD over the measured current pixels of the T x T template whose top-left corner is at region
+// (sy, sx), against the past-frame patch words P held in registers
+template <int T>
+__device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const uint32_t (&P)[T][3])
+{
+    constexpr uint32_t w0 = T >= 4 ? 0xffffffffu : (1u << (8 * T)) - 1u;
+    constexpr uint32_t w1 = T >= 8 ? 0xffffffffu : (T > 4 ? (1u << (8 * (T - 4))) - 1u : 0u);
+    constexpr uint32_t w2 = T >= 12 ? 0xffffffffu : (T > 8 ? (1u << (8 * (T - 8))) - 1u : 0u);
+    const int j = sx & 3, w = sx >> 2;
+    int acc = 0;
+#pragma unroll
+    for (int r = 0; r < T; ++r) {
+        const uint32_t *cs = sm.cs[j][sy + r] + w;
+        const uint32_t *cm = sm.cm[j][sy + r] + w;
+        acc += __vsadu4(cs[0] & w0, P[r][0] & cm[0] & w0);
+        if (w1) acc += __vsadu4(cs[1] & w1, P[r][1] & cm[1] & w1);
+        if (w2) acc += __vsadu4(cs[2] & w2, P[r][2] & cm[2] & w2);
+    }
+    return acc;
+}
+
+template <int T>
+__global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    constexpr int h = T / 2;
+    const int H = t.H, W = t.W;
+    const int x0 = blockIdx.x * TP, y0 = blockIdx.y * TP;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (*t.status) return;
+    const bool use_nnc = t.cc_mode == 4 || t.cc_mode == 5;
+    const bool frmc = t.cc_mode == 3 || t.cc_mode == 5;
+    const bool rmc = t.cc_mode == 2;
+    const bool rme = t.cc_mode == 1;
+
+    stage<0>(sm.cs, t.cur_smp, H, W, y0, x0);
+    stage<1>(sm.cm, t.cur_msk, H, W, y0, x0);
+    __syncthreads();
+    // template counts n around every source position of the tile +- 9 (current mask, 0 outside)
+    for (int i = tid; i < NS * NS; i += NT) {
+        const int sy = i / NS, sx = i - sy * NS;
+        const int ry = sy + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
+        int n = 0;
+        for (int r = 0; r < T; ++r) {
+            const uint32_t *cm = sm.cm[rx & 3][ry + r] + (rx >> 2);
+#pragma unroll
+            for (int b = 0; b < (T + 3) / 4; ++b) {
+                uint32_t m = cm[b];
+                if (4 * b + 4 > T) m &= (1u << (8 * (T - 4 * b))) - 1u;
+                n += __popc(m);
+            }
+        }
+        sm.nsrc[sy][sx] = (uint8_t)(n >> 3);
+    }
+
+    int sum[PPT], cnt[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) sum[i] = cnt[i] = 0;
+
+    for (int k = 0; k < t.K; ++k) {
+        const char2 *mvk = reinterpret_cast<const char2 *>(t.mv[k]);
+        __syncthreads();
+        for (int i = tid; i < MT * MT; i += NT) {
+            const int r = i / MT, c = i - r * MT;
+            const int gy = min(max(y0 - 2 + r, 0), H - 1), gx = min(max(x0 - 2 + c, 0), W - 1);
+            sm.mv[r][c] = mvk[(size_t)gy * W + gx];
+        }
+        if (tid == 0) sm.nlist = 0;
+        if (frmc || rmc) stage<2>(sm.rf, t.ref_rec[k], H, W, y0, x0);
+        __syncthreads();
+        if (use_nnc) {
+            for (int i = tid; i < MD * MD; i += NT) {
+                const int r = i / MD, c = i - r * MD;
+                const char2 a0 = sm.mv[r][c], a1 = sm.mv[r][c + 1], a2 = sm.mv[r][c + 2];
+                const char2 a3 = sm.mv[r + 1][c], a4 = sm.mv[r + 1][c + 1], a5 = sm.mv[r + 1][c + 2];
+                const char2 a6 = sm.mv[r + 2][c], a7 = sm.mv[r + 2][c + 1], a8 = sm.mv[r + 2][c + 2];
+                const int my = median9(a0.x, a1.x, a2.x, a3.x, a4.x, a5.x, a6.x, a7.x, a8.x);
+                const int mx = median9(a0.y, a1.y, a2.y, a3.y, a4.y, a5.y, a6.y, a7.y, a8.y);
+                sm.md[r][c] = make_char2((signed char)my, (signed char)mx);
+            }
+            __syncthreads();
+        }
+        // decide every pixel; list the ones that need a reverse check
+        uint8_t dec[PPT];
+        int qv[PPT];
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const int pi = tid + i * NT, py = pi / TP, px = pi - py * TP;
+            const int y = y0 + py, x = x0 + px;
+            dec[i] = 255;
+            qv[i] = -1;
+            if (y >= H || x >= W) continue;
+            int fy, fx;
+            bool pass = true;
+            if (use_nnc) {
+                const char2 c = sm.md[py + 1][px + 1];
+                fy = c.x;
+                fx = c.y;
+                const int nb[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int yy = y + nb[j][0], xx = x + nb[j][1];
+                    if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)W) continue;
+                    const char2 u = sm.md[py + 1 + nb[j][0]][px + 1 + nb[j][1]];
+                    if (iabs(fy - u.x) + iabs(fx - u.y) > 1) pass = false;
+                }
+            } else {
+                const char2 c = sm.mv[py + 2][px + 2];
+                fy = c.x;
+                fx = c.y;
+            }
+            const size_t gi = (size_t)y * W + x;
+            reinterpret_cast<char2 *>(t.fmv[k])[gi] = make_char2((signed char)fy, (signed char)fx);
+            const int qy = y + fy, qx = x + fx;
+            const uint32_t mword = sm.cm[0][py + HC][(px + HC) >> 2];
+            const bool measured = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
+            if (measured) {
+                dec[i] = 0;
+            } else if ((unsigned)qy >= (unsigned)H || (unsigned)qx >= (unsigned)W ||
+                       !t.ref_msk[k][(size_t)qy * W + qx]) {
+                dec[i] = 1;
+            } else if (use_nnc && !pass) {
+                dec[i] = 2;
+            } else {
+                qv[i] = qy * W + qx;
+                if (rme) {
+                    const char2 w = reinterpret_cast<const char2 *>(t.rmv[k])[(size_t)qy * W + qx];
+                    dec[i] = (w.x == -fy && w.y == -fx) ? 4 : 3;
+                } else if (frmc || rmc) {
+                    dec[i] = 254;                               // pending reverse check
+                    sm.rej[pi] = 0;
+                    sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)pi;
+                } else {
+                    dec[i] = 4;
+                }
+            }
+        }
+        __syncthreads();
+        // reverse checks: one warp per listed pixel
+        const int nl = sm.nlist;
+        const int side = frmc ? 7 : 2 * t.Rc + 1;
+        const int ncand = side * side, centre = ncand / 2;
+        for (int li = warp; li < nl; li += NW) {
+            const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
+            const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
+            const int fy = c.x, fx = c.y;
+            uint32_t P[T][3];                          // past-frame patch around q
+            {
+                const int ry = py + HC + fy - h, rx = px + HC + fx - h;
+                const uint32_t *base = &sm.rf[rx & 3][ry][rx >> 2];
+#pragma unroll
+                for (int r = 0; r < T; ++r) {
+                    P[r][0] = base[r * RWD];
+                    P[r][1] = base[r * RWD + 1];
+                    P[r][2] = base[r * RWD + 2];
+                }
+            }
+            int s0 = 0, n0 = 0;
+            bool rej = false;
+            // candidate order starts at d = 0 (lane 0 of the first round)
+            for (int c0 = 0; c0 < ncand; c0 += 32) {
+                const int ci = c0 + lane;
+                int s = 0, n = 0;
+                bool valid = false;
+                if (ci < ncand) {
+                    const int cc = ci + centre < ncand ? ci + centre : ci + centre - ncand;
+                    const int dy = frmc ? frmc_offset(cc / 7) : cc / side - t.Rc;
+                    const int dx = frmc ? frmc_offset(cc % 7) : cc % side - t.Rc;
+                    const int sy = y0 + py + dy, sx = x0 + px + dx;
+                    if ((unsigned)sy < (unsigned)H && (unsigned)sx < (unsigned)W) {
+                        s = sad_against<T>(sm, py + dy + HC - h, px + dx + HC - h, P);
+                        n = sm.nsrc[py + dy + kMaxRadius][px + dx + kMaxRadius];
+                        valid = true;
+                    }
+                }
+                if (c0 == 0) {
+                    s0 = __shfl_sync(0xffffffffu, s, 0);
+                    n0 = __shfl_sync(0xffffffffu, n, 0);
+                    if (lane == 0) valid = false;
+                }
+                const bool better = valid && s * n0 < s0 * n;
+                if (__any_sync(0xffffffffu, better)) {
+                    rej = true;
+                    break;
+                }
+            }
+            if (lane == 0) sm.rej[pi] = rej ? 1 : 0;
+        }
+        __syncthreads();
+        const uint8_t *rs = t.ref_smp[k];
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            if (dec[i] == 255) continue;
+            const int pi = tid + i * NT, py = pi / TP, px = pi - py * TP;
+            uint8_t d = dec[i];
+            if (d == 254) d = sm.rej[pi] ? 3 : 4;
+            t.dec[k][(size_t)(y0 + py) * W + x0 + px] = d;
+            if (d == 4) {
+                sum[i] += rs[qv[i]];
+                cnt[i] += 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        const int pi = tid + i * NT, py = pi / TP, px = pi - py * TP;
+        const int y = y0 + py, x = x0 + px;
+        if (y >= H || x >= W) continue;
+        t.psum[(size_t)y * W + x] = (uint16_t)sum[i];
+        t.pcnt[(size_t)y * W + x] = (uint8_t)cnt[i];
+    }
+}
+
+// template cost at a single source (RME reverse field): SAD over measured current pixels
 __device__ void cost_at(const FrameTask &t, const uint8_t *__restrict__ ref, int sy, int sx,
                         int vy, int vx, int &sad, int &n)
 {
@@ -55,143 +364,12 @@ __device__ void cost_at(const FrameTask &t, const uint8_t *__restrict__ ref, int
     n = c;
 }
 
-// a = (sa, na) strictly lower mean cost than b = (sb, nb)
-__device__ __forceinline__ bool lower(int sa, int na, int sb, int nb)
-{
-    return (long long)sa * nb < (long long)sb * na;
-}
-
 __device__ __forceinline__ bool tie_before(int ay, int ax, int by, int bx)
 {
     const int la = iabs(ay) + iabs(ax), lb = iabs(by) + iabs(bx);
     if (la != lb) return la < lb;
     if (ay != by) return ay < by;
     return ax < bx;
-}
-
-// RMC / FRMC: accept iff no tested reverse vector has a strictly lower cost than d = 0
-__device__ bool reverse_check(const FrameTask &t, const uint8_t *__restrict__ ref, int py, int px,
-                              int vy, int vx, bool fast)
-{
-    const int fset[7] = {-7, -3, -1, 0, 1, 3, 7};
-    int s0, n0;
-    cost_at(t, ref, py, px, vy, vx, s0, n0);
-    const int nset = fast ? 7 : 2 * t.Rc + 1;
-    for (int i = 0; i < nset; ++i) {
-        const int dy = fast ? fset[i] : i - t.Rc;
-        const int sy = py + dy;
-        if ((unsigned)sy >= (unsigned)t.H) continue;
-        for (int j = 0; j < nset; ++j) {
-            const int dx = fast ? fset[j] : j - t.Rc;
-            if (dy == 0 && dx == 0) continue;
-            const int sx = px + dx;
-            if ((unsigned)sx >= (unsigned)t.W) continue;
-            int s, n;
-            cost_at(t, ref, sy, sx, vy - dy, vx - dx, s, n);
-            if (lower(s, n, s0, n0)) return false;
-        }
-    }
-    return true;
-}
-
-// median of nine values: sort each group of three, then the median of (largest minimum,
-// median of medians, smallest maximum) -- exact for any input, ties included.
-__device__ __forceinline__ void cswap(int &a, int &b)
-{
-    const int lo = min(a, b), hi = max(a, b);
-    a = lo;
-    b = hi;
-}
-
-__device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
-
-__device__ int median9(int p0, int p1, int p2, int p3, int p4, int p5, int p6, int p7, int p8)
-{
-    cswap(p0, p1); cswap(p1, p2); cswap(p0, p1);
-    cswap(p3, p4); cswap(p4, p5); cswap(p3, p4);
-    cswap(p6, p7); cswap(p7, p8); cswap(p6, p7);
-    const int lo = max(max(p0, p3), p6);
-    const int hi = min(min(p2, p5), p8);
-    return med3(lo, med3(p1, p4, p7), hi);
-}
-
-__device__ __forceinline__ char2 load_mv(const char2 *mv, int H, int W, int y, int x)
-{
-    y = min(max(y, 0), H - 1);
-    x = min(max(x, 0), W - 1);
-    return mv[(size_t)y * W + x];
-}
-
-__device__ void median_vec(const char2 *mv, int H, int W, int y, int x, int &my, int &mx)
-{
-    char2 a[9];
-    int c = 0;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) a[c++] = load_mv(mv, H, W, y + dy, x + dx);
-    my = median9(a[0].x, a[1].x, a[2].x, a[3].x, a[4].x, a[5].x, a[6].x, a[7].x, a[8].x);
-    mx = median9(a[0].y, a[1].y, a[2].y, a[3].y, a[4].y, a[5].y, a[6].y, a[7].y, a[8].y);
-}
-
-__global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
-{
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
-    if (x >= t.W || y >= t.H || *t.status) return;
-    const int H = t.H, W = t.W;
-    const size_t i = (size_t)y * W + x;
-    const bool use_nnc = t.cc_mode == 4 || t.cc_mode == 5;
-    const bool measured = t.cur_msk[i] != 0;
-    int sum = 0, cnt = 0;
-    for (int k = 0; k < t.K; ++k) {
-        const char2 *mv = reinterpret_cast<const char2 *>(t.mv[k]);
-        int fy, fx;
-        bool pass = true;
-        if (use_nnc) {
-            median_vec(mv, H, W, y, x, fy, fx);
-            const int nb[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int yy = y + nb[j][0], xx = x + nb[j][1];
-                if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)W) continue;
-                int ny, nx;
-                median_vec(mv, H, W, yy, xx, ny, nx);
-                if (iabs(fy - ny) + iabs(fx - nx) > 1) pass = false;
-            }
-        } else {
-            const char2 v = mv[i];
-            fy = v.x;
-            fx = v.y;
-        }
-        reinterpret_cast<char2 *>(t.fmv[k])[i] = make_char2((signed char)fy, (signed char)fx);
-        const int qy = y + fy, qx = x + fx;
-        uint8_t d;
-        if (measured) {
-            d = 0;                                               // MEASURED
-        } else if ((unsigned)qy >= (unsigned)H || (unsigned)qx >= (unsigned)W ||
-                   !t.ref_msk[k][(size_t)qy * W + qx]) {
-            d = 1;                                               // NOT_PROJECTABLE
-        } else if (use_nnc && !pass) {
-            d = 2;                                               // NNC_REJECT
-        } else {
-            bool ok = true;
-            if (t.cc_mode == 3 || t.cc_mode == 5) ok = reverse_check(t, t.ref_rec[k], y, x, fy, fx, true);
-            else if (t.cc_mode == 2) ok = reverse_check(t, t.ref_rec[k], y, x, fy, fx, false);
-            else if (t.cc_mode == 1) {
-                const char2 w = reinterpret_cast<const char2 *>(t.rmv[k])[(size_t)qy * W + qx];
-                ok = (w.x == -fy) && (w.y == -fx);
-            }
-            d = ok ? 4 : 3;                                      // ACCEPT / CHECK_REJECT
-        }
-        t.dec[k][i] = d;
-        if (d == 4) {
-            sum += t.ref_smp[k][(size_t)qy * W + qx];
-            cnt += 1;
-        }
-    }
-    t.psum[i] = (uint16_t)sum;
-    t.pcnt[i] = (uint8_t)cnt;
 }
 
 // RME (Sec. 2.2): reverse motion vector at every past-frame pixel q: argmin over w in [-R, R]^2
@@ -219,17 +397,42 @@ __global__ void __launch_bounds__(NT) rme_field_kernel(FrameTask t)
             }
         }
     }
-    reinterpret_cast<char2 *>(t.rmv[k])[(size_t)qy * t.W + qx] = make_char2((signed char)by, (signed char)bx);
+    reinterpret_cast<char2 *>(t.rmv[k])[(size_t)qy * t.W + qx] =
+        make_char2((signed char)by, (signed char)bx);
+}
+
+template <int T>
+cudaError_t launch_cc_t(const FrameTask &t, cudaStream_t st)
+{
+    static bool attr = false;
+    const size_t smem = sizeof(Smem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cc_project_kernel<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((t.W + TP - 1) / TP, (t.H + TP - 1) / TP);
+    cc_project_kernel<T><<<grid, NT, smem, st>>>(t);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st)
 {
-    dim3 grid((t.W + 31) / 32, (t.H + NT / 32 - 1) / (NT / 32));
-    cc_project_kernel<<<grid, NT, 0, st>>>(t);
+    cudaError_t e;
+    switch (t.T) {
+    case 1: e = launch_cc_t<1>(t, st); break;
+    case 3: e = launch_cc_t<3>(t, st); break;
+    case 5: e = launch_cc_t<5>(t, st); break;
+    case 7: e = launch_cc_t<7>(t, st); break;
+    case 9: e = launch_cc_t<9>(t, st); break;
+    case 11: e = launch_cc_t<11>(t, st); break;
+    default: return cudaErrorInvalidValue;
+    }
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st)
