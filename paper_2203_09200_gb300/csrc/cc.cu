@@ -46,11 +46,13 @@ constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
+constexpr int CPY = RS * RWD + 8;             // words per shifted copy; the pad puts the four
+                                              // copies of a word in different banks
 
 struct Smem {
-    uint32_t cs[4][RS][RWD];      // masked samples, byte-shifted copies
-    uint32_t cm[4][RS][RWD];      // byte masks, byte-shifted copies
-    uint32_t rf[4][RS][RWD];      // past frame (clamped coordinates), byte-shifted copies
+    uint32_t cs[4 * CPY];         // masked samples, byte-shifted copies
+    uint32_t cm[4 * CPY];         // byte masks, byte-shifted copies
+    uint32_t rf[4 * CPY];         // past frame (clamped coordinates), byte-shifted copies
     uint8_t nsrc[NS][NS];         // measured pixels in the template around each source
     char2 mv[MT][MT];
     char2 md[MD][MD];
@@ -93,8 +95,7 @@ __device__ __forceinline__ int frmc_offset(int i)
 // of a row holds region bytes 4w+j .. 4w+j+3.  MODE 0: masked samples and 1: byte mask (both 0
 // outside the frame); MODE 2: past frame with clamped coordinates.
 template <int MODE>
-__device__ void stage(uint32_t (&dst)[4][RS][RWD], const uint8_t *__restrict__ src, int H, int W,
-                      int y0, int x0)
+__device__ void stage(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
 {
     for (int i = threadIdx.x; i < RS * RWD; i += NT) {
         const int r = i / RWD, w = i - r * RWD;
@@ -114,14 +115,14 @@ __device__ void stage(uint32_t (&dst)[4][RS][RWD], const uint8_t *__restrict__ s
                     v |= (uint32_t)(*reinterpret_cast<const uint16_t *>(row + x)) << (8 * b);
             }
         }
-        dst[0][r][w] = v;
+        dst[r * RWD + w] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * RS * (RWD - 1); i += NT) {
         const int j = 1 + i / (RS * (RWD - 1));
         const int rem = i - (j - 1) * RS * (RWD - 1);
         const int r = rem / (RWD - 1), w = rem - r * (RWD - 1);
-        dst[j][r][w] = __funnelshift_r(dst[0][r][w], dst[0][r][w + 1], 8 * j);
+        dst[j * CPY + r * RWD + w] = __funnelshift_r(dst[r * RWD + w], dst[r * RWD + w + 1], 8 * j);
     }
 }
 
@@ -137,8 +138,8 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     int acc = 0;
 #pragma unroll
     for (int r = 0; r < T; ++r) {
-        const uint32_t *cs = sm.cs[j][sy + r] + w;
-        const uint32_t *cm = sm.cm[j][sy + r] + w;
+        const uint32_t *cs = sm.cs + j * CPY + (sy + r) * RWD + w;
+        const uint32_t *cm = sm.cm + j * CPY + (sy + r) * RWD + w;
         acc += __vsadu4(cs[0] & w0, P[r][0] & cm[0] & w0);
         if (w1) acc += __vsadu4(cs[1] & w1, P[r][1] & cm[1] & w1);
         if (w2) acc += __vsadu4(cs[2] & w2, P[r][2] & cm[2] & w2);
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
         const int ry = sy + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
         int n = 0;
         for (int r = 0; r < T; ++r) {
-            const uint32_t *cm = sm.cm[rx & 3][ry + r] + (rx >> 2);
+            const uint32_t *cm = sm.cm + (rx & 3) * CPY + (ry + r) * RWD + (rx >> 2);
 #pragma unroll
             for (int b = 0; b < (T + 3) / 4; ++b) {
                 uint32_t m = cm[b];
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
             const size_t gi = (size_t)y * W + x;
             reinterpret_cast<char2 *>(t.fmv[k])[gi] = make_char2((signed char)fy, (signed char)fx);
             const int qy = y + fy, qx = x + fx;
-            const uint32_t mword = sm.cm[0][py + HC][(px + HC) >> 2];
+            const uint32_t mword = sm.cm[(py + HC) * RWD + ((px + HC) >> 2)];
             const bool measured = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
             if (measured) {
                 dec[i] = 0;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
             uint32_t P[T][3];                          // past-frame patch around q
             {
                 const int ry = py + HC + fy - h, rx = px + HC + fx - h;
-                const uint32_t *base = &sm.rf[rx & 3][ry][rx >> 2];
+                const uint32_t *base = sm.rf + (rx & 3) * CPY + ry * RWD + (rx >> 2);
 #pragma unroll
                 for (int r = 0; r < T; ++r) {
                     P[r][0] = base[r * RWD];

@@ -14,11 +14,22 @@
 //   pixels, measured pixels overwritten by their samples (and, for R-FSR, projected pixels by
 //   their projected value).
 //
-// GB300 design: one warp per block.  R is Hermitian (the signal is real), so only the half
-// spectrum l = 0..16 is kept: lane k holds R(k, 0..16) in registers.  The full weight spectrum W
-// (needed at arbitrary shifts k -+ u) lives in shared memory with a padded row stride so that the
-// 32 lanes' row-shifted reads are conflict-free.  The 2-D DFTs are row / column passes with a
-// host-computed twiddle table (no device transcendental functions).  FP32 throughout.
+// GB300 design: one warp per block, FP32.
+//   * DFTs by FFT: each lane transforms one support row (32 real values as a 16-point complex
+//     radix-2 FFT plus the real-input split), then one column of the half spectrum (32-point
+//     complex radix-2 FFT, in place in shared memory); twiddles come from a host-computed table
+//     in constant memory at compile-time indices.
+//   * R is Hermitian (the signal is real), so only l = 0..16 is kept: lane k holds R(k, 0..16)
+//     in registers, with its frequency weights (0 for the non-canonical member of a pair) and tie
+//     keys.  The full weight spectrum W (read at shifts k -+ u) lives in shared memory with a
+//     padded row stride, so the 32 lanes' row-shifted reads are conflict-free.
+//   * Selection: per-lane maximum, warp maximum by __reduce_max_sync on the (non-negative) float
+//     bits, then the lowest tie key among the bins that reach it by __reduce_min_sync; the winning
+//     R value comes from its owner lane by one shuffle pair.
+//   * The per-warp shared memory is one 8.7 KB union (support, row spectra, W) so more warps fit.
+#include <cmath>
+#include <type_traits>
+
 #include "rfsr_internal.h"
 
 namespace rfsr {
@@ -28,12 +39,22 @@ namespace {
 constexpr int N = kFsrN;
 constexpr int NH = kFsrHalf;
 constexpr int WPB = 4;                     // warps (blocks) per CTA
-constexpr int WSTRIDE = N + 1;             // padded row stride of W (float2)
+constexpr int WS = N + 1;                  // padded row stride of W (float2)
+constexpr int SS = N + 1;                  // padded row stride of the support (float)
 
-struct WarpSmem {
-    float2 Wf[N * WSTRIDE];   // full weight spectrum; first holds the support (w, w*f)
-    float2 rw[N * NH];        // row DFTs of the weights
-    float2 rr[N * NH];        // row DFTs of the weighted values
+__constant__ float c_cs[N];                // cos(2 pi j / 32)
+__constant__ float c_sn[N];                // sin(2 pi j / 32)
+
+union WarpSmem {
+    struct {
+        float w[N * SS];                   // support weights
+        float f[N * SS];                   // weighted values
+    } sup;
+    struct {
+        float2 w[N * NH];                  // row spectra of the weights, then column pass in place
+        float2 f[N * NH];                  // row spectra of the weighted values
+    } dft;
+    float2 W[N * WS];                      // full weight spectrum
 };
 
 struct Smem {
@@ -44,7 +65,105 @@ struct Smem {
     WarpSmem w[WPB];
 };
 
-__global__ void __launch_bounds__(WPB * 32) fsr_kernel(FrameTask t)
+__host__ __device__ constexpr int bitrev(int x, int bits)
+{
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E), so that every register
+// array index below is a constant expression
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// in-place radix-2 decimation-in-time FFT (forward, exp(-2 pi i k n / M)) of M points given in
+// bit-reversed order; twiddle W_M^j = cos(2 pi j/M) - i sin(2 pi j/M) = table index j * 32 / M
+template <int M, int LEN = 2>
+__device__ __forceinline__ void fft_dit(float (&re)[M], float (&im)[M])
+{
+    if constexpr (LEN <= M) {
+        static_for<0, M / 2>([&](auto q) {
+            constexpr int Q = decltype(q)::value;
+            constexpr int i = (Q / (LEN / 2)) * LEN, j = Q % (LEN / 2);
+            constexpr int a = i + j, b = i + j + LEN / 2;
+            constexpr int tw = j * (N / LEN);
+            float xr, xi;
+            if constexpr (tw == 0) {
+                xr = re[b];
+                xi = im[b];
+            } else if constexpr (tw == N / 4) {         // -i
+                xr = im[b];
+                xi = -re[b];
+            } else {
+                const float wr = c_cs[tw], wi = -c_sn[tw];
+                xr = re[b] * wr - im[b] * wi;
+                xi = re[b] * wi + im[b] * wr;
+            }
+            re[b] = re[a] - xr;
+            im[b] = im[a] - xi;
+            re[a] += xr;
+            im[a] += xi;
+        });
+        fft_dit<M, 2 * LEN>(re, im);
+    }
+}
+
+// DFT of one 32-point real row x (natural order) -> X[0..16], via a 16-point complex FFT of
+// z[n] = x[2n] + i x[2n+1] and X[l] = E[l] + W_32^l O[l] with E, O the even / odd spectra
+__device__ __forceinline__ void real_row_dft(const float (&x)[N], float2 *out)
+{
+    float zr[16], zi[16];
+    static_for<0, 16>([&](auto nn) {
+        constexpr int n = decltype(nn)::value;
+        zr[bitrev(n, 4)] = x[2 * n];
+        zi[bitrev(n, 4)] = x[2 * n + 1];
+    });
+    fft_dit<16>(zr, zi);
+    static_for<0, 17>([&](auto ll) {
+        constexpr int l = decltype(ll)::value;
+        constexpr int a = l & 15, b = (16 - l) & 15;
+        const float ar = zr[a], ai = zi[a], br = zr[b], bi = -zi[b];   // Z[l], conj(Z[16-l])
+        const float er = 0.5f * (ar + br), ei = 0.5f * (ai + bi);       // E = (Z + conj Z') / 2
+        const float orr = 0.5f * (ai - bi), oi = -0.5f * (ar - br);     // O = (Z - conj Z') / 2i
+        float tr, ti;
+        if constexpr (l == 0 || l == 16) {                              // W = +1 / -1
+            tr = l == 0 ? orr : -orr;
+            ti = l == 0 ? oi : -oi;
+        } else if constexpr (l == 8) {                                  // W = -i
+            tr = oi;
+            ti = -orr;
+        } else {
+            const float wr = c_cs[l], wi = -c_sn[l];
+            tr = orr * wr - oi * wi;
+            ti = orr * wi + oi * wr;
+        }
+        out[l] = make_float2(er + tr, ei + ti);
+    });
+}
+
+// 32-point complex DFT of column c of a [32][17] array, in place
+__device__ __forceinline__ void column_dft(float2 *a, int c)
+{
+    float re[N], im[N];
+    static_for<0, N>([&](auto mm) {
+        constexpr int m = decltype(mm)::value;
+        const float2 v = a[m * NH + c];
+        re[bitrev(m, 5)] = v.x;
+        im[bitrev(m, 5)] = v.y;
+    });
+    fft_dit<N>(re, im);
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
+}
+
+__global__ void __launch_bounds__(WPB * 32, 5) fsr_kernel(FrameTask t)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -67,8 +186,6 @@ __global__ void __launch_bounds__(WPB * 32) fsr_kernel(FrameTask t)
     const int o = (N - kFsrB) / 2;
     const int ys = kFsrB * bi - o, xs = kFsrB * bj - o;
     WarpSmem &ws = sm.w[warp];
-    float *sw = reinterpret_cast<float *>(ws.Wf);           // support weights  [N][WSTRIDE]
-    float *sf = sw + N * WSTRIDE;                           // weighted values [N][WSTRIDE]
     const float mu = t.fsr_proj_weight;
 
     // 1. support: lane = column, coalesced row loads
@@ -85,111 +202,112 @@ __global__ void __launch_bounds__(WPB * 32) fsr_kernel(FrameTask t)
                 val = (float)t.psum[i] / (255.0f * (float)t.pcnt[i]);
             }
         }
-        sw[m * WSTRIDE + lane] = wt;
-        sf[m * WSTRIDE + lane] = wt * val;
+        ws.sup.w[m * SS + lane] = wt;
+        ws.sup.f[m * SS + lane] = wt * val;
     }
     __syncwarp();
 
-    // 2. row DFTs (lane = row m): X(m, l) = sum_n a(m, n) exp(-2 pi i l n / N), l = 0..16
+    // 2. row DFTs: lane = support row
     {
-        const int m = lane;
-        for (int l = 0; l < NH; ++l) {
-            float wr = 0.f, wi = 0.f, fr = 0.f, fi = 0.f;
-#pragma unroll 8
-            for (int n = 0; n < N; ++n) {
-                const int j = (l * n) & (N - 1);
-                const float c = sm.cs[j], s = sm.sn[j];
-                const float a = sw[m * WSTRIDE + n], f = sf[m * WSTRIDE + n];
-                wr = fmaf(a, c, wr);
-                wi = fmaf(-a, s, wi);
-                fr = fmaf(f, c, fr);
-                fi = fmaf(-f, s, fi);
-            }
-            ws.rw[m * NH + l] = make_float2(wr, wi);
-            ws.rr[m * NH + l] = make_float2(fr, fi);
+        float xw[N], xf[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            xw[n] = ws.sup.w[lane * SS + n];
+            xf[n] = ws.sup.f[lane * SS + n];
         }
+        __syncwarp();                                  // the union is rewritten below
+        real_row_dft(xw, &ws.dft.w[lane * NH]);
+        real_row_dft(xf, &ws.dft.f[lane * NH]);
     }
     __syncwarp();
 
-    // 3. column DFTs (lane = output row k); R stays in registers, W goes to shared memory
-    float Rre[NH], Rim[NH];
+    // 3. column DFTs in place: 34 columns over 32 lanes (17 of W, then 17 of R)
+    column_dft(lane < NH ? ws.dft.w : ws.dft.f, lane < NH ? lane : lane - NH);
+    if (lane < 2) column_dft(ws.dft.f, N - NH + lane);
+    __syncwarp();
+
+    // 4. lane k takes R(k, 0..16) into registers; W goes to the full padded layout
     const int k = lane;
+    float Rre[NH], Rim[NH];
+    {
+        float2 Wt[NH];
 #pragma unroll
-    for (int l = 0; l < NH; ++l) {
-        float wr = 0.f, wi = 0.f, fr = 0.f, fi = 0.f;
-        for (int m = 0; m < N; ++m) {
-            const int j = (k * m) & (N - 1);
-            const float c = sm.cs[j], s = -sm.sn[j];        // exp(-i a) = c + i s
-            const float2 a = ws.rw[m * NH + l], f = ws.rr[m * NH + l];
-            wr = fmaf(a.x, c, fmaf(-a.y, s, wr));
-            wi = fmaf(a.x, s, fmaf(a.y, c, wi));
-            fr = fmaf(f.x, c, fmaf(-f.y, s, fr));
-            fi = fmaf(f.x, s, fmaf(f.y, c, fi));
+        for (int l = 0; l < NH; ++l) {
+            const float2 r = ws.dft.f[k * NH + l];
+            Rre[l] = r.x;
+            Rim[l] = r.y;
+            Wt[l] = ws.dft.w[k * NH + l];
         }
-        ws.Wf[k * WSTRIDE + l] = make_float2(wr, wi);
-        Rre[l] = fr;
-        Rim[l] = fi;
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l < NH; ++l) ws.W[k * WS + l] = Wt[l];
     }
     __syncwarp();
     // W(k, l) for l = 17..31 from Hermitian symmetry: W(k, l) = conj(W(-k, -l))
+#pragma unroll
     for (int l = NH; l < N; ++l) {
-        const float2 a = ws.Wf[((N - k) & (N - 1)) * WSTRIDE + (N - l)];
-        ws.Wf[k * WSTRIDE + l] = make_float2(a.x, -a.y);
+        const float2 a = ws.W[((N - k) & (N - 1)) * WS + (N - l)];
+        ws.W[k * WS + l] = make_float2(a.x, -a.y);
     }
     __syncwarp();
-    const float W0 = ws.Wf[0].x;
+    const float W0 = ws.W[0].x;
 
-    // block pixel owned by lanes 0..15
-    const int pm = (lane >> 2) & 3, pn = lane & 3;
+    // frequency weights (0 for the non-canonical member of a pair) and tie keys of this row:
+    // key = lower linear index of the pair, packed with the column (key << 5 | l)
+    float wfr[NH];
+    int keyl[NH];
+#pragma unroll
+    for (int l = 0; l < NH; ++l) {
+        const bool canon = (l != 0 && l != NH - 1) || k <= N / 2;
+        wfr[l] = canon ? sm.wf[k * NH + l] : 0.f;
+        const int lin = k * N + l, clin = ((N - k) & (N - 1)) * N + ((N - l) & (N - 1));
+        keyl[l] = (min(lin, clin) << 5) | l;
+    }
+
+    const int pm = (lane >> 2) & 3, pn = lane & 3;     // block pixel of lanes 0..15
     float g = 0.f;
-
-    // 4. iterations
     const float gamma = t.fsr_gamma;
     for (int it = 0; it < t.fsr_iters && W0 > 0.f; ++it) {
-        float be = -1.f, bre = 0.f, bim = 0.f;
-        int bkey = 0x7fffffff, bu = 0;
+        float m = 0.f;
+#pragma unroll
+        for (int l = 0; l < NH; ++l) m = fmaxf(m, wfr[l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]));
+        m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+        if (!(m > 0.f)) break;                          // residual exhausted
+        int best = 0x7fffffff;
+        float sr = 0.f, si = 0.f;
 #pragma unroll
         for (int l = 0; l < NH; ++l) {
-            const bool canon = (l != 0 && l != NH - 1) || k <= N / 2;
-            const float e = sm.wf[k * NH + l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]);
-            const int lin = k * N + l;
-            const int clin = ((N - k) & (N - 1)) * N + ((N - l) & (N - 1));
-            const int key = min(lin, clin);
-            if (canon && (e > be || (e == be && key < bkey))) {
-                be = e; bkey = key; bu = lin; bre = Rre[l]; bim = Rim[l];
-            }
+            const float e = wfr[l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]);
+            const bool take = (e == m) && (keyl[l] < best);
+            best = take ? keyl[l] : best;
+            sr = take ? Rre[l] : sr;
+            si = take ? Rim[l] : si;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float oe = __shfl_xor_sync(0xffffffffu, be, off);
-            const int ok = __shfl_xor_sync(0xffffffffu, bkey, off);
-            const int ou = __shfl_xor_sync(0xffffffffu, bu, off);
-            if (oe > be || (oe == be && ok < bkey)) {
-                be = oe; bkey = ok; bu = ou;
-            }
+        const int win = __reduce_min_sync(0xffffffffu, best);
+        // the stored representative of the winning pair and its owner lane
+        int uk = (win >> 5) >> 5, ul = (win >> 5) & (N - 1);
+        if (ul > N / 2) {
+            uk = (N - uk) & (N - 1);
+            ul = N - ul;
         }
-        const int src = bu >> 5;
-        const float ure = __shfl_sync(0xffffffffu, bre, src);
-        const float uim = __shfl_sync(0xffffffffu, bim, src);
-        if (!(be > 0.f)) break;                              // residual exhausted
-        const int uk = bu >> 5, ul = bu & (N - 1);
+        const float ure = __shfl_sync(0xffffffffu, sr, uk);
+        const float uim = __shfl_sync(0xffffffffu, si, uk);
         const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
         const float dr = gamma * ure / W0;
         const float di = self ? 0.f : gamma * uim / W0;
-        // residual update over the half spectrum held by this lane
-        const int ra = ((k - uk) & (N - 1)) * WSTRIDE, rb = ((k + uk) & (N - 1)) * WSTRIDE;
+        const int ra = ((k - uk) & (N - 1)) * WS, rb = ((k + uk) & (N - 1)) * WS;
         if (self) {
 #pragma unroll
             for (int l = 0; l < NH; ++l) {
-                const float2 a = ws.Wf[ra + ((l - ul) & (N - 1))];
+                const float2 a = ws.W[ra + ((l - ul) & (N - 1))];
                 Rre[l] = fmaf(-dr, a.x, Rre[l]);
                 Rim[l] = fmaf(-dr, a.y, Rim[l]);
             }
         } else {
 #pragma unroll
             for (int l = 0; l < NH; ++l) {
-                const float2 a = ws.Wf[ra + ((l - ul) & (N - 1))];
-                const float2 c = ws.Wf[rb + ((l + ul) & (N - 1))];
+                const float2 a = ws.W[ra + ((l - ul) & (N - 1))];
+                const float2 c = ws.W[rb + ((l + ul) & (N - 1))];
                 // dc * a + conj(dc) * c
                 const float xr = dr * (a.x + c.x) + di * (c.y - a.y);
                 const float xi = dr * (a.y + c.y) + di * (a.x - c.x);
@@ -228,18 +346,38 @@ __global__ void __launch_bounds__(WPB * 32) fsr_kernel(FrameTask t)
 
 }  // namespace
 
+namespace {
+int g_ready[64];   // per device: constant twiddles and the shared-memory attribute are set
+}
+
+cudaError_t init_fsr(int dev)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (g_ready[dev]) return cudaSuccess;
+    // DFT twiddles computed on the host (no device transcendental functions)
+    float cs[N], sn[N];
+    for (int j = 0; j < N; ++j) {
+        cs[j] = (float)std::cos(2.0 * M_PI * j / N);
+        sn[j] = (float)std::sin(2.0 * M_PI * j / N);
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_cs, cs, sizeof(cs));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sn, sn, sizeof(sn));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fsr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Smem));
+    if (e == cudaSuccess) g_ready[dev] = 1;
+    return e;
+}
+
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
 {
-    static bool attr_set = false;
-    const size_t smem = sizeof(Smem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fsr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = init_fsr(dev);
+    if (e != cudaSuccess) return e;
     const int nb = ((t.W + kFsrB - 1) / kFsrB) * ((t.H + kFsrB - 1) / kFsrB);
-    fsr_kernel<<<(nb + WPB - 1) / WPB, WPB * 32, smem, st>>>(t);
+    fsr_kernel<<<(nb + WPB - 1) / WPB, WPB * 32, sizeof(Smem), st>>>(t);
     count_launch();
     return cudaGetLastError();
 }

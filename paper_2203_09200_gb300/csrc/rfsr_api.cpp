@@ -238,6 +238,14 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
         }
         e->own_stream = true;
     }
+    {
+        cudaError_t ie = init_fsr(cfg->device);
+        if (ie != cudaSuccess) {
+            if (e->own_stream) cudaStreamDestroy(e->stream);
+            delete e;
+            return cuda_fail(ie, "FSR set-up");
+        }
+    }
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     e->budget = cfg->memory_budget ? cfg->memory_budget : (size_t)(0.8 * (double)fr);

@@ -74,6 +74,8 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st);
+// one-time per-device set-up of the FSR kernel (constant twiddles, shared-memory limit)
+cudaError_t init_fsr(int device);
 
 // set the calling thread's rfsr_last_error() message; returns code
 int set_error(int code, const std::string &msg);
