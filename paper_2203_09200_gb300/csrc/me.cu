@@ -147,13 +147,185 @@ __global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// T = 9: warp-strip kernel with byte SIMD.  Lane l of a warp owns four adjacent columns (one
+// 32-bit word of bytes) of a 128-column strip, the warp owns 8 output rows, the CTA 8 warps.
+// For each candidate the lane walks the 16 rows of D_v its outputs need: one byte permute to
+// align the past-frame word, __vabsdiffu4, AND with the mask, and running vertical sums kept as
+// two packed 16-bit words (columns 0,2 and 1,3).  The 9-column horizontal sums take the left and
+// right lanes' vertical sums (four shuffles) and a few packed adds.  The running argmin is packed
+// too: two outputs per word, a guard-bit compare (cost + 0x7fff - new has its lane MSB set iff
+// new < cost), a sign-replicating prmt into a lane mask and two bit selects.  Candidates
+// run in tie order with strict improvement, so the first minimum in tie order wins.  Lanes 0 and
+// 31 only feed their neighbours: a strip yields 120 output columns.
+// ---------------------------------------------------------------------------------------------
+constexpr int S_ROWS = 8;                  // output rows per warp
+constexpr int S_WARPS = 8;
+constexpr int S_NT = 32 * S_WARPS;
+constexpr int S_OUTW = 120;                // output columns per CTA
+constexpr int S_OUTH = S_ROWS * S_WARPS;   // output rows per CTA
+constexpr int S_DROWS = S_ROWS + 8;        // D rows per warp (T = 9)
+constexpr int S_RROWS = S_OUTH + 8 + 2 * kMaxRadius;            // past-frame rows staged
+constexpr int S_RWORDS = (128 + 2 * kMaxRadius + 3) / 4 + 1;   // words per staged row
+
+// lane masks from the guard bits of a packed pair: 0xffff in each 16-bit lane whose bit 15 (lo)
+// or bit 31 (hi) is set (prmt's default mode replicates the sign bit when a selector's msb is set)
+__device__ __forceinline__ uint32_t lane_mask(uint32_t t)
+{
+    uint32_t m;
+    asm("prmt.b32 %0, %1, 0, 0xbb99;" : "=r"(m) : "r"(t));
+    return m;
+}
+
+struct Smem9 {
+    uint32_t rf[S_RROWS * S_RWORDS];
+    short2 vord[NVMAX];
+};
+
+__global__ void __launch_bounds__(S_NT, 2) me9_kernel(FrameTask t)
+{
+    __shared__ Smem9 sm;
+    const int k = blockIdx.z;
+    const int x0 = blockIdx.x * S_OUTW, y0 = blockIdx.y * S_OUTH;
+    const int H = t.H, W = t.W, R = t.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (*t.status) return;
+    const uint8_t *__restrict__ ref = t.ref_rec[k];
+
+    // past frame around the CTA: rows y0-4-R .., columns x0-4-R .., clamped coordinates
+    const int rx0 = x0 - 4 - R, ry0 = y0 - 4 - R;
+    const int nrows = S_OUTH + 8 + 2 * R;
+    for (int i = threadIdx.x; i < nrows * S_RWORDS; i += S_NT) {
+        const int r = i / S_RWORDS, w = i - r * S_RWORDS;
+        const uint8_t *row = ref + (size_t)min(max(ry0 + r, 0), H - 1) * W;
+        const int gx = rx0 + 4 * w;
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        sm.rf[i] = v;
+    }
+    build_tie_order(sm.vord, R);
+
+    // current frame: this lane's 16 rows of 4 columns (masked samples, byte masks; 0 outside)
+    const int cx = x0 - 4 + 4 * lane;                     // first column of the lane's word
+    const int cy0 = y0 + S_ROWS * warp - 4;               // first D row of the warp
+    uint32_t cs[S_DROWS], cmk[S_DROWS];
+#pragma unroll
+    for (int i = 0; i < S_DROWS; ++i) {
+        const int y = cy0 + i;
+        uint32_t a = 0, m = 0;
+        if (y >= 0 && y < H) {
+            const size_t ro = (size_t)y * W;
+#pragma unroll
+            for (int b = 0; b < 4; b += 2) {
+                const int x = cx + b;
+                if (x >= 0 && x < W) {        // W even, x even: pixel pairs never straddle
+                    a |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_smp + ro + x)) << (8 * b);
+                    m |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_msk + ro + x)) << (8 * b);
+                }
+            }
+        }
+        cs[i] = a;
+        cmk[i] = m;
+    }
+    __syncthreads();
+
+    // border handling: candidates with p + v outside the frame are not allowed
+    const bool border = (x0 - 4 - R < 0) || (x0 + 124 + R > W) || (y0 - R < 0) || (y0 + S_OUTH + R > H);
+    uint32_t best02[S_ROWS], best13[S_ROWS], idx02[S_ROWS], idx13[S_ROWS];
+#pragma unroll
+    for (int j = 0; j < S_ROWS; ++j) {
+        best02[j] = best13[j] = 0x7fff7fffu;
+        idx02[j] = idx13[j] = 0u;
+    }
+    const int nv = (2 * R + 1) * (2 * R + 1);
+    const int oy = y0 + S_ROWS * warp;                     // first output row of the warp
+    for (int o = 0; o < nv; ++o) {
+        const short2 v = sm.vord[o];
+        const int vy = v.x, vx = v.y;
+        const int sh = (vx + R) & 3, q = (vx + R) >> 2;
+        const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)sh;
+        const uint32_t *rrow = sm.rf + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
+        uint32_t inv02 = 0, inv13 = 0;                     // lanes of invalid columns -> 0x7fff
+        if (border) {
+            const int c0 = cx + vx;
+            inv02 = ((unsigned)(c0) >= (unsigned)W ? 0x7fffu : 0u) |
+                    ((unsigned)(c0 + 2) >= (unsigned)W ? 0x7fff0000u : 0u);
+            inv13 = ((unsigned)(c0 + 1) >= (unsigned)W ? 0x7fffu : 0u) |
+                    ((unsigned)(c0 + 3) >= (unsigned)W ? 0x7fff0000u : 0u);
+        }
+        uint32_t lo = 0, hi = 0;                           // vertical sums, columns (0,2) (1,3)
+        uint32_t dlo[S_DROWS], dhi[S_DROWS];
+        const uint32_t o2 = (uint32_t)o * 0x00010001u;
+#pragma unroll
+        for (int i = 0; i < S_DROWS; ++i) {
+            const uint32_t r4 = __byte_perm(rrow[i * S_RWORDS], rrow[i * S_RWORDS + 1], sel);
+            const uint32_t d4 = __vabsdiffu4(cs[i], r4) & cmk[i];
+            dlo[i] = __byte_perm(d4, 0u, 0x4240);
+            dhi[i] = __byte_perm(d4, 0u, 0x4341);
+            lo += dlo[i];
+            hi += dhi[i];
+            if (i >= 9) {
+                lo -= dlo[i - 9];
+                hi -= dhi[i - 9];
+            }
+            if (i >= 8) {
+                const int j = i - 8;                       // output row of this window
+                const uint32_t Q = lo + hi;                // (c0+c1, c2+c3)
+                const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
+                const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
+                const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
+                const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
+                const uint32_t A = __byte_perm(Ql, Q, 0x5432);   // (left c-2+c-1, c0+c1)
+                const uint32_t B = __byte_perm(Q, Qr, 0x5432);   // (c2+c3, right c4+c5)
+                uint32_t h02 = Ql + A + Q + B + lor;             // (H0, H2)
+                uint32_t h13 = h02 + Qr - lol - lor;             // (H1, H3)
+                uint32_t rinv = 0;
+                if (border) {
+                    const int py = oy + j;
+                    rinv = (unsigned)(py + vy) >= (unsigned)H ? 0x7fff7fffu : 0u;
+                }
+                h02 |= inv02 | rinv;
+                h13 |= inv13 | rinv;
+                const uint32_t m02 = lane_mask(best02[j] + 0x7fff7fffu - h02);
+                const uint32_t m13 = lane_mask(best13[j] + 0x7fff7fffu - h13);
+                best02[j] = (best02[j] & ~m02) | (h02 & m02);
+                idx02[j] = (idx02[j] & ~m02) | (o2 & m02);
+                best13[j] = (best13[j] & ~m13) | (h13 & m13);
+                idx13[j] = (idx13[j] & ~m13) | (o2 & m13);
+            }
+        }
+    }
+    if (lane == 0 || lane == 31) return;
+    char2 *mv = reinterpret_cast<char2 *>(t.mv[k]);
+#pragma unroll
+    for (int j = 0; j < S_ROWS; ++j) {
+        const int y = oy + j;
+        if (y >= H) continue;
+        const uint32_t id[4] = {idx02[j] & 0xffffu, idx13[j] & 0xffffu, idx02[j] >> 16, idx13[j] >> 16};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int x = cx + c;
+            if (x < W) {
+                const short2 v = sm.vord[id[c]];
+                mv[(size_t)y * W + x] = make_char2((signed char)v.x, (signed char)v.y);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
 {
     if (t.K <= 0) return cudaSuccess;
-    dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
-    me_kernel<<<grid, NT, 0, st>>>(t);
+    if (t.T == 9) {
+        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + S_OUTH - 1) / S_OUTH, t.K);
+        me9_kernel<<<grid, S_NT, 0, st>>>(t);
+    } else {
+        dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
+        me_kernel<<<grid, NT, 0, st>>>(t);
+    }
     count_launch();
     return cudaGetLastError();
 }
