@@ -20,13 +20,15 @@
 //     complex radix-2 FFT, in place in shared memory); twiddles come from a host-computed table
 //     in constant memory at compile-time indices.
 //   * R is Hermitian (the signal is real), so only l = 0..16 is kept: lane k holds R(k, 0..16)
-//     in registers, with its frequency weights (0 for the non-canonical member of a pair) and tie
-//     keys.  The full weight spectrum W (read at shifts k -+ u) lives in shared memory with a
-//     padded row stride, so the 32 lanes' row-shifted reads are conflict-free.
-//   * Selection: per-lane maximum, warp maximum by __reduce_max_sync on the (non-negative) float
-//     bits, then the lowest tie key among the bins that reach it by __reduce_min_sync; the winning
-//     R value comes from its owner lane by one shuffle pair.
-//   * The per-warp shared memory is one 8.7 KB union (support, row spectra, W) so more warps fit.
+//     in registers, with its frequency weights (0 for the non-canonical member of a pair).  The
+//     full weight spectrum W (read at shifts k -+ u) lives in shared memory as rows of 49 columns
+//     (0..31 and 0..16 again), so both shifted reads are immediate offsets from one pointer and
+//     the 32 lanes' row-shifted reads fall in distinct banks.
+//   * Selection: one pass per lane keeps its maximum and the R value there, the warp maximum
+//     comes from __reduce_max_sync on the (non-negative) float bits and the lowest canonical index
+//     among the lanes that reach it from __reduce_min_sync; the owner lane's R value arrives by one
+//     shuffle pair.  The rank-2 residual update is eight fused multiply-adds per bin.
+//   * The per-warp shared memory is one 12.5 KB union (support, row spectra, W).
 #include <cmath>
 #include <type_traits>
 
@@ -39,7 +41,8 @@ namespace {
 constexpr int N = kFsrN;
 constexpr int NH = kFsrHalf;
 constexpr int WPB = 4;                     // warps (blocks) per CTA
-constexpr int WS = N + 1;                  // padded row stride of W (float2)
+constexpr int WC = N + NH;                 // W row with wrap-around: column c holds W(., c mod 32)
+constexpr int WS = WC;                     // row stride of W (float2); 49 -> rows 2 banks apart
 constexpr int SS = N + 1;                  // padded row stride of the support (float)
 
 __constant__ float c_cs[N];                // cos(2 pi j / 32)
@@ -54,12 +57,10 @@ union WarpSmem {
         float2 w[N * NH];                  // row spectra of the weights, then column pass in place
         float2 f[N * NH];                  // row spectra of the weighted values
     } dft;
-    float2 W[N * WS];                      // full weight spectrum
+    float2 W[N * WS];                      // full weight spectrum, columns 0..48 (wrapped)
 };
 
 struct Smem {
-    float wsp[N * N];
-    float wf[N * NH];
     float cs[N];
     float sn[N];
     WarpSmem w[WPB];
@@ -163,14 +164,12 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
-__global__ void __launch_bounds__(WPB * 32, 5) fsr_kernel(FrameTask t)
+__global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const FsrTables *tab = reinterpret_cast<const FsrTables *>(t.fsr_tables);
-    for (int i = threadIdx.x; i < N * N; i += WPB * 32) sm.wsp[i] = tab->wsp[i];
-    for (int i = threadIdx.x; i < N * NH; i += WPB * 32) sm.wf[i] = tab->wf[i];
     if (threadIdx.x < N) {
         sm.cs[threadIdx.x] = tab->cs[threadIdx.x];
         sm.sn[threadIdx.x] = tab->sn[threadIdx.x];
@@ -195,10 +194,10 @@ __global__ void __launch_bounds__(WPB * 32, 5) fsr_kernel(FrameTask t)
         if ((unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) {
             const size_t i = (size_t)y * W + x;
             if (t.cur_msk[i]) {
-                wt = sm.wsp[m * N + lane];
+                wt = __ldg(&tab->wsp[m * N + lane]);
                 val = (float)t.cur_smp[i] * (1.0f / 255.0f);
             } else if (t.pcnt != nullptr && t.pcnt[i]) {
-                wt = mu * sm.wsp[m * N + lane];
+                wt = mu * __ldg(&tab->wsp[m * N + lane]);
                 val = (float)t.psum[i] / (255.0f * (float)t.pcnt[i]);
             }
         }
@@ -243,49 +242,57 @@ __global__ void __launch_bounds__(WPB * 32, 5) fsr_kernel(FrameTask t)
         for (int l = 0; l < NH; ++l) ws.W[k * WS + l] = Wt[l];
     }
     __syncwarp();
-    // W(k, l) for l = 17..31 from Hermitian symmetry: W(k, l) = conj(W(-k, -l))
+    // W(k, l) for l = 17..31 from Hermitian symmetry, W(k, l) = conj(W(-k, -l)); columns 32..48
+    // repeat 0..16 so that the shifted reads W(k -+ u, l -+ u_l) need no wrap-around
 #pragma unroll
     for (int l = NH; l < N; ++l) {
         const float2 a = ws.W[((N - k) & (N - 1)) * WS + (N - l)];
         ws.W[k * WS + l] = make_float2(a.x, -a.y);
     }
+#pragma unroll
+    for (int l = 0; l < NH; ++l) ws.W[k * WS + N + l] = ws.W[k * WS + l];
     __syncwarp();
     const float W0 = ws.W[0].x;
 
-    // frequency weights (0 for the non-canonical member of a pair) and tie keys of this row:
-    // key = lower linear index of the pair, packed with the column (key << 5 | l)
+    // frequency weights of this row, 0 for the non-canonical member of a pair
     float wfr[NH];
-    int keyl[NH];
 #pragma unroll
     for (int l = 0; l < NH; ++l) {
         const bool canon = (l != 0 && l != NH - 1) || k <= N / 2;
-        wfr[l] = canon ? sm.wf[k * NH + l] : 0.f;
-        const int lin = k * N + l, clin = ((N - k) & (N - 1)) * N + ((N - l) & (N - 1));
-        keyl[l] = (min(lin, clin) << 5) | l;
+        wfr[l] = canon ? __ldg(&tab->wf[k * NH + l]) : 0.f;
     }
+    // Ties go to the pair with the lower canonical linear index min(32k+l, 32k'+l'), k' = -k,
+    // l' = -l (mod 32).  Within a stored row that index grows with l for k <= 16 and falls with l
+    // for k > 16 (whose l = 0, 16 bins are not canonical), so a scan in increasing l keeps the
+    // first maximum (strict >) in rows k <= 16 and the last one (>=) in rows k > 16.  Both are one
+    // integer compare on the float bits (e >= 0): e >= be <=> bits(e) + 1 > bits(be).
+    const uint32_t bias = k > N / 2 ? 1u : 0u;
 
     const int pm = (lane >> 2) & 3, pn = lane & 3;     // block pixel of lanes 0..15
     float g = 0.f;
-    const float gamma = t.fsr_gamma;
+    const float gscale = W0 > 0.f ? t.fsr_gamma / W0 : 0.f;
     for (int it = 0; it < t.fsr_iters && W0 > 0.f; ++it) {
-        float m = 0.f;
-#pragma unroll
-        for (int l = 0; l < NH; ++l) m = fmaxf(m, wfr[l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]));
-        m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-        if (!(m > 0.f)) break;                          // residual exhausted
-        int best = 0x7fffffff;
-        float sr = 0.f, si = 0.f;
+        float be = 0.f, sr = 0.f, si = 0.f;
+        int bl = -1;
 #pragma unroll
         for (int l = 0; l < NH; ++l) {
             const float e = wfr[l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]);
-            const bool take = (e == m) && (keyl[l] < best);
-            best = take ? keyl[l] : best;
+            const bool take = (int)(__float_as_uint(e) + bias) > (int)__float_as_uint(be);
+            be = take ? e : be;
             sr = take ? Rre[l] : sr;
             si = take ? Rim[l] : si;
+            bl = take ? l : bl;
         }
-        const int win = __reduce_min_sync(0xffffffffu, best);
+        const float m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(be)));
+        if (!(m > 0.f)) break;                          // residual exhausted
+        int mykey = 0x7fffffff;
+        if (be == m) {
+            const int lin = k * N + bl, clin = ((N - k) & (N - 1)) * N + ((N - bl) & (N - 1));
+            mykey = min(lin, clin);
+        }
+        const int win = __reduce_min_sync(0xffffffffu, mykey);
         // the stored representative of the winning pair and its owner lane
-        int uk = (win >> 5) >> 5, ul = (win >> 5) & (N - 1);
+        int uk = win >> 5, ul = win & (N - 1);
         if (ul > N / 2) {
             uk = (N - uk) & (N - 1);
             ul = N - ul;
@@ -293,26 +300,31 @@ __global__ void __launch_bounds__(WPB * 32, 5) fsr_kernel(FrameTask t)
         const float ure = __shfl_sync(0xffffffffu, sr, uk);
         const float uim = __shfl_sync(0xffffffffu, si, uk);
         const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
-        const float dr = gamma * ure / W0;
-        const float di = self ? 0.f : gamma * uim / W0;
-        const int ra = ((k - uk) & (N - 1)) * WS, rb = ((k + uk) & (N - 1)) * WS;
+        const float dr = gscale * ure;
+        const float di = self ? 0.f : gscale * uim;
+        // W(k-u) at column l - u_l + 32, W(k+u) at column l + u_l of the wrapped rows
+        const float2 *pa = ws.W + ((k - uk) & (N - 1)) * WS + (N - ul);
+        const float2 *pc = ws.W + ((k + uk) & (N - 1)) * WS + ul;
         if (self) {
 #pragma unroll
             for (int l = 0; l < NH; ++l) {
-                const float2 a = ws.W[ra + ((l - ul) & (N - 1))];
+                const float2 a = pa[l];
                 Rre[l] = fmaf(-dr, a.x, Rre[l]);
                 Rim[l] = fmaf(-dr, a.y, Rim[l]);
             }
         } else {
 #pragma unroll
             for (int l = 0; l < NH; ++l) {
-                const float2 a = ws.W[ra + ((l - ul) & (N - 1))];
-                const float2 c = ws.W[rb + ((l + ul) & (N - 1))];
-                // dc * a + conj(dc) * c
-                const float xr = dr * (a.x + c.x) + di * (c.y - a.y);
-                const float xi = dr * (a.y + c.y) + di * (a.x - c.x);
-                Rre[l] -= xr;
-                Rim[l] -= xi;
+                const float2 a = pa[l], c = pc[l];
+                // R -= dc * a + conj(dc) * c
+                float xr = fmaf(-dr, a.x, Rre[l]);
+                xr = fmaf(di, a.y, xr);
+                xr = fmaf(-dr, c.x, xr);
+                Rre[l] = fmaf(-di, c.y, xr);
+                float xi = fmaf(-dr, a.y, Rim[l]);
+                xi = fmaf(-di, a.x, xi);
+                xi = fmaf(-dr, c.y, xi);
+                Rim[l] = fmaf(di, c.x, xi);
             }
         }
         // model at the block pixel of this lane: g += (1 or 2) Re(dc phi_u)
