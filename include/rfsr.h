@@ -86,7 +86,10 @@ typedef struct {
     int batched;           /* 0: each push launches its frame step at once; 1: pushes are staged
                               and rfsr_engine_step() runs one batched step over all streams      */
     int profile;           /* 1: record CUDA events between the phases of every frame step
-                              (read with rfsr_stream_phase_ms)                                   */
+                              (rfsr_stream_phase_ms) or around every batched step
+                              (rfsr_engine_last_step_ms)                                         */
+    int serve;             /* 1: batched engine with its own thread that launches a batched step
+                              whenever frames are staged (continuous batching); implies batched  */
 } rfsr_engine_config;
 
 typedef struct {
@@ -115,24 +118,37 @@ void rfsr_stream_config_default(rfsr_stream_config *cfg);
 int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out);
 /* Waits for all work, destroys all streams of the engine and frees everything. */
 int rfsr_engine_destroy(rfsr_engine *eng);
-/* Batched engines: one frame step (Fig. 1) over every live stream that has a staged frame,
- * launched as one batch.  Returns the number of frames launched (>= 0) or an error. */
+/* Batched engines: one frame step (Fig. 1) over every live stream that has a staged frame.
+ * Each phase (ingest, ME, RME field, checks + projection, FSR) is one persistent launch over the
+ * (stream, tile) pairs of all streams; the task-table copy and the launches are one CUDA graph
+ * (captured at the first step of each template size, then replayed).  Host frames are read and
+ * results written in mapped pinned memory by the kernels themselves.  Streams with more staged
+ * frames get further steps in the same call.  Returns the number of frames launched (>= 0) or an
+ * error (ESTATE: engine not batched). */
 int rfsr_engine_step(rfsr_engine *eng);
+/* Device time of the most recently launched batched step (waits for it) and its frame count.
+ * Needs a batched engine created with profile = 1 (else ESTATE). */
+int rfsr_engine_last_step_ms(rfsr_engine *eng, float *ms, int *frames);
 /* Wait (bounded) until all launched work of the engine is done.  ETIMEDOUT on timeout. */
 int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
 
 /* ---- streams (the four calls of the serving interface) ---------------------------------- */
 /* Create a video stream.  The stream owns its device state: K+1 ring slots of reconstruction,
- * sample plane and mask, the motion fields, decisions, projection sums and FSR output.
- * Errors: EINVAL (sizes / parameters), ENOMEM (device memory, or the engine budget would be
- * exceeded), EDEVICE.  *out is owned by the library until rfsr_destroy. */
+ * sample plane and mask, the motion fields, decisions, projection sums and FSR output.  If that
+ * state does not fit the engine's memory budget now, the stream is queued: *out is set and the
+ * call returns EAGAIN; the stream becomes live (rfsr_stream_get_info: live = 1) when enough
+ * streams have been destroyed, in arrival order; until then pushes return EAGAIN.
+ * Errors: EINVAL (sizes / parameters), ENOMEM (the stream alone exceeds the budget, or device
+ * memory ran out), EDEVICE.  *out is owned by the library until rfsr_destroy. */
 int rfsr_create_stream(rfsr_engine *eng, const rfsr_stream_config *cfg, rfsr_stream **out);
 
 /* Push frame t: samples = f_sub (H x W, unmeasured bytes ignored), mask = b (H x W, 0/1, one 1
  * per 2x2 block), both HOST memory owned by the caller and copied before return, so the caller
- * may reuse them at once.  The frame step runs asynchronously on the GPU.
+ * may reuse them at once.  The frame step runs asynchronously on the GPU (batched engines: at the
+ * next rfsr_engine_step, or at once in a serving engine).
  * Errors: EINVAL, EMASK (checked on the host before anything is enqueued; the stream state is
- * unchanged), EBUSY (max_inflight frames not yet collected), EDEVICE. */
+ * unchanged), EBUSY (max_inflight frames not yet collected), EAGAIN (stream still queued),
+ * EDEVICE. */
 int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask);
 
 /* As rfsr_push_frame, but samples and mask are DEVICE buffers (2-byte aligned, else EINVAL) that

@@ -148,13 +148,11 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
 }
 
 template <int T>
-__global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
+__device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, int tby)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     constexpr int h = T / 2;
     const int H = t.H, W = t.W;
-    const int x0 = blockIdx.x * TP, y0 = blockIdx.y * TP;
+    const int x0 = tbx * TP, y0 = tby * TP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*t.status) return;
     const bool use_nnc = t.cc_mode == 4 || t.cc_mode == 5;
@@ -373,13 +371,35 @@ __device__ __forceinline__ bool tie_before(int ay, int ax, int by, int bx)
     return ax < bx;
 }
 
+template <int T>
+__global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cc_tile<T>(*reinterpret_cast<Smem *>(smem_raw), t, blockIdx.x, blockIdx.y);
+}
+
+template <int T>
+__global__ void __launch_bounds__(NT) cc_batched_kernel(const BatchDesc *bd)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FrameTask task;
+    const int n = bd->ntiles[kPhCc];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhCc, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        const int tx = (task.W + TP - 1) / TP;
+        const int l = tile - bd->off[kPhCc][ti];
+        cc_tile<T>(*reinterpret_cast<Smem *>(smem_raw), task, l % tx, l / tx);
+    }
+}
+
 // RME (Sec. 2.2): reverse motion vector at every past-frame pixel q: argmin over w in [-R, R]^2
 // with q + w inside of C(q + w, -w), exact mean-cost order, tie order on w.
-__global__ void __launch_bounds__(NT) rme_field_kernel(FrameTask t)
+__device__ __forceinline__ void rme_tile(const FrameTask &t, int tbx, int tby, int k)
 {
-    const int qx = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int qy = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
-    const int k = blockIdx.z;
+    const int qx = tbx * 32 + (threadIdx.x & 31);
+    const int qy = tby * (NT / 32) + (threadIdx.x >> 5);
     if (qx >= t.W || qy >= t.H || *t.status) return;
     const int R = t.R;
     int bs = 0, bn = 0, by = 0, bx = 0;
@@ -402,23 +422,68 @@ __global__ void __launch_bounds__(NT) rme_field_kernel(FrameTask t)
         make_char2((signed char)by, (signed char)bx);
 }
 
+__global__ void __launch_bounds__(NT) rme_field_kernel(FrameTask t)
+{
+    rme_tile(t, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(NT) rme_batched_kernel(const BatchDesc *bd)
+{
+    __shared__ FrameTask task;
+    const int n = bd->ntiles[kPhRme];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhRme, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        const int tx = (task.W + 31) / 32, ty = (task.H + NT / 32 - 1) / (NT / 32);
+        const int l = tile - bd->off[kPhRme][ti];
+        rme_tile(task, l % tx, (l / tx) % ty, l / (tx * ty));
+    }
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, bool &done)
+{
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 template <int T>
 cudaError_t launch_cc_t(const FrameTask &t, cudaStream_t st)
 {
     static bool attr = false;
-    const size_t smem = sizeof(Smem);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(cc_project_kernel<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = set_smem(cc_project_kernel<T>, attr);
+    if (e != cudaSuccess) return e;
     dim3 grid((t.W + TP - 1) / TP, (t.H + TP - 1) / TP);
-    cc_project_kernel<T><<<grid, NT, smem, st>>>(t);
+    cc_project_kernel<T><<<grid, NT, sizeof(Smem), st>>>(t);
+    return cudaGetLastError();
+}
+
+template <int T>
+cudaError_t launch_cc_batched_t(const BatchDesc *bd, cudaStream_t st)
+{
+    static bool attr = false;
+    cudaError_t e = set_smem(cc_batched_kernel<T>, attr);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cc_batched_kernel<T><<<sms * 2, NT, sizeof(Smem), st>>>(bd);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int tiles_cc(const FrameTask &t) { return ((t.W + TP - 1) / TP) * ((t.H + TP - 1) / TP); }
+
+int tiles_rme(const FrameTask &t)
+{
+    if (t.K <= 0 || t.cc_mode != 1) return 0;
+    return ((t.W + 31) / 32) * ((t.H + NT / 32 - 1) / (NT / 32)) * t.K;
+}
 
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st)
 {
@@ -436,11 +501,37 @@ cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st)
     return e;
 }
 
+cudaError_t launch_cc_batched(const BatchDesc *bd, int T, cudaStream_t st)
+{
+    cudaError_t e;
+    switch (T) {
+    case 1: e = launch_cc_batched_t<1>(bd, st); break;
+    case 3: e = launch_cc_batched_t<3>(bd, st); break;
+    case 5: e = launch_cc_batched_t<5>(bd, st); break;
+    case 7: e = launch_cc_batched_t<7>(bd, st); break;
+    case 9: e = launch_cc_batched_t<9>(bd, st); break;
+    case 11: e = launch_cc_batched_t<11>(bd, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return e;
+}
+
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st)
 {
     if (t.K <= 0) return cudaSuccess;
     dim3 grid((t.W + 31) / 32, (t.H + NT / 32 - 1) / (NT / 32), t.K);
     rme_field_kernel<<<grid, NT, 0, st>>>(t);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rme_batched(const BatchDesc *bd, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    rme_batched_kernel<<<sms * 4, NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

@@ -164,22 +164,18 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
-__global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
+// one CTA = WPB blocks; sm.cs / sm.sn must hold the twiddles
+__device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const FsrTables *tab = reinterpret_cast<const FsrTables *>(t.fsr_tables);
-    if (threadIdx.x < N) {
-        sm.cs[threadIdx.x] = tab->cs[threadIdx.x];
-        sm.sn[threadIdx.x] = tab->sn[threadIdx.x];
-    }
-    __syncthreads();
-    if (*t.status) return;
+    const int status = *t.status;
+    if (cta == 0 && threadIdx.x == 0 && t.status_out != nullptr) *t.status_out = status;
+    if (status) return;
 
     const int H = t.H, W = t.W;
     const int nbx = (W + kFsrB - 1) / kFsrB, nby = (H + kFsrB - 1) / kFsrB;
-    const int b = blockIdx.x * WPB + warp;
+    const int b = cta * WPB + warp;
     if (b >= nbx * nby) return;
     const int bi = b / nbx, bj = b - bi * nbx;
     const int o = (N - kFsrB) / 2;
@@ -356,6 +352,38 @@ __global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
     }
 }
 
+__device__ __forceinline__ void load_twiddles(Smem &sm)
+{
+    if (threadIdx.x < N) {
+        sm.cs[threadIdx.x] = c_cs[threadIdx.x];
+        sm.sn[threadIdx.x] = c_sn[threadIdx.x];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    load_twiddles(sm);
+    fsr_tile(sm, t, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(WPB * 32, 4) fsr_batched_kernel(const BatchDesc *bd)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ FrameTask task;
+    load_twiddles(sm);
+    const int n = bd->ntiles[kPhFsr];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhFsr, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        fsr_tile(sm, task, tile - bd->off[kPhFsr][ti]);
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -377,8 +405,30 @@ cudaError_t init_fsr(int dev)
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fsr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fsr_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Smem));
     if (e == cudaSuccess) g_ready[dev] = 1;
     return e;
+}
+
+int tiles_fsr(const FrameTask &t)
+{
+    const int nb = ((t.W + kFsrB - 1) / kFsrB) * ((t.H + kFsrB - 1) / kFsrB);
+    return (nb + WPB - 1) / WPB;
+}
+
+cudaError_t launch_fsr_batched(const BatchDesc *bd, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = init_fsr(dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    fsr_batched_kernel<<<sms * 4, WPB * 32, sizeof(Smem), st>>>(bd);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
@@ -388,8 +438,7 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
     if (e != cudaSuccess) return e;
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
-    const int nb = ((t.W + kFsrB - 1) / kFsrB) * ((t.H + kFsrB - 1) / kFsrB);
-    fsr_kernel<<<(nb + WPB - 1) / WPB, WPB * 32, sizeof(Smem), st>>>(t);
+    fsr_kernel<<<tiles_fsr(t), WPB * 32, sizeof(Smem), st>>>(t);
     count_launch();
     return cudaGetLastError();
 }

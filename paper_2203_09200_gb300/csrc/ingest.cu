@@ -18,10 +18,18 @@ std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
 long long launches() { return g_launches.load(); }
 
-__global__ void ingest_kernel(FrameTask t)
+constexpr int kIngestThreads = 256;
+
+int tiles_ingest(const FrameTask &t)
+{
+    const int nb = (t.H / 2) * (t.W / 2);
+    return (nb + kIngestThreads - 1) / kIngestThreads;
+}
+
+__device__ __forceinline__ void ingest_tile(const FrameTask &t, int tile)
 {
     const int bw = t.W >> 1, bh = t.H >> 1;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = tile * kIngestThreads + threadIdx.x;
     if (i == 0 && t.prev_status != nullptr && *t.prev_status != 0)
         atomicOr(t.status, kStatusPoisoned);
     if (i >= bw * bh) return;
@@ -44,10 +52,50 @@ __global__ void ingest_kernel(FrameTask t)
     *reinterpret_cast<uint16_t *>(t.cur_smp + o1) = (uint16_t)(s1 & bm1);
 }
 
+__global__ void __launch_bounds__(kIngestThreads) ingest_kernel(FrameTask t)
+{
+    ingest_tile(t, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kIngestThreads) ingest_batched_kernel(const BatchDesc *bd)
+{
+    __shared__ FrameTask task;
+    const int n = bd->ntiles[kPhIngest];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhIngest, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        ingest_tile(task, tile - bd->off[kPhIngest][ti]);
+    }
+}
+
+// start of a batched step: clear the status word of every task (ingest only ever sets bits)
+__global__ void batch_prologue_kernel(const BatchDesc *bd)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bd->ntasks; i += gridDim.x * blockDim.x)
+        *bd->task[i].status = 0;
+}
+
+cudaError_t launch_batch_prologue(const BatchDesc *bd, cudaStream_t st)
+{
+    batch_prologue_kernel<<<1, kMaxBatch, 0, st>>>(bd);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ingest(const FrameTask &t, cudaStream_t st)
 {
-    const int nb = (t.H / 2) * (t.W / 2);
-    ingest_kernel<<<(nb + 255) / 256, 256, 0, st>>>(t);
+    ingest_kernel<<<tiles_ingest(t), kIngestThreads, 0, st>>>(t);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_batched(const BatchDesc *bd, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ingest_batched_kernel<<<sms * 8, kIngestThreads, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

@@ -59,11 +59,9 @@ __device__ void build_tie_order(short2 *vord, int R)
         }
 }
 
-__global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
+__device__ __forceinline__ void me_tile(Smem &sm, const FrameTask &t, int tbx, int tby, int k)
 {
-    __shared__ Smem sm;
-    const int k = blockIdx.z;
-    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int x0 = tbx * TW, y0 = tby * TH;
     const int H = t.H, W = t.W, T = t.T, h = t.T / 2, R = t.R;
     const int CW = TW + 2 * h, CH = TH + 2 * h;
     const int RW = CW + 2 * R, RH = CH + 2 * R;
@@ -182,11 +180,9 @@ struct Smem9 {
     short2 vord[NVMAX];
 };
 
-__global__ void __launch_bounds__(S_NT, 2) me9_kernel(FrameTask t)
+__device__ __forceinline__ void me9_tile(Smem9 &sm, const FrameTask &t, int tbx, int tby, int k)
 {
-    __shared__ Smem9 sm;
-    const int k = blockIdx.z;
-    const int x0 = blockIdx.x * S_OUTW, y0 = blockIdx.y * S_OUTH;
+    const int x0 = tbx * S_OUTW, y0 = tby * S_OUTH;
     const int H = t.H, W = t.W, R = t.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (*t.status) return;
@@ -314,7 +310,57 @@ __global__ void __launch_bounds__(S_NT, 2) me9_kernel(FrameTask t)
     }
 }
 
+__global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
+{
+    __shared__ Smem sm;
+    me_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(S_NT, 2) me9_kernel(FrameTask t)
+{
+    __shared__ Smem9 sm;
+    me9_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// persistent batched forms: tiles flattened as (k, by, bx), bx fastest
+__global__ void __launch_bounds__(NT) me_batched_kernel(const BatchDesc *bd)
+{
+    __shared__ Smem sm;
+    __shared__ FrameTask task;
+    const int n = bd->ntiles[kPhMe];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhMe, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        const int tx = (task.W + TW - 1) / TW, ty = (task.H + TH - 1) / TH;
+        const int l = tile - bd->off[kPhMe][ti];
+        me_tile(sm, task, l % tx, (l / tx) % ty, l / (tx * ty));
+    }
+}
+
+__global__ void __launch_bounds__(S_NT, 2) me9_batched_kernel(const BatchDesc *bd)
+{
+    __shared__ Smem9 sm;
+    __shared__ FrameTask task;
+    const int n = bd->ntiles[kPhMe];
+    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
+        const int ti = batch_task(bd, kPhMe, tile);
+        __syncthreads();
+        load_task(task, bd->task[ti]);
+        const int tx = (task.W + S_OUTW - 1) / S_OUTW, ty = (task.H + S_OUTH - 1) / S_OUTH;
+        const int l = tile - bd->off[kPhMe][ti];
+        me9_tile(sm, task, l % tx, (l / tx) % ty, l / (tx * ty));
+    }
+}
+
 }  // namespace
+
+int tiles_me(const FrameTask &t)
+{
+    if (t.K <= 0) return 0;
+    if (t.T == 9) return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + S_OUTH - 1) / S_OUTH) * t.K;
+    return ((t.W + TW - 1) / TW) * ((t.H + TH - 1) / TH) * t.K;
+}
 
 cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
 {
@@ -326,6 +372,17 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);
     }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_me_batched(const BatchDesc *bd, int T, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (T == 9) me9_batched_kernel<<<sms * 2, S_NT, 0, st>>>(bd);
+    else me_batched_kernel<<<sms * 4, NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
 // rfsr_api.cpp -- the C ABI declared in include/rfsr.h: engines, streams with their device-
-// resident state, the asynchronous frame step and its host <-> device staging.
+// resident state, the asynchronous frame step, batching and serving.
 //
 // A stream keeps everything the recursion needs on the device (Sec. 2.2 / Fig. 1): a ring of
 // K+1 slots holding the reconstruction, sample plane and mask of the current and the K previous
@@ -7,15 +7,28 @@
 // frame step is one sequence of kernels on the engine's CUDA stream:
 //     ingest -> ME (all K references in one launch) -> [RME reverse field] -> checks + projection
 //     -> FSR + 8-bit reconstruction
-// preceded (host push) by one pinned host->device copy of the frame and followed by one
-// device->host copy of the result into a pinned slot, so the frame loop never leaves the device.
+//
+// Unbatched engines launch a stream's step when its frame is pushed, preceded (host push) by one
+// pinned host->device copy of the frame and followed by one device->host copy of the result.
+//
+// Batched engines stage pushed frames and run one step over every stream that has one: a task
+// table (one FrameTask per stream) is copied to the device and each phase is one persistent
+// launch over the (stream, tile) pairs of all tasks; the copy and the launches are captured once
+// in a CUDA graph per template size and replayed.  Host frames are read by the ingest kernel and
+// results written by the FSR kernel directly in mapped pinned memory, so a batched step issues
+// no per-stream copies.  Streams whose state does not fit the engine's memory budget are queued
+// (EAGAIN) and admitted when memory frees.  With serve = 1 an engine thread launches a batched
+// step whenever frames are staged (continuous batching: frames that arrive while a step runs go
+// into the next one).
 #include "rfsr.h"
 
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -84,17 +97,18 @@ void fill_fsr_tables(FsrTables &tb, double rho)
     }
 }
 
-int wait_event(cudaEvent_t ev, int timeout_ms)
+using Clock = std::chrono::steady_clock;
+
+// bounded wait on an event: polls (never blocks the driver) and gives up after timeout_ms
+int wait_event(cudaEvent_t ev, int timeout_ms, Clock::time_point t0 = Clock::now())
 {
-    const auto t0 = std::chrono::steady_clock::now();
     int spins = 0;
     for (;;) {
         const cudaError_t e = cudaEventQuery(ev);
         if (e == cudaSuccess) return RFSR_OK;
         if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
         if (timeout_ms >= 0) {
-            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
-                                std::chrono::steady_clock::now() - t0).count();
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count();
             if (ms >= timeout_ms) return fail(RFSR_ETIMEDOUT, "frame not ready within timeout");
         }
         if (++spins < 2000) std::this_thread::yield();
@@ -107,17 +121,32 @@ int wait_event(cudaEvent_t ev, int timeout_ms)
 int rfsr::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
 struct Slot {
-    uint8_t *h_in = nullptr;    // pinned samples | mask
-    uint8_t *d_in = nullptr;    // device samples | mask
-    uint8_t *h_out = nullptr;   // pinned reconstruction
+    uint8_t *h_in = nullptr;    // pinned, mapped: samples | mask
+    uint8_t *h_in_dev = nullptr;
+    uint8_t *d_in = nullptr;    // device samples | mask (unbatched host pushes)
+    uint8_t *h_out = nullptr;   // pinned, mapped: reconstruction
+    uint8_t *h_out_dev = nullptr;
     float *h_out32 = nullptr;   // pinned FSR output (keep_f32)
     uint8_t *d_out = nullptr;   // device reconstruction
     float *d_out32 = nullptr;   // device FSR output (keep_f32)
     int *d_status = nullptr;
-    int *h_status = nullptr;
+    int *h_status = nullptr;    // pinned, mapped
+    int *h_status_dev = nullptr;
     cudaEvent_t done = nullptr;
     cudaEvent_t phase[5] = {};  // profile: before ingest, after ingest / ME / checks / FSR
     bool host_push = false;
+    const uint8_t *in_smp = nullptr;   // staged input of a batched engine (device-visible)
+    const uint8_t *in_msk = nullptr;
+};
+
+struct BatchSet {                      // one of two alternating batch buffers
+    BatchDesc *h = nullptr;            // pinned staging
+    BatchDesc *d = nullptr;            // device copy the kernels read
+    cudaEvent_t done = nullptr;        // recorded after the batch's last kernel
+    cudaEvent_t t0 = nullptr, t1 = nullptr;   // timing events around the batch (profile)
+    std::map<int, cudaGraphExec_t> graphs;    // key 2*T + rme
+    std::map<int, int> graph_kernels;
+    bool used = false;
 };
 
 struct rfsr_engine {
@@ -126,14 +155,25 @@ struct rfsr_engine {
     bool own_stream = false;
     size_t budget = 0, used = 0;
     std::mutex mu;
-    std::vector<rfsr_stream *> streams;
+    std::vector<rfsr_stream *> streams;        // live and queued
+    std::deque<rfsr_stream *> queued;          // waiting for memory, in arrival order
+    BatchSet sets[2];
+    int next_set = 0;
+    bool graphs_ok = true;
+    long long staged = 0;                      // frames pushed but not launched (batched)
+    long long batches = 0;
+    int last_batch_set = -1, last_batch_frames = 0;
+    std::thread server;
+    std::condition_variable cv;
+    bool stop = false;
 };
 
 struct rfsr_stream {
     rfsr_engine *eng = nullptr;
     rfsr_stream_config cfg{};
     int H = 0, W = 0, K = 0;
-    size_t bytes = 0;
+    size_t bytes = 0, need = 0;
+    bool live = false;
     std::vector<void *> dev_allocs;
     std::vector<void *> host_allocs;
     uint8_t *ring_rec[kMaxRefs + 1] = {}, *ring_smp[kMaxRefs + 1] = {}, *ring_msk[kMaxRefs + 1] = {};
@@ -145,7 +185,7 @@ struct rfsr_stream {
     float *tables = nullptr;
     int *d_zero = nullptr;
     std::vector<Slot> slots;
-    long long pushed = 0, collected = 0;
+    long long pushed = 0, launched = 0, collected = 0;
     int hist = 0;          // history frames available to the next frame
     int ring_head = 0;     // ring index of the next frame
     int last_slot = -1, last_ring = -1, last_K = 0;
@@ -154,15 +194,15 @@ struct rfsr_stream {
     int dev_alloc(void **p, size_t n)
     {
         cudaError_t e = cudaMalloc(p, n);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if (e != cudaSuccess) return fail(RFSR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
         dev_allocs.push_back(*p);
         bytes += n;
         return RFSR_OK;
     }
     int host_alloc(void **p, size_t n)
     {
-        cudaError_t e = cudaMallocHost(p, n);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+        cudaError_t e = cudaHostAlloc(p, n, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return fail(RFSR_ENOMEM, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
         host_allocs.push_back(*p);
         return RFSR_OK;
     }
@@ -178,8 +218,307 @@ struct rfsr_stream {
         dev_allocs.clear();
         host_allocs.clear();
         slots.clear();
+        bytes = 0;
     }
 };
+
+namespace {
+
+bool batched(const rfsr_engine *e) { return e->cfg.batched || e->cfg.serve; }
+
+// device bytes a stream will hold (admission against the engine budget)
+size_t stream_need(const rfsr_stream_config *c, int M)
+{
+    const size_t HW = (size_t)c->height * c->width;
+    const int K = c->num_refs;
+    const bool rme = c->cc_mode == RFSR_CC_RME;
+    return (size_t)(K + 1) * 3 * HW + (size_t)K * (2 * HW * (rme ? 3 : 2) + HW) + 3 * HW + 4 * HW +
+           sizeof(FsrTables) + 64 + (size_t)M * (3 * HW + (c->keep_f32 ? 4 * HW : 0) + 4);
+}
+
+// allocate a stream's device and pinned state (engine lock held)
+int admit(rfsr_stream *s)
+{
+    rfsr_engine *e = s->eng;
+    const size_t HW = (size_t)s->H * s->W;
+    const int M = e->cfg.max_inflight;
+    const bool rme = s->cfg.cc_mode == RFSR_CC_RME;
+    auto bail = [&](int code) {
+        s->release();
+        return code;
+    };
+#define AL(ptr, n)                                                 \
+    do {                                                           \
+        int r_ = s->dev_alloc((void **)&(ptr), (n));               \
+        if (r_) return bail(r_);                                   \
+    } while (0)
+    for (int r = 0; r <= s->K; ++r) {
+        AL(s->ring_rec[r], HW);
+        AL(s->ring_smp[r], HW);
+        AL(s->ring_msk[r], HW);
+    }
+    for (int k = 0; k < s->K; ++k) {
+        AL(s->mv[k], 2 * HW);
+        AL(s->fmv[k], 2 * HW);
+        AL(s->dec[k], HW);
+        if (rme) AL(s->rmv[k], 2 * HW);
+    }
+    AL(s->psum, 2 * HW);
+    AL(s->pcnt, HW);
+    AL(s->fsr, 4 * HW);
+    AL(s->tables, sizeof(FsrTables));
+    AL(s->d_zero, 64);
+    cudaError_t er = cudaMemset(s->d_zero, 0, 64);
+    if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemset"));
+    {
+        FsrTables tb;
+        fill_fsr_tables(tb, s->cfg.fsr_rho);
+        er = cudaMemcpy(s->tables, &tb, sizeof(tb), cudaMemcpyHostToDevice);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemcpy tables"));
+    }
+    s->slots.assign(M, Slot());
+    for (int i = 0; i < M; ++i) {
+        Slot &sl = s->slots[i];
+        AL(sl.d_in, 2 * HW);
+        AL(sl.d_out, HW);
+        AL(sl.d_status, 4);
+        if (s->cfg.keep_f32) AL(sl.d_out32, 4 * HW);
+        int r_ = s->host_alloc((void **)&sl.h_in, 2 * HW);
+        if (!r_) r_ = s->host_alloc((void **)&sl.h_out, HW);
+        if (!r_) r_ = s->host_alloc((void **)&sl.h_status, 64);
+        if (!r_ && s->cfg.keep_f32) r_ = s->host_alloc((void **)&sl.h_out32, 4 * HW);
+        if (r_) return bail(r_);
+        er = cudaHostGetDevicePointer((void **)&sl.h_in_dev, sl.h_in, 0);
+        if (er == cudaSuccess) er = cudaHostGetDevicePointer((void **)&sl.h_out_dev, sl.h_out, 0);
+        if (er == cudaSuccess) er = cudaHostGetDevicePointer((void **)&sl.h_status_dev, sl.h_status, 0);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaHostGetDevicePointer"));
+        *sl.h_status = 0;
+        er = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
+        if (e->cfg.profile)
+            for (auto &ev : sl.phase) {
+                er = cudaEventCreate(&ev);
+                if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
+            }
+    }
+#undef AL
+    s->live = true;
+    return RFSR_OK;
+}
+
+// admit queued streams in arrival order while they fit (engine lock held)
+void admit_queued(rfsr_engine *e)
+{
+    while (!e->queued.empty()) {
+        rfsr_stream *s = e->queued.front();
+        if (e->used + s->need > e->budget) break;
+        e->used += s->need;
+        if (admit(s) != RFSR_OK) {          // device memory is short after all: keep it queued
+            e->used -= s->need;
+            break;
+        }
+        e->queued.pop_front();
+    }
+}
+
+// the FrameTask of a stream's next frame; advances the ring (engine lock held)
+void prepare_frame(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint8_t *in_msk,
+                   FrameTask &t)
+{
+    Slot &sl = s->slots[slot_idx];
+    std::memset(&t, 0, sizeof(t));
+    const int R1 = s->K + 1;
+    const int r = s->ring_head;
+    t.H = s->H;
+    t.W = s->W;
+    t.K = s->hist;
+    t.T = s->cfg.template_size;
+    t.R = s->cfg.search_radius;
+    t.Rc = s->cfg.check_radius;
+    t.cc_mode = s->cfg.cc_mode;
+    t.fsr_iters = s->cfg.fsr_iterations;
+    t.fsr_gamma = s->cfg.fsr_gamma;
+    t.fsr_proj_weight = s->cfg.fsr_proj_weight;
+    t.fsr_overwrite_projected = s->cfg.fsr_overwrite_projected;
+    t.fsr_tables = s->tables;
+    t.in_smp = in_smp;
+    t.in_msk = in_msk;
+    t.cur_smp = s->ring_smp[r];
+    t.cur_msk = s->ring_msk[r];
+    t.cur_rec = s->ring_rec[r];
+    for (int k = 1; k <= t.K; ++k) {
+        const int rr = ((r - k) % R1 + R1) % R1;
+        t.ref_rec[k - 1] = s->ring_rec[rr];
+        t.ref_smp[k - 1] = s->ring_smp[rr];
+        t.ref_msk[k - 1] = s->ring_msk[rr];
+        t.mv[k - 1] = s->mv[k - 1];
+        t.fmv[k - 1] = s->fmv[k - 1];
+        t.dec[k - 1] = s->dec[k - 1];
+        t.rmv[k - 1] = s->rmv[k - 1];
+    }
+    t.psum = s->psum;
+    t.pcnt = s->pcnt;
+    t.fsr_out = sl.d_out32 ? sl.d_out32 : s->fsr;
+    t.out_u8 = sl.d_out;
+    t.status = sl.d_status;
+    t.prev_status = s->last_slot >= 0 ? s->slots[s->last_slot].d_status : s->d_zero;
+    t.status_out = nullptr;
+    s->last_K = t.K;
+    s->last_ring = s->ring_head;
+    s->last_slot = slot_idx;
+    s->ring_head = (s->ring_head + 1) % (s->K + 1);
+    s->hist = std::min(s->hist + 1, s->K);
+}
+
+// unbatched: the whole frame step of one stream on the engine stream
+int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint8_t *in_msk)
+{
+    rfsr_engine *e = s->eng;
+    Slot &sl = s->slots[slot_idx];
+    FrameTask t;
+    prepare_frame(s, slot_idx, in_smp, in_msk, t);
+    const bool prof = e->cfg.profile != 0;
+    CK(cudaMemsetAsync(sl.d_status, 0, sizeof(int), e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[0], e->stream));
+    CK(launch_ingest(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[1], e->stream));
+    CK(launch_me(t, e->stream));
+    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
+    CK(launch_cc_project(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[3], e->stream));
+    CK(launch_fsr(t, e->stream));
+    if (prof) CK(cudaEventRecord(sl.phase[4], e->stream));
+    CK(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    return RFSR_OK;
+}
+
+// launch the phases of one batch (captured into a graph, or directly)
+cudaError_t launch_batch_phases(const BatchDesc *d, int T, bool rme, cudaStream_t st)
+{
+    cudaError_t e = launch_batch_prologue(d, st);
+    if (e == cudaSuccess) e = launch_ingest_batched(d, st);
+    if (e == cudaSuccess) e = launch_me_batched(d, T, st);
+    if (e == cudaSuccess && rme) e = launch_rme_batched(d, st);
+    if (e == cudaSuccess) e = launch_cc_batched(d, T, st);
+    if (e == cudaSuccess) e = launch_fsr_batched(d, st);
+    return e;
+}
+
+// one batched step over at most kMaxBatch streams sharing one template size (engine lock held).
+// Returns the number of frames launched.
+int step_batch_locked(rfsr_engine *e)
+{
+    if (e->staged <= 0) return 0;
+    BatchSet &set = e->sets[e->next_set];
+    if (set.used) {                                  // its previous batch must be done
+        cudaError_t er = cudaEventSynchronize(set.done);
+        if (er != cudaSuccess) return cuda_fail(er, "cudaEventSynchronize");
+    }
+    BatchDesc *bd = set.h;
+    int T = -1, n = 0;
+    bool rme = false;
+    std::vector<std::pair<rfsr_stream *, int>> taken;
+    for (rfsr_stream *s : e->streams) {
+        if (!s->live || s->launched >= s->pushed || n >= kMaxBatch) continue;
+        if (T < 0) T = s->cfg.template_size;
+        if (s->cfg.template_size != T) continue;
+        const int si = (int)(s->launched % (long long)s->slots.size());
+        Slot &sl = s->slots[si];
+        FrameTask &t = bd->task[n];
+        prepare_frame(s, si, sl.in_smp, sl.in_msk, t);
+        t.status_out = sl.h_status_dev;
+        if (sl.host_push) t.out_u8 = sl.h_out_dev;
+        rme = rme || t.cc_mode == RFSR_CC_RME;
+        taken.emplace_back(s, si);
+        ++n;
+    }
+    if (n == 0) return 0;
+    bd->ntasks = n;
+    int tot[kPhases] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        const FrameTask &t = bd->task[i];
+        const int c[kPhases] = {tiles_ingest(t), tiles_me(t), tiles_rme(t), tiles_cc(t), tiles_fsr(t)};
+        for (int p = 0; p < kPhases; ++p) {
+            bd->off[p][i] = tot[p];
+            tot[p] += c[p];
+        }
+    }
+    for (int p = 0; p < kPhases; ++p) {
+        bd->off[p][n] = tot[p];
+        bd->ntiles[p] = tot[p];
+    }
+    const bool prof = e->cfg.profile != 0;
+    if (prof) CK(cudaEventRecord(set.t0, e->stream));
+    const int key = 2 * T + (rme ? 1 : 0);
+    bool launched = false;
+    if (e->graphs_ok) {
+        auto it = set.graphs.find(key);
+        if (it == set.graphs.end()) {
+            const long long before = launches();
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t er = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+            if (er == cudaSuccess) {
+                cudaError_t er2 = cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream);
+                if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, e->stream);
+                er = cudaStreamEndCapture(e->stream, &g);
+                if (er == cudaSuccess) er = er2;
+            }
+            if (er == cudaSuccess) er = cudaGraphInstantiate(&ex, g, 0);
+            if (g) cudaGraphDestroy(g);
+            const int nk = (int)(launches() - before);
+            count_launch(-nk);                       // counted again at every replay
+            if (er == cudaSuccess) {
+                it = set.graphs.emplace(key, ex).first;
+                set.graph_kernels[key] = nk;
+            } else {
+                e->graphs_ok = false;                // fall back to direct launches
+                cudaGetLastError();
+            }
+        }
+        if (e->graphs_ok) {
+            CK(cudaGraphLaunch(it->second, e->stream));
+            count_launch(set.graph_kernels[key]);
+            launched = true;
+        }
+    }
+    if (!launched) {
+        CK(cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream));
+        CK(launch_batch_phases(set.d, T, rme, e->stream));
+    }
+    if (prof) CK(cudaEventRecord(set.t1, e->stream));
+    CK(cudaEventRecord(set.done, e->stream));
+    set.used = true;
+    for (auto &p : taken) {
+        CK(cudaEventRecord(p.first->slots[p.second].done, e->stream));
+        p.first->launched++;
+        e->staged--;
+    }
+    e->last_batch_set = e->next_set;
+    e->last_batch_frames = n;
+    e->batches++;
+    e->next_set ^= 1;
+    return n;
+}
+
+void serve_loop(rfsr_engine *e)
+{
+    cudaSetDevice(e->cfg.device);
+    std::unique_lock<std::mutex> lk(e->mu);
+    while (!e->stop) {
+        e->cv.wait(lk, [&] { return e->stop || e->staged > 0; });
+        if (e->stop) break;
+        if (step_batch_locked(e) < 0) {
+            // a CUDA error: leave the frames to time out in rfsr_get_frame and back off
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::milliseconds(1));
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -223,32 +562,47 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     if (cfg->device < 0 || cfg->device >= ndev) return fail(RFSR_EINVAL, "engine_create: no such device");
     if (cfg->max_inflight < 0 || cfg->max_inflight > 64)
         return fail(RFSR_EINVAL, "engine_create: max_inflight out of range");
-    if (cfg->batched) return fail(RFSR_EINVAL, "engine_create: batched mode is not available");
     CK(cudaSetDevice(cfg->device));
     auto *e = new rfsr_engine();
     e->cfg = *cfg;
     if (e->cfg.max_inflight == 0) e->cfg.max_inflight = 4;
+    auto bail = [&](cudaError_t er, const char *what) {
+        for (auto &set : e->sets) {
+            if (set.h) cudaFreeHost(set.h);
+            if (set.d) cudaFree(set.d);
+            if (set.done) cudaEventDestroy(set.done);
+            if (set.t0) cudaEventDestroy(set.t0);
+            if (set.t1) cudaEventDestroy(set.t1);
+        }
+        if (e->own_stream) cudaStreamDestroy(e->stream);
+        delete e;
+        return cuda_fail(er, what);
+    };
     if (cfg->cuda_stream) {
         e->stream = (cudaStream_t)cfg->cuda_stream;
     } else {
         cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
-        if (err != cudaSuccess) {
-            delete e;
-            return cuda_fail(err, "cudaStreamCreateWithFlags");
-        }
+        if (err != cudaSuccess) return bail(err, "cudaStreamCreateWithFlags");
         e->own_stream = true;
     }
-    {
-        cudaError_t ie = init_fsr(cfg->device);
-        if (ie != cudaSuccess) {
-            if (e->own_stream) cudaStreamDestroy(e->stream);
-            delete e;
-            return cuda_fail(ie, "FSR set-up");
+    cudaError_t ie = init_fsr(cfg->device);
+    if (ie != cudaSuccess) return bail(ie, "FSR set-up");
+    if (batched(e)) {
+        for (auto &set : e->sets) {
+            cudaError_t er = cudaHostAlloc((void **)&set.h, sizeof(BatchDesc), cudaHostAllocPortable);
+            if (er == cudaSuccess) er = cudaMalloc((void **)&set.d, sizeof(BatchDesc));
+            if (er == cudaSuccess) er = cudaEventCreateWithFlags(&set.done, cudaEventDisableTiming);
+            if (er == cudaSuccess) er = cudaEventCreate(&set.t0);
+            if (er == cudaSuccess) er = cudaEventCreate(&set.t1);
+            if (er != cudaSuccess) return bail(er, "batch buffers");
+            std::memset(set.h, 0, sizeof(BatchDesc));
         }
     }
     size_t fr = 0, tot = 0;
-    CK(cudaMemGetInfo(&fr, &tot));
+    cudaError_t er = cudaMemGetInfo(&fr, &tot);
+    if (er != cudaSuccess) return bail(er, "cudaMemGetInfo");
     e->budget = cfg->memory_budget ? cfg->memory_budget : (size_t)(0.8 * (double)fr);
+    if (cfg->serve) e->server = std::thread(serve_loop, e);
     *out = e;
     return RFSR_OK;
 }
@@ -257,14 +611,32 @@ int rfsr_engine_sync(rfsr_engine *e, int timeout_ms)
 {
     if (!e) return fail(RFSR_EINVAL, "engine_sync: NULL engine");
     CK(cudaSetDevice(e->cfg.device));
+    const auto t0 = Clock::now();
+    if (batched(e)) {                                // wait until every staged frame is launched
+        for (;;) {
+            {
+                std::lock_guard<std::mutex> g(e->mu);
+                if (e->staged == 0) break;
+                if (!e->cfg.serve) return fail(RFSR_ESTATE, "engine_sync: frames staged; call rfsr_engine_step");
+            }
+            if (timeout_ms >= 0 &&
+                std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() >= timeout_ms)
+                return fail(RFSR_ETIMEDOUT, "engine_sync: staged frames not launched within timeout");
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+    }
     cudaEvent_t ev;
     CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    cudaError_t err = cudaEventRecord(ev, e->stream);
+    cudaError_t err;
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        err = cudaEventRecord(ev, e->stream);
+    }
     if (err != cudaSuccess) {
         cudaEventDestroy(ev);
         return cuda_fail(err, "cudaEventRecord");
     }
-    int rc = wait_event(ev, timeout_ms);
+    int rc = wait_event(ev, timeout_ms, t0);
     cudaEventDestroy(ev);
     return rc;
 }
@@ -275,6 +647,15 @@ int rfsr_engine_destroy(rfsr_engine *e)
 {
     if (!e) return fail(RFSR_EINVAL, "engine_destroy: NULL engine");
     cudaSetDevice(e->cfg.device);
+    if (e->server.joinable()) {
+        {
+            std::lock_guard<std::mutex> g(e->mu);
+            e->stop = true;
+        }
+        e->cv.notify_all();
+        e->server.join();
+        e->cfg.serve = 0;                           // streams left are stepped by rfsr_destroy
+    }
     cudaStreamSynchronize(e->stream);
     std::vector<rfsr_stream *> ss;
     {
@@ -282,6 +663,14 @@ int rfsr_engine_destroy(rfsr_engine *e)
         ss = e->streams;
     }
     for (auto *s : ss) rfsr_destroy(s);
+    for (auto &set : e->sets) {
+        for (auto &kv : set.graphs) cudaGraphExecDestroy(kv.second);
+        if (set.h) cudaFreeHost(set.h);
+        if (set.d) cudaFree(set.d);
+        if (set.done) cudaEventDestroy(set.done);
+        if (set.t0) cudaEventDestroy(set.t0);
+        if (set.t1) cudaEventDestroy(set.t1);
+    }
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
     return RFSR_OK;
@@ -290,7 +679,37 @@ int rfsr_engine_destroy(rfsr_engine *e)
 int rfsr_engine_step(rfsr_engine *e)
 {
     if (!e) return fail(RFSR_EINVAL, "engine_step: NULL engine");
-    return fail(RFSR_ESTATE, "engine_step: engine is not batched");
+    if (!batched(e)) return fail(RFSR_ESTATE, "engine_step: engine is not batched");
+    CK(cudaSetDevice(e->cfg.device));
+    std::lock_guard<std::mutex> g(e->mu);
+    int total = 0;
+    for (;;) {
+        const int n = step_batch_locked(e);
+        if (n < 0) return n;
+        if (n == 0) break;
+        total += n;
+    }
+    return total;
+}
+
+int rfsr_engine_last_step_ms(rfsr_engine *e, float *ms, int *frames)
+{
+    if (!e || !ms) return fail(RFSR_EINVAL, "engine_last_step_ms: NULL argument");
+    if (!batched(e) || !e->cfg.profile)
+        return fail(RFSR_ESTATE, "engine_last_step_ms: needs a batched engine with profile = 1");
+    BatchSet *set;
+    int nf;
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        if (e->last_batch_set < 0) return fail(RFSR_ESTATE, "engine_last_step_ms: no batch launched");
+        set = &e->sets[e->last_batch_set];
+        nf = e->last_batch_frames;
+    }
+    CK(cudaSetDevice(e->cfg.device));
+    CK(cudaEventSynchronize(set->t1));
+    CK(cudaEventElapsedTime(ms, set->t0, set->t1));
+    if (frames) *frames = nf;
+    return RFSR_OK;
 }
 
 static int check_stream_config(const rfsr_stream_config *c)
@@ -326,159 +745,33 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
     s->H = cfg->height;
     s->W = cfg->width;
     s->K = cfg->num_refs;
-    const size_t HW = (size_t)s->H * s->W;
-    const int M = e->cfg.max_inflight;
-    const bool rme = cfg->cc_mode == RFSR_CC_RME;
-    // device bytes this stream will hold (admission against the engine budget)
-    size_t need = (size_t)(s->K + 1) * 3 * HW + (size_t)s->K * (2 * HW * (rme ? 3 : 2) + HW) +
-                  3 * HW + 4 * HW + sizeof(FsrTables) + 64 +
-                  (size_t)M * (3 * HW + (cfg->keep_f32 ? 4 * HW : 0) + 4);
-    {
-        std::lock_guard<std::mutex> g(e->mu);
-        if (e->used + need > e->budget) {
-            delete s;
-            return fail(RFSR_ENOMEM, "create_stream: engine memory budget exceeded");
-        }
-        e->used += need;
-    }
-    auto bail = [&](int code) {
-        s->release();
-        {
-            std::lock_guard<std::mutex> g(e->mu);
-            e->used -= need;
-        }
+    s->need = stream_need(cfg, e->cfg.max_inflight);
+    std::lock_guard<std::mutex> g(e->mu);
+    if (s->need > e->budget) {
         delete s;
-        return code;
-    };
-#define AL(ptr, n)                                                 \
-    do {                                                           \
-        int r_ = s->dev_alloc((void **)&(ptr), (n));               \
-        if (r_) return bail(r_);                                   \
-    } while (0)
-    for (int r = 0; r <= s->K; ++r) {
-        AL(s->ring_rec[r], HW);
-        AL(s->ring_smp[r], HW);
-        AL(s->ring_msk[r], HW);
+        return fail(RFSR_ENOMEM, "create_stream: the stream alone exceeds the engine memory budget");
     }
-    for (int k = 0; k < s->K; ++k) {
-        AL(s->mv[k], 2 * HW);
-        AL(s->fmv[k], 2 * HW);
-        AL(s->dec[k], HW);
-        if (rme) AL(s->rmv[k], 2 * HW);
-    }
-    AL(s->psum, 2 * HW);
-    AL(s->pcnt, HW);
-    AL(s->fsr, 4 * HW);
-    AL(s->tables, sizeof(FsrTables));
-    AL(s->d_zero, 64);
-    if (cudaMemset(s->d_zero, 0, 64) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
-    {
-        FsrTables tb;
-        fill_fsr_tables(tb, cfg->fsr_rho);
-        cudaError_t er = cudaMemcpy(s->tables, &tb, sizeof(tb), cudaMemcpyHostToDevice);
-        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemcpy tables"));
-    }
-    s->slots.resize(M);
-    for (int i = 0; i < M; ++i) {
-        Slot &sl = s->slots[i];
-        AL(sl.d_in, 2 * HW);
-        AL(sl.d_out, HW);
-        AL(sl.d_status, 4);
-        if (cfg->keep_f32) AL(sl.d_out32, 4 * HW);
-        int r_ = s->host_alloc((void **)&sl.h_in, 2 * HW);
-        if (!r_) r_ = s->host_alloc((void **)&sl.h_out, HW);
-        if (!r_) r_ = s->host_alloc((void **)&sl.h_status, sizeof(int));
-        if (!r_ && cfg->keep_f32) r_ = s->host_alloc((void **)&sl.h_out32, 4 * HW);
-        if (r_) return bail(r_);
-        cudaError_t er = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
-        if (e->cfg.profile)
-            for (auto &ev : sl.phase) {
-                er = cudaEventCreate(&ev);
-                if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
-            }
-    }
-#undef AL
-    {
-        std::lock_guard<std::mutex> g(e->mu);
+    if (!e->queued.empty() || e->used + s->need > e->budget) {
+        e->queued.push_back(s);
         e->streams.push_back(s);
+        *out = s;
+        return fail(RFSR_EAGAIN, "create_stream: queued until device memory frees up");
     }
+    e->used += s->need;
+    rc = admit(s);
+    if (rc) {
+        e->used -= s->need;
+        delete s;
+        return rc;
+    }
+    e->streams.push_back(s);
     *out = s;
     return RFSR_OK;
 }
 
-static void fill_task(rfsr_stream *s, Slot &sl, FrameTask &t, const uint8_t *in_smp,
-                      const uint8_t *in_msk, const int *prev_status)
+static int push_common(rfsr_stream *s)
 {
-    std::memset(&t, 0, sizeof(t));
-    const int R1 = s->K + 1;
-    const int r = s->ring_head;
-    t.H = s->H;
-    t.W = s->W;
-    t.K = s->hist;
-    t.T = s->cfg.template_size;
-    t.R = s->cfg.search_radius;
-    t.Rc = s->cfg.check_radius;
-    t.cc_mode = s->cfg.cc_mode;
-    t.fsr_iters = s->cfg.fsr_iterations;
-    t.fsr_gamma = s->cfg.fsr_gamma;
-    t.fsr_proj_weight = s->cfg.fsr_proj_weight;
-    t.fsr_overwrite_projected = s->cfg.fsr_overwrite_projected;
-    t.fsr_tables = s->tables;
-    t.in_smp = in_smp;
-    t.in_msk = in_msk;
-    t.cur_smp = s->ring_smp[r];
-    t.cur_msk = s->ring_msk[r];
-    t.cur_rec = s->ring_rec[r];
-    for (int k = 1; k <= t.K; ++k) {
-        const int rr = ((r - k) % R1 + R1) % R1;
-        t.ref_rec[k - 1] = s->ring_rec[rr];
-        t.ref_smp[k - 1] = s->ring_smp[rr];
-        t.ref_msk[k - 1] = s->ring_msk[rr];
-        t.mv[k - 1] = s->mv[k - 1];
-        t.fmv[k - 1] = s->fmv[k - 1];
-        t.dec[k - 1] = s->dec[k - 1];
-        t.rmv[k - 1] = s->rmv[k - 1];
-    }
-    t.psum = s->psum;
-    t.pcnt = s->pcnt;
-    t.fsr_out = sl.d_out32 ? sl.d_out32 : s->fsr;
-    t.out_u8 = sl.d_out;
-    t.status = sl.d_status;
-    t.prev_status = prev_status;
-}
-
-static int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint8_t *in_msk)
-{
-    rfsr_engine *e = s->eng;
-    Slot &sl = s->slots[slot_idx];
-    const int *prev = s->last_slot >= 0 ? s->slots[s->last_slot].d_status : s->d_zero;
-    FrameTask t;
-    fill_task(s, sl, t, in_smp, in_msk, prev);
-    const bool prof = e->cfg.profile != 0;
-    CK(cudaMemsetAsync(sl.d_status, 0, sizeof(int), e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[0], e->stream));
-    CK(launch_ingest(t, e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[1], e->stream));
-    CK(launch_me(t, e->stream));
-    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
-    CK(launch_cc_project(t, e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[3], e->stream));
-    CK(launch_fsr(t, e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[4], e->stream));
-    CK(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
-    s->last_K = t.K;
-    s->last_ring = s->ring_head;
-    s->last_slot = slot_idx;
-    s->ring_head = (s->ring_head + 1) % (s->K + 1);
-    s->hist = std::min(s->hist + 1, s->K);
-    return RFSR_OK;
-}
-
-static int push_common(rfsr_stream *s, const void *a, const void *b)
-{
-    if (!s || !a || !b) return fail(RFSR_EINVAL, "push_frame: NULL argument");
+    if (!s->live) return fail(RFSR_EAGAIN, "push_frame: stream is queued for admission");
     if (s->poisoned) return fail(RFSR_ESTATE, "push_frame: stream had a bad mask; reset it with rfsr_set_history");
     if (s->pushed - s->collected >= (long long)s->slots.size())
         return fail(RFSR_EBUSY, "push_frame: in-flight limit reached, collect frames first");
@@ -487,52 +780,100 @@ static int push_common(rfsr_stream *s, const void *a, const void *b)
 
 int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask)
 {
-    int rc = push_common(s, samples, mask);
-    if (rc) return rc;
+    if (!s || !samples || !mask) return fail(RFSR_EINVAL, "push_frame: NULL argument");
     if (!mask_ok(mask, s->H, s->W)) return fail(RFSR_EMASK, "push_frame: not a quarter-sampling mask");
-    CK(cudaSetDevice(s->eng->cfg.device));
+    rfsr_engine *e = s->eng;
+    CK(cudaSetDevice(e->cfg.device));
     const size_t HW = (size_t)s->H * s->W;
+    std::unique_lock<std::mutex> lk(e->mu);
+    int rc = push_common(s);
+    if (rc) return rc;
     const int si = (int)(s->pushed % (long long)s->slots.size());
     Slot &sl = s->slots[si];
     std::memcpy(sl.h_in, samples, HW);
     std::memcpy(sl.h_in + HW, mask, HW);
-    cudaStream_t st = s->eng->stream;
+    sl.host_push = true;
+    if (batched(e)) {
+        sl.in_smp = sl.h_in_dev;
+        sl.in_msk = sl.h_in_dev + HW;
+        s->pushed++;
+        e->staged++;
+        lk.unlock();
+        e->cv.notify_one();
+        return RFSR_OK;
+    }
+    cudaStream_t st = e->stream;
     CK(cudaMemcpyAsync(sl.d_in, sl.h_in, 2 * HW, cudaMemcpyHostToDevice, st));
     rc = enqueue_step(s, si, sl.d_in, sl.d_in + HW);
     if (rc) return rc;
     CK(cudaMemcpyAsync(sl.h_out, sl.d_out, HW, cudaMemcpyDeviceToHost, st));
     if (sl.h_out32) CK(cudaMemcpyAsync(sl.h_out32, sl.d_out32, 4 * HW, cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(sl.done, st));
-    sl.host_push = true;
     s->pushed++;
+    s->launched++;
     return RFSR_OK;
 }
 
 int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask)
 {
-    int rc = push_common(s, d_samples, d_mask);
-    if (rc) return rc;
+    if (!s || !d_samples || !d_mask) return fail(RFSR_EINVAL, "push_frame: NULL argument");
     if (((uintptr_t)d_samples | (uintptr_t)d_mask) & 1u)
         return fail(RFSR_EINVAL, "push_frame_device: buffers must be 2-byte aligned");
-    CK(cudaSetDevice(s->eng->cfg.device));
+    rfsr_engine *e = s->eng;
+    CK(cudaSetDevice(e->cfg.device));
+    std::unique_lock<std::mutex> lk(e->mu);
+    int rc = push_common(s);
+    if (rc) return rc;
     const int si = (int)(s->pushed % (long long)s->slots.size());
     Slot &sl = s->slots[si];
+    sl.host_push = false;
+    if (batched(e)) {
+        sl.in_smp = d_samples;
+        sl.in_msk = d_mask;
+        s->pushed++;
+        e->staged++;
+        lk.unlock();
+        e->cv.notify_one();
+        return RFSR_OK;
+    }
     rc = enqueue_step(s, si, d_samples, d_mask);
     if (rc) return rc;
-    CK(cudaEventRecord(sl.done, s->eng->stream));
-    sl.host_push = false;
+    CK(cudaEventRecord(sl.done, e->stream));
     s->pushed++;
+    s->launched++;
     return RFSR_OK;
 }
 
+// wait (bounded) until the oldest uncollected frame is launched and done
 static int collect(rfsr_stream *s, int timeout_ms, Slot **out)
 {
-    if (s->collected >= s->pushed) return fail(RFSR_ESTATE, "get_frame: no frame pushed");
-    Slot &sl = s->slots[(size_t)(s->collected % (long long)s->slots.size())];
-    int rc = wait_event(sl.done, timeout_ms);
+    rfsr_engine *e = s->eng;
+    const auto t0 = Clock::now();
+    int si;
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        if (s->collected >= s->pushed) return fail(RFSR_ESTATE, "get_frame: no frame pushed");
+        si = (int)(s->collected % (long long)s->slots.size());
+    }
+    for (int spins = 0;; ++spins) {                 // batched engines: wait for its launch
+        {
+            std::lock_guard<std::mutex> g(e->mu);
+            if (s->launched > s->collected) break;
+        }
+        if (timeout_ms >= 0 &&
+            std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() >= timeout_ms)
+            return fail(RFSR_ETIMEDOUT, "frame not launched within timeout (batched engine: call rfsr_engine_step)");
+        if (spins < 2000) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    Slot &sl = s->slots[si];
+    int rc = wait_event(sl.done, timeout_ms, t0);
     if (rc) return rc;
-    s->collected++;
-    const int st = *sl.h_status;
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        s->collected++;
+    }
+    const int st = *(volatile int *)sl.h_status;
     if (st & kStatusBadMask) {
         s->poisoned = true;
         return fail(RFSR_EMASK, "get_frame: the frame's device mask is not a quarter-sampling mask");
@@ -556,7 +897,10 @@ int rfsr_get_frame(rfsr_stream *s, uint8_t *out_u8, float *out_f32, int timeout_
     const size_t HW = (size_t)s->H * s->W;
     if (sl->host_push) {
         if (out_u8) std::memcpy(out_u8, sl->h_out, HW);
-        if (out_f32) std::memcpy(out_f32, sl->h_out32, 4 * HW);
+        if (out_f32) {
+            if (batched(s->eng)) CK(cudaMemcpy(out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToHost));
+            else std::memcpy(out_f32, sl->h_out32, 4 * HW);
+        }
     } else {
         if (out_u8) CK(cudaMemcpy(out_u8, sl->d_out, HW, cudaMemcpyDeviceToHost));
         if (out_f32) CK(cudaMemcpy(out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToHost));
@@ -568,16 +912,25 @@ int rfsr_get_frame_device(rfsr_stream *s, uint8_t *d_out_u8, float *d_out_f32, i
 {
     if (!s) return fail(RFSR_EINVAL, "get_frame_device: NULL stream");
     if (d_out_f32 && !s->cfg.keep_f32) return fail(RFSR_EINVAL, "get_frame_device: out_f32 needs keep_f32");
-    CK(cudaSetDevice(s->eng->cfg.device));
+    rfsr_engine *e = s->eng;
+    CK(cudaSetDevice(e->cfg.device));
     Slot *sl = nullptr;
     int rc = collect(s, timeout_ms, &sl);
     if (rc) return rc;
     const size_t HW = (size_t)s->H * s->W;
-    cudaStream_t st = s->eng->stream;
-    if (d_out_u8) CK(cudaMemcpyAsync(d_out_u8, sl->d_out, HW, cudaMemcpyDeviceToDevice, st));
-    if (d_out_f32) CK(cudaMemcpyAsync(d_out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToDevice, st));
-    CK(cudaEventRecord(sl->done, st));
-    return wait_event(sl->done, -1);
+    if (!d_out_u8 && !d_out_f32) return RFSR_OK;
+    const uint8_t *src = (sl->host_push && batched(e)) ? sl->h_out_dev : sl->d_out;
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    {
+        std::lock_guard<std::mutex> g(e->mu);
+        if (d_out_u8) CK(cudaMemcpyAsync(d_out_u8, src, HW, cudaMemcpyDeviceToDevice, e->stream));
+        if (d_out_f32) CK(cudaMemcpyAsync(d_out_f32, sl->d_out32, 4 * HW, cudaMemcpyDeviceToDevice, e->stream));
+        CK(cudaEventRecord(ev, e->stream));
+    }
+    rc = wait_event(ev, -1);
+    cudaEventDestroy(ev);
+    return rc;
 }
 
 int rfsr_destroy(rfsr_stream *s)
@@ -585,34 +938,37 @@ int rfsr_destroy(rfsr_stream *s)
     if (!s) return fail(RFSR_EINVAL, "destroy: NULL stream");
     rfsr_engine *e = s->eng;
     cudaSetDevice(e->cfg.device);
+    // frames staged in a batched engine are launched first, then every frame in flight ends
+    for (;;) {
+        std::unique_lock<std::mutex> lk(e->mu);
+        if (s->launched >= s->pushed) break;
+        if (!e->cfg.serve) {
+            if (step_batch_locked(e) <= 0) break;   // (a CUDA error leaves nothing to wait for)
+            continue;
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
     for (auto &sl : s->slots)
         if (sl.done) cudaEventSynchronize(sl.done);
+    std::lock_guard<std::mutex> g(e->mu);
+    const bool was_live = s->live;
     s->release();
-    {
-        std::lock_guard<std::mutex> g(e->mu);
-        e->streams.erase(std::remove(e->streams.begin(), e->streams.end(), s), e->streams.end());
-    }
-    // return the admission bytes (recomputed as in create)
-    {
-        const size_t HW = (size_t)s->H * s->W;
-        const int M = e->cfg.max_inflight;
-        const bool rme = s->cfg.cc_mode == RFSR_CC_RME;
-        size_t n = (size_t)(s->K + 1) * 3 * HW + (size_t)s->K * (2 * HW * (rme ? 3 : 2) + HW) +
-                   3 * HW + 4 * HW + sizeof(FsrTables) + 64 +
-                   (size_t)M * (3 * HW + (s->cfg.keep_f32 ? 4 * HW : 0) + 4);
-        std::lock_guard<std::mutex> g(e->mu);
-        e->used -= std::min(e->used, n);
-    }
+    e->streams.erase(std::remove(e->streams.begin(), e->streams.end(), s), e->streams.end());
+    e->queued.erase(std::remove(e->queued.begin(), e->queued.end(), s), e->queued.end());
+    if (was_live) e->used -= std::min(e->used, s->need);
     delete s;
+    admit_queued(e);
     return RFSR_OK;
 }
 
 int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info)
 {
     if (!s || !info) return fail(RFSR_EINVAL, "stream_get_info: NULL argument");
+    std::lock_guard<std::mutex> g(s->eng->mu);
     info->height = s->H;
     info->width = s->W;
-    info->live = 1;
+    info->live = s->live ? 1 : 0;
     info->frames_pushed = s->pushed;
     info->frames_collected = s->collected;
     info->history_frames = s->hist;
@@ -620,8 +976,20 @@ int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info)
     return RFSR_OK;
 }
 
+// every pushed frame launched and done (batched engines without a server step them here)
 static int wait_all(rfsr_stream *s)
 {
+    rfsr_engine *e = s->eng;
+    for (;;) {
+        std::unique_lock<std::mutex> lk(e->mu);
+        if (s->launched >= s->pushed) break;
+        if (!e->cfg.serve) {
+            if (step_batch_locked(e) <= 0) return fail(RFSR_EDEVICE, "wait_all: batched step failed");
+            continue;
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
     for (auto &sl : s->slots) CK(cudaEventSynchronize(sl.done));
     return RFSR_OK;
 }
@@ -630,6 +998,7 @@ int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
                      const uint8_t *const *smp, const uint8_t *const *msk)
 {
     if (!s) return fail(RFSR_EINVAL, "set_history: NULL stream");
+    if (!s->live) return fail(RFSR_EAGAIN, "set_history: stream is queued for admission");
     if (nrefs < 0 || nrefs > s->K) return fail(RFSR_EINVAL, "set_history: nrefs must be in [0, K]");
     if (nrefs > 0 && (!rec || !smp || !msk)) return fail(RFSR_EINVAL, "set_history: NULL arrays");
     for (int k = 0; k < nrefs; ++k)
@@ -652,6 +1021,7 @@ int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
         CK(cudaMemcpy(s->ring_smp[rr], sm.data(), HW, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(s->ring_msk[rr], bm.data(), HW, cudaMemcpyHostToDevice));
     }
+    std::lock_guard<std::mutex> g(s->eng->mu);
     s->hist = nrefs;
     s->poisoned = false;
     s->last_slot = -1;      // the poison chain restarts
@@ -661,10 +1031,11 @@ int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
 int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
 {
     if (!s || !dst) return fail(RFSR_EINVAL, "debug_get: NULL argument");
-    if (s->last_slot < 0 || s->pushed == 0) return fail(RFSR_ESTATE, "debug_get: no frame processed");
+    if (!s->live || s->pushed == 0) return fail(RFSR_ESTATE, "debug_get: no frame processed");
     CK(cudaSetDevice(s->eng->cfg.device));
     int rc = wait_all(s);
     if (rc) return rc;
+    if (s->last_slot < 0) return fail(RFSR_ESTATE, "debug_get: no frame processed");
     const size_t HW = (size_t)s->H * s->W;
     const bool per_ref = what == RFSR_DBG_MV || what == RFSR_DBG_FMV || what == RFSR_DBG_DECISION ||
                          what == RFSR_DBG_RMV;
@@ -696,7 +1067,8 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
 int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4])
 {
     if (!s || !ms) return fail(RFSR_EINVAL, "stream_phase_ms: NULL argument");
-    if (!s->eng->cfg.profile) return fail(RFSR_ESTATE, "stream_phase_ms: engine not created with profile = 1");
+    if (!s->eng->cfg.profile || batched(s->eng))
+        return fail(RFSR_ESTATE, "stream_phase_ms: needs an unbatched engine created with profile = 1");
     if (s->last_slot < 0) return fail(RFSR_ESTATE, "stream_phase_ms: no frame pushed");
     CK(cudaSetDevice(s->eng->cfg.device));
     Slot &sl = s->slots[s->last_slot];

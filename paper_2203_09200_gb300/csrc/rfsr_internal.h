@@ -57,7 +57,58 @@ struct FrameTask {
     uint8_t *out_u8;           // optional extra copy of the reconstruction (per in-flight slot)
     int *status;               // frame status word (kStatus* bits)
     const int *prev_status;    // status word of the previous frame of the stream (poison chain)
+    int *status_out;           // optional: receives the final status word (written by FSR)
 };
+
+// A batched frame step: up to kMaxBatch frame tasks (one per stream) run by one persistent
+// launch per phase.  Each phase flattens its tiles over the tasks: task i owns the tiles
+// [off[phase][i], off[phase][i+1]) and a CTA finds the task of a tile by binary search.
+constexpr int kMaxBatch = 256;
+enum Phase { kPhIngest = 0, kPhMe = 1, kPhRme = 2, kPhCc = 3, kPhFsr = 4, kPhases = 5 };
+
+struct BatchDesc {
+    int ntasks;
+    int ntiles[kPhases];
+    int off[kPhases][kMaxBatch + 1];
+    FrameTask task[kMaxBatch];
+};
+
+// tiles of a task in each phase (the single-stream launches use the same decomposition)
+int tiles_ingest(const FrameTask &t);
+int tiles_me(const FrameTask &t);
+int tiles_rme(const FrameTask &t);
+int tiles_cc(const FrameTask &t);
+int tiles_fsr(const FrameTask &t);
+
+// task of flattened tile `tile` of phase ph (binary search over the offsets)
+__device__ __forceinline__ int batch_task(const BatchDesc *bd, int ph, int tile)
+{
+    int lo = 0, hi = bd->ntasks;           // off[ph][lo] <= tile < off[ph][hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bd->off[ph][mid] <= tile) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// copy a task into shared memory (all threads of the CTA call it; ends with a barrier)
+__device__ __forceinline__ void load_task(FrameTask &dst, const FrameTask &src)
+{
+    const int *s = reinterpret_cast<const int *>(&src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(FrameTask) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+// batched launchers: one persistent launch per phase over all tasks of bd (device pointer);
+// the grid sizes depend only on the device, so the sequence can be captured in a CUDA graph
+cudaError_t launch_batch_prologue(const BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_ingest_batched(const BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_me_batched(const BatchDesc *bd, int T, cudaStream_t st);
+cudaError_t launch_rme_batched(const BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_cc_batched(const BatchDesc *bd, int T, cudaStream_t st);
+cudaError_t launch_fsr_batched(const BatchDesc *bd, cudaStream_t st);
 
 // FSR tables computed on the host (no device transcendentals): spatial weights rho^d over the
 // support, frequency weights over the stored half spectrum and the DFT twiddles.

@@ -35,7 +35,8 @@ class RfsrError(RuntimeError):
 
 class rfsr_engine_config(C.Structure):
     _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
-                ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int)]
+                ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int),
+                ("serve", C.c_int)]
 
 
 class rfsr_stream_config(C.Structure):
@@ -62,6 +63,7 @@ SYMBOLS = {
     "rfsr_engine_destroy": ([_VP], _I),
     "rfsr_engine_step": ([_VP], _I),
     "rfsr_engine_sync": ([_VP, _I], _I),
+    "rfsr_engine_last_step_ms": ([_VP, C.POINTER(C.c_float), C.POINTER(C.c_int)], _I),
     "rfsr_create_stream": ([_VP, C.POINTER(rfsr_stream_config), C.POINTER(_VP)], _I),
     "rfsr_push_frame": ([_VP, _VP, _VP], _I),
     "rfsr_push_frame_device": ([_VP, _VP, _VP], _I),
@@ -145,25 +147,37 @@ class Engine:
     """rfsr_engine_create / rfsr_engine_destroy."""
 
     def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
-                 max_inflight: int = 4, batched: bool = False, profile: bool = False):
+                 max_inflight: int = 4, batched: bool = False, profile: bool = False,
+                 serve: bool = False):
         lib = load()
         cfg = rfsr_engine_config()
         lib.rfsr_engine_config_default(C.byref(cfg))
         cfg.device, cfg.memory_budget = device, memory_budget
         cfg.cuda_stream = cuda_stream
         cfg.max_inflight, cfg.batched, cfg.profile = max_inflight, int(batched), int(profile)
+        cfg.serve = int(serve)
         h = C.c_void_p()
         _check(lib.rfsr_engine_create(C.byref(cfg), C.byref(h)))
         self.handle = h
         self.streams = []
 
-    def create_stream(self, **kw) -> "Stream":
+    def create_stream(self, allow_queued: bool = False, **kw) -> "Stream":
+        """rfsr_create_stream.  With allow_queued, a stream queued by memory admission (EAGAIN)
+        is returned instead of raising; Stream.live tells when it is admitted."""
         cfg = stream_config(**kw)
         h = C.c_void_p()
-        _check(load().rfsr_create_stream(self.handle, C.byref(cfg), C.byref(h)))
+        rc = load().rfsr_create_stream(self.handle, C.byref(cfg), C.byref(h))
+        if not (allow_queued and rc == RFSR_EAGAIN):
+            _check(rc)
         s = Stream(self, h, cfg)
         self.streams.append(s)
         return s
+
+    def last_step_ms(self):
+        """(device ms, frames) of the most recent batched step (profile engines)."""
+        ms, n = C.c_float(), C.c_int()
+        _check(load().rfsr_engine_last_step_ms(self.handle, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def step(self) -> int:
         return _check(load().rfsr_engine_step(self.handle))
@@ -237,6 +251,10 @@ class Stream:
         a = (C.c_float * 4)()
         _check(load().rfsr_stream_phase_ms(self.handle, a))
         return tuple(float(x) for x in a)
+
+    @property
+    def live(self) -> bool:
+        return bool(self.info().live)
 
     def info(self) -> rfsr_stream_info:
         i = rfsr_stream_info()
