@@ -60,9 +60,45 @@ union WarpSmem {
     float2 W[N * WS];                      // full weight spectrum, columns 0..48 (wrapped)
 };
 
+// the fields of a FrameTask that the FSR of one block reads
+struct FsrArgs {
+    const uint8_t *msk, *smp;              // current mask (0x00 / 0xFF) and masked samples
+    const uint16_t *psum;                  // projection sums and counts (null: none)
+    const uint8_t *pcnt;
+    float *fsr_out;                        // optional outputs
+    uint8_t *rec, *out_u8;
+    const FsrTables *tab;
+    const int *status;
+    int *status_out;
+    int H, W, iters, overwrite;
+    float gamma, mu;
+};
+
+__device__ __forceinline__ void fsr_args(FsrArgs &a, const FrameTask &t)
+{
+    a.msk = t.cur_msk;
+    a.smp = t.cur_smp;
+    a.psum = t.psum;
+    a.pcnt = t.pcnt;
+    a.fsr_out = t.fsr_out;
+    a.rec = t.cur_rec;
+    a.out_u8 = t.out_u8;
+    a.tab = reinterpret_cast<const FsrTables *>(t.fsr_tables);
+    a.status = t.status;
+    a.status_out = t.status_out;
+    a.H = t.H;
+    a.W = t.W;
+    a.iters = t.fsr_iters;
+    a.overwrite = t.fsr_overwrite_projected;
+    a.gamma = t.fsr_gamma;
+    a.mu = t.fsr_proj_weight;
+}
+
 struct Smem {
     float cs[N];
     float sn[N];
+    FsrArgs args[WPB];                     // batched kernel: each warp's current task
+    int tile[2];                           // batched kernel: claimed tiles (double-buffered)
     WarpSmem w[WPB];
 };
 
@@ -164,41 +200,53 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
-// one CTA = WPB blocks; sm.cs / sm.sn must hold the twiddles
-__device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
+// block b of a frame, computed by one warp with its shared-memory area ws; sm.cs / sm.sn must
+// hold the twiddles.  Block 0 also publishes the frame's final status word.
+__device__ __forceinline__ void fsr_block(const Smem &sm, WarpSmem &ws, const FsrArgs &a, int b)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const FsrTables *tab = reinterpret_cast<const FsrTables *>(t.fsr_tables);
-    const int status = *t.status;
-    if (cta == 0 && threadIdx.x == 0 && t.status_out != nullptr) *t.status_out = status;
+    const int lane = threadIdx.x & 31;
+    const int status = *a.status;
+    if (b == 0 && lane == 0 && a.status_out != nullptr) *a.status_out = status;
     if (status) return;
 
-    const int H = t.H, W = t.W;
+    const int H = a.H, W = a.W;
     const int nbx = (W + kFsrB - 1) / kFsrB, nby = (H + kFsrB - 1) / kFsrB;
-    const int b = cta * WPB + warp;
     if (b >= nbx * nby) return;
     const int bi = b / nbx, bj = b - bi * nbx;
     const int o = (N - kFsrB) / 2;
     const int ys = kFsrB * bi - o, xs = kFsrB * bj - o;
-    WarpSmem &ws = sm.w[warp];
-    const float mu = t.fsr_proj_weight;
+    const int iters = a.iters;
+    const float gamma = a.gamma;
+    const FsrTables *tab = a.tab;
 
-    // 1. support: lane = column, coalesced row loads
-    for (int m = 0; m < N; ++m) {
-        const int y = ys + m, x = xs + lane;
-        float wt = 0.f, val = 0.f;
-        if ((unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) {
-            const size_t i = (size_t)y * W + x;
-            if (t.cur_msk[i]) {
-                wt = __ldg(&tab->wsp[m * N + lane]);
-                val = (float)t.cur_smp[i] * (1.0f / 255.0f);
-            } else if (t.pcnt != nullptr && t.pcnt[i]) {
-                wt = mu * __ldg(&tab->wsp[m * N + lane]);
-                val = (float)t.psum[i] / (255.0f * (float)t.pcnt[i]);
+    // 1. support: lane = column, coalesced row loads; rows unrolled so that their loads overlap
+    {
+        const uint8_t *msk = a.msk, *smp = a.smp, *pcnt = a.pcnt;
+        const uint16_t *psum = a.psum;
+        const float mu = a.mu;
+        const int x = xs + lane;
+        const bool xin = (unsigned)x < (unsigned)W;
+#pragma unroll 4
+        for (int m = 0; m < N; ++m) {
+            const int y = ys + m;
+            float wt = 0.f, val = 0.f;
+            if (xin && (unsigned)y < (unsigned)H) {
+                const size_t i = (size_t)y * W + x;
+                const float wd = __ldg(&tab->wsp[m * N + lane]);
+                const unsigned mk = __ldg(msk + i), sv = __ldg(smp + i);
+                const unsigned c = pcnt != nullptr ? __ldg(pcnt + i) : 0u;
+                const unsigned ps = pcnt != nullptr ? __ldg(psum + i) : 0u;
+                if (mk) {
+                    wt = wd;
+                    val = (float)sv * (1.0f / 255.0f);
+                } else if (c) {
+                    wt = mu * wd;
+                    val = (float)ps / (255.0f * (float)c);
+                }
             }
+            ws.sup.w[m * SS + lane] = wt;
+            ws.sup.f[m * SS + lane] = wt * val;
         }
-        ws.sup.w[m * SS + lane] = wt;
-        ws.sup.f[m * SS + lane] = wt * val;
     }
     __syncwarp();
 
@@ -266,8 +314,8 @@ __device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
 
     const int pm = (lane >> 2) & 3, pn = lane & 3;     // block pixel of lanes 0..15
     float g = 0.f;
-    const float gscale = W0 > 0.f ? t.fsr_gamma / W0 : 0.f;
-    for (int it = 0; it < t.fsr_iters && W0 > 0.f; ++it) {
+    const float gscale = W0 > 0.f ? gamma / W0 : 0.f;
+    for (int it = 0; it < iters && W0 > 0.f; ++it) {
         float be = 0.f, sr = 0.f, si = 0.f;
         int bl = -1;
 #pragma unroll
@@ -336,20 +384,29 @@ __device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
             const size_t i = (size_t)y * W + x;
             float v = g;
             uint8_t q;
-            if (t.cur_msk[i]) {
-                v = (float)t.cur_smp[i] * (1.0f / 255.0f);
-                q = t.cur_smp[i];
+            if (a.msk[i]) {
+                v = (float)a.smp[i] * (1.0f / 255.0f);
+                q = a.smp[i];
             } else {
-                if (t.fsr_overwrite_projected && t.pcnt != nullptr && t.pcnt[i])
-                    v = (float)t.psum[i] / (255.0f * (float)t.pcnt[i]);
+                if (a.overwrite && a.pcnt != nullptr && a.pcnt[i])
+                    v = (float)a.psum[i] / (255.0f * (float)a.pcnt[i]);
                 const float r = rintf(255.0f * v);
                 q = (uint8_t)fminf(fmaxf(r, 0.0f), 255.0f);
             }
-            if (t.fsr_out) t.fsr_out[i] = v;
-            if (t.cur_rec) t.cur_rec[i] = q;
-            if (t.out_u8) t.out_u8[i] = q;
+            if (a.fsr_out) a.fsr_out[i] = v;
+            if (a.rec) a.rec[i] = q;
+            if (a.out_u8) a.out_u8[i] = q;
         }
     }
+}
+
+// one CTA = WPB consecutive blocks, one per warp
+__device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
+{
+    const int warp = threadIdx.x >> 5;
+    FsrArgs a;
+    fsr_args(a, t);
+    fsr_block(sm, sm.w[warp], a, cta * WPB + warp);
 }
 
 __device__ __forceinline__ void load_twiddles(Smem &sm)
@@ -369,18 +426,37 @@ __global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
     fsr_tile(sm, t, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(WPB * 32, 4) fsr_batched_kernel(const BatchDesc *bd)
+// batched form: CTAs claim tiles (WPB consecutive blocks of one task) in increasing order from
+// the batch's tile queue, so each tile runs as in the single-stream launch (its warps start
+// together on adjacent blocks and share their support rows in L1).  The next claim is issued
+// before the current tile's work so that its latency is hidden.
+__global__ void __launch_bounds__(WPB * 32, 4) fsr_batched_kernel(BatchDesc *bd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ FrameTask task;
-    load_twiddles(sm);
+    int *queue = &bd->queue[kPhFsr];
+    if (threadIdx.x == 0) sm.tile[0] = atomicAdd(queue, 1);
+    load_twiddles(sm);                                 // ends with a barrier
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = bd->ntiles[kPhFsr];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhFsr, tile);
+    int lo = 0, hi = -1;                               // tile range of the warp's cached task
+    for (int it = 0;; ++it) {
+        const int c = sm.tile[it & 1];
+        if (c >= n) break;                             // uniform over the CTA
+        int nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(queue, 1);
+        if (c < lo || c >= hi) {                       // task change: refresh the warp's copy
+            const int ti = batch_task(bd, kPhFsr, c);
+            lo = bd->off[kPhFsr][ti];
+            hi = bd->off[kPhFsr][ti + 1];
+            __syncwarp();
+            if (lane == 0) fsr_args(sm.args[warp], bd->task[ti]);
+            __syncwarp();
+        }
+        fsr_block(sm, sm.w[warp], sm.args[warp], (c - lo) * WPB + warp);
+        // slot (it+1)&1 was last read before the previous barrier, so it may be rewritten now
+        if (threadIdx.x == 0) sm.tile[(it + 1) & 1] = nxt;
         __syncthreads();
-        load_task(task, bd->task[ti]);
-        fsr_tile(sm, task, tile - bd->off[kPhFsr][ti]);
     }
 }
 
@@ -426,7 +502,8 @@ cudaError_t launch_fsr_batched(const BatchDesc *bd, cudaStream_t st)
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    fsr_batched_kernel<<<sms * 4, WPB * 32, sizeof(Smem), st>>>(bd);
+    // the queue head is written by the kernel; the table is otherwise read-only
+    fsr_batched_kernel<<<sms * 4, WPB * 32, sizeof(Smem), st>>>(const_cast<BatchDesc *>(bd));
     count_launch();
     return cudaGetLastError();
 }

@@ -438,7 +438,8 @@ int step_batch_locked(rfsr_engine *e)
     int tot[kPhases] = {0, 0, 0, 0, 0};
     for (int i = 0; i < n; ++i) {
         const FrameTask &t = bd->task[i];
-        const int c[kPhases] = {tiles_ingest(t), tiles_me(t), tiles_rme(t), tiles_cc(t), tiles_fsr(t)};
+        const int c[kPhases] = {tiles_ingest(t), tiles_me(t), tiles_rme(t), tiles_cc(t),
+                                tiles_fsr(t)};
         for (int p = 0; p < kPhases; ++p) {
             bd->off[p][i] = tot[p];
             tot[p] += c[p];
@@ -447,6 +448,7 @@ int step_batch_locked(rfsr_engine *e)
     for (int p = 0; p < kPhases; ++p) {
         bd->off[p][n] = tot[p];
         bd->ntiles[p] = tot[p];
+        bd->queue[p] = 0;
     }
     const bool prof = e->cfg.profile != 0;
     if (prof) CK(cudaEventRecord(set.t0, e->stream));

@@ -69,6 +69,7 @@ enum Phase { kPhIngest = 0, kPhMe = 1, kPhRme = 2, kPhCc = 3, kPhFsr = 4, kPhase
 struct BatchDesc {
     int ntasks;
     int ntiles[kPhases];
+    int queue[kPhases];                    // tile queue heads (0 in the host copy; atomic claims)
     int off[kPhases][kMaxBatch + 1];
     FrameTask task[kMaxBatch];
 };
@@ -78,7 +79,7 @@ int tiles_ingest(const FrameTask &t);
 int tiles_me(const FrameTask &t);
 int tiles_rme(const FrameTask &t);
 int tiles_cc(const FrameTask &t);
-int tiles_fsr(const FrameTask &t);
+int tiles_fsr(const FrameTask &t);         // CTAs of WPB blocks (single-stream launch)
 
 // task of flattened tile `tile` of phase ph (binary search over the offsets)
 __device__ __forceinline__ int batch_task(const BatchDesc *bd, int ph, int tile)
