@@ -90,7 +90,28 @@ typedef struct {
                               (rfsr_engine_last_step_ms)                                         */
     int serve;             /* 1: batched engine with its own thread that launches a batched step
                               whenever frames are staged (continuous batching); implies batched  */
+    int autotune;          /* batched engines, 1 (default): the first batched steps measure the
+                              tile shapes (rfsr_batch_shape) and keep the fastest; 0: default
+                              shape.  Results are identical for every shape.                    */
 } rfsr_engine_config;
+
+/* Tile shapes of the batched launches (a performance choice only; no counterpart in the paper,
+ * every shape gives bit-identical results). */
+typedef struct {
+    int me_tile_rows;      /* ME (T = 9) template tile of a CTA: 32 or 64 rows x 120 columns; the
+                              staged search window is the tile + (T - 1) + 2R rows (default 64)  */
+    int fsr_blocks;        /* FSR 4x4 blocks per CTA (one per warp): 2, 4 or 8 (default 4)        */
+} rfsr_batch_shape;
+
+/* State of a batched engine's autotuner (rfsr_engine_get_tuning). */
+typedef struct {
+    int tuned;                 /* 1: the shape is final (measured, set, or tuning off)            */
+    int steps;                 /* tuning steps measured so far                                    */
+    rfsr_batch_shape shape;    /* the shape the batched steps use now                             */
+    float me_ns[2];            /* mean device ns per pixel x reference, me_tile_rows 64 / 32
+                                  (0: not measured)                                               */
+    float fsr_ns[3];           /* mean device ns per 4x4 block, fsr_blocks 4 / 2 / 8              */
+} rfsr_tuning;
 
 typedef struct {
     int height, width;     /* HR frame size (even, >= 16)                                        */
@@ -131,6 +152,15 @@ int rfsr_engine_step(rfsr_engine *eng);
 int rfsr_engine_last_step_ms(rfsr_engine *eng, float *ms, int *frames);
 /* Wait (bounded) until all launched work of the engine is done.  ETIMEDOUT on timeout. */
 int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
+/* Batched engines: use this tile shape from the next step on (waits for the engine's launched
+ * work, drops its captured graphs and ends autotuning).  Errors: EINVAL (shape not one of the
+ * listed values), ESTATE (engine not batched). */
+int rfsr_engine_set_shape(rfsr_engine *eng, const rfsr_batch_shape *shape);
+/* Batched engines: the autotuner's state and measurements (ESTATE: engine not batched).  The
+ * autotuner runs tuning step i with ME candidate i mod 2 (64 / 32 rows) and FSR candidate i mod
+ * 3 (4 / 2 / 8 blocks), timing those two phases with CUDA events per unit of work, and keeps per
+ * phase the fastest once each candidate has two measurements (at most 32 tuning steps). */
+int rfsr_engine_get_tuning(rfsr_engine *eng, rfsr_tuning *out);
 
 /* ---- streams (the four calls of the serving interface) ---------------------------------- */
 /* Create a video stream.  The stream owns its device state: K+1 ring slots of reconstruction,

@@ -379,19 +379,16 @@ __global__ void __launch_bounds__(NT) cc_project_kernel(FrameTask t)
 }
 
 template <int T>
-__global__ void __launch_bounds__(NT) cc_batched_kernel(const BatchDesc *bd)
+__global__ void __launch_bounds__(NT) cc_batched_kernel(BatchDesc *bd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ FrameTask task;
-    const int n = bd->ntiles[kPhCc];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhCc, tile);
-        __syncthreads();
-        load_task(task, bd->task[ti]);
-        const int tx = (task.W + TP - 1) / TP;
-        const int l = tile - bd->off[kPhCc][ti];
-        cc_tile<T>(*reinterpret_cast<Smem *>(smem_raw), task, l % tx, l / tx);
-    }
+    __shared__ int claim[2];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    claim_tiles(bd, kPhCc, task, claim, [&](const FrameTask &t, int l) {
+        const int tx = (t.W + TP - 1) / TP;
+        cc_tile<T>(sm, t, l % tx, l / tx);
+    });
 }
 
 // RME (Sec. 2.2): reverse motion vector at every past-frame pixel q: argmin over w in [-R, R]^2
@@ -427,18 +424,14 @@ __global__ void __launch_bounds__(NT) rme_field_kernel(FrameTask t)
     rme_tile(t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(NT) rme_batched_kernel(const BatchDesc *bd)
+__global__ void __launch_bounds__(NT) rme_batched_kernel(BatchDesc *bd)
 {
     __shared__ FrameTask task;
-    const int n = bd->ntiles[kPhRme];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhRme, tile);
-        __syncthreads();
-        load_task(task, bd->task[ti]);
-        const int tx = (task.W + 31) / 32, ty = (task.H + NT / 32 - 1) / (NT / 32);
-        const int l = tile - bd->off[kPhRme][ti];
-        rme_tile(task, l % tx, (l / tx) % ty, l / (tx * ty));
-    }
+    __shared__ int claim[2];
+    claim_tiles(bd, kPhRme, task, claim, [](const FrameTask &t, int l) {
+        const int tx = (t.W + 31) / 32, ty = (t.H + NT / 32 - 1) / (NT / 32);
+        rme_tile(t, l % tx, (l / tx) % ty, l / (tx * ty));
+    });
 }
 
 template <typename K>
@@ -463,15 +456,13 @@ cudaError_t launch_cc_t(const FrameTask &t, cudaStream_t st)
 }
 
 template <int T>
-cudaError_t launch_cc_batched_t(const BatchDesc *bd, cudaStream_t st)
+cudaError_t launch_cc_batched_t(BatchDesc *bd, cudaStream_t st)
 {
     static bool attr = false;
     cudaError_t e = set_smem(cc_batched_kernel<T>, attr);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cc_batched_kernel<T><<<sms * 2, NT, sizeof(Smem), st>>>(bd);
+    static const int grid = persistent_grid(cc_batched_kernel<T>, NT, sizeof(Smem));
+    cc_batched_kernel<T><<<grid, NT, sizeof(Smem), st>>>(bd);
     return cudaGetLastError();
 }
 
@@ -501,7 +492,7 @@ cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st)
     return e;
 }
 
-cudaError_t launch_cc_batched(const BatchDesc *bd, int T, cudaStream_t st)
+cudaError_t launch_cc_batched(BatchDesc *bd, int T, cudaStream_t st)
 {
     cudaError_t e;
     switch (T) {
@@ -526,12 +517,10 @@ cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_rme_batched(const BatchDesc *bd, cudaStream_t st)
+cudaError_t launch_rme_batched(BatchDesc *bd, cudaStream_t st)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    rme_batched_kernel<<<sms * 4, NT, 0, st>>>(bd);
+    static const int grid = persistent_grid(rme_batched_kernel, NT, 0);
+    rme_batched_kernel<<<grid, NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ namespace {
 
 constexpr int N = kFsrN;
 constexpr int NH = kFsrHalf;
-constexpr int WPB = 4;                     // warps (blocks) per CTA
+constexpr int WPB1 = 4;                    // warps (blocks) per CTA of the single-stream launch
 constexpr int WC = N + NH;                 // W row with wrap-around: column c holds W(., c mod 32)
 constexpr int WS = WC;                     // row stride of W (float2); 49 -> rows 2 banks apart
 constexpr int SS = N + 1;                  // padded row stride of the support (float)
@@ -94,9 +94,14 @@ __device__ __forceinline__ void fsr_args(FsrArgs &a, const FrameTask &t)
     a.mu = t.fsr_proj_weight;
 }
 
-struct Smem {
+struct Twiddles {
     float cs[N];
     float sn[N];
+};
+
+template <int WPB>                         // WPB blocks (one per warp) per CTA
+struct Smem {
+    Twiddles tw;
     FsrArgs args[WPB];                     // batched kernel: each warp's current task
     int tile[2];                           // batched kernel: claimed tiles (double-buffered)
     WarpSmem w[WPB];
@@ -200,9 +205,9 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
-// block b of a frame, computed by one warp with its shared-memory area ws; sm.cs / sm.sn must
-// hold the twiddles.  Block 0 also publishes the frame's final status word.
-__device__ __forceinline__ void fsr_block(const Smem &sm, WarpSmem &ws, const FsrArgs &a, int b)
+// block b of a frame, computed by one warp with its shared-memory area ws; tw holds the
+// twiddles.  Block 0 also publishes the frame's final status word.
+__device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, const FsrArgs &a, int b)
 {
     const int lane = threadIdx.x & 31;
     const int status = *a.status;
@@ -373,7 +378,7 @@ __device__ __forceinline__ void fsr_block(const Smem &sm, WarpSmem &ws, const Fs
         }
         // model at the block pixel of this lane: g += (1 or 2) Re(dc phi_u)
         const int j = (uk * (o + pm) + ul * (o + pn)) & (N - 1);
-        const float re_part = dr * sm.cs[j] - di * sm.sn[j];
+        const float re_part = dr * tw.cs[j] - di * tw.sn[j];
         g += self ? re_part : 2.f * re_part;
     }
 
@@ -400,43 +405,40 @@ __device__ __forceinline__ void fsr_block(const Smem &sm, WarpSmem &ws, const Fs
     }
 }
 
-// one CTA = WPB consecutive blocks, one per warp
-__device__ __forceinline__ void fsr_tile(Smem &sm, const FrameTask &t, int cta)
-{
-    const int warp = threadIdx.x >> 5;
-    FsrArgs a;
-    fsr_args(a, t);
-    fsr_block(sm, sm.w[warp], a, cta * WPB + warp);
-}
-
-__device__ __forceinline__ void load_twiddles(Smem &sm)
+__device__ __forceinline__ void load_twiddles(Twiddles &tw)
 {
     if (threadIdx.x < N) {
-        sm.cs[threadIdx.x] = c_cs[threadIdx.x];
-        sm.sn[threadIdx.x] = c_sn[threadIdx.x];
+        tw.cs[threadIdx.x] = c_cs[threadIdx.x];
+        tw.sn[threadIdx.x] = c_sn[threadIdx.x];
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(WPB * 32, 4) fsr_kernel(FrameTask t)
+// single-stream launch: one CTA = WPB1 consecutive blocks, one per warp
+__global__ void __launch_bounds__(WPB1 * 32, 4) fsr_kernel(FrameTask t)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    load_twiddles(sm);
-    fsr_tile(sm, t, blockIdx.x);
+    Smem<WPB1> &sm = *reinterpret_cast<Smem<WPB1> *>(smem_raw);
+    load_twiddles(sm.tw);
+    const int warp = threadIdx.x >> 5;
+    FsrArgs a;
+    fsr_args(a, t);
+    fsr_block(sm.tw, sm.w[warp], a, blockIdx.x * WPB1 + warp);
 }
 
 // batched form: CTAs claim tiles (WPB consecutive blocks of one task) in increasing order from
 // the batch's tile queue, so each tile runs as in the single-stream launch (its warps start
 // together on adjacent blocks and share their support rows in L1).  The next claim is issued
-// before the current tile's work so that its latency is hidden.
-__global__ void __launch_bounds__(WPB * 32, 4) fsr_batched_kernel(BatchDesc *bd)
+// before the current tile's work so that its latency is hidden.  Each warp keeps the arguments
+// of its task in shared memory (refreshed when the task changes).
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, 16 / WPB) fsr_batched_kernel(BatchDesc *bd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<WPB> &sm = *reinterpret_cast<Smem<WPB> *>(smem_raw);
     int *queue = &bd->queue[kPhFsr];
     if (threadIdx.x == 0) sm.tile[0] = atomicAdd(queue, 1);
-    load_twiddles(sm);                                 // ends with a barrier
+    load_twiddles(sm.tw);                              // ends with a barrier
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = bd->ntiles[kPhFsr];
     int lo = 0, hi = -1;                               // tile range of the warp's cached task
@@ -453,11 +455,17 @@ __global__ void __launch_bounds__(WPB * 32, 4) fsr_batched_kernel(BatchDesc *bd)
             if (lane == 0) fsr_args(sm.args[warp], bd->task[ti]);
             __syncwarp();
         }
-        fsr_block(sm, sm.w[warp], sm.args[warp], (c - lo) * WPB + warp);
+        fsr_block(sm.tw, sm.w[warp], sm.args[warp], (c - lo) * WPB + warp);
         // slot (it+1)&1 was last read before the previous barrier, so it may be rewritten now
         if (threadIdx.x == 0) sm.tile[(it + 1) & 1] = nxt;
         __syncthreads();
     }
+}
+
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace
@@ -478,32 +486,41 @@ cudaError_t init_fsr(int dev)
     }
     cudaError_t e = cudaMemcpyToSymbol(c_cs, cs, sizeof(cs));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sn, sn, sizeof(sn));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fsr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(Smem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fsr_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(Smem));
+    if (e == cudaSuccess) e = smem_attr(fsr_kernel, sizeof(Smem<WPB1>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2>, sizeof(Smem<2>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4>, sizeof(Smem<4>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8>, sizeof(Smem<8>));
     if (e == cudaSuccess) g_ready[dev] = 1;
     return e;
 }
 
-int tiles_fsr(const FrameTask &t)
+int tiles_fsr(const FrameTask &t, int fsr_blocks)
 {
     const int nb = ((t.W + kFsrB - 1) / kFsrB) * ((t.H + kFsrB - 1) / kFsrB);
-    return (nb + WPB - 1) / WPB;
+    return (nb + fsr_blocks - 1) / fsr_blocks;
 }
 
-cudaError_t launch_fsr_batched(const BatchDesc *bd, cudaStream_t st)
+namespace {
+template <int WPB>
+void launch_fsr_batched_t(BatchDesc *bd, cudaStream_t st)
 {
-    int dev = 0, sms = 0;
+    static const int grid = persistent_grid(fsr_batched_kernel<WPB>, WPB * 32, sizeof(Smem<WPB>));
+    fsr_batched_kernel<WPB><<<grid, WPB * 32, sizeof(Smem<WPB>), st>>>(bd);
+}
+}  // namespace
+
+cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, cudaStream_t st)
+{
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // the queue head is written by the kernel; the table is otherwise read-only
-    fsr_batched_kernel<<<sms * 4, WPB * 32, sizeof(Smem), st>>>(const_cast<BatchDesc *>(bd));
+    switch (fsr_blocks) {
+    case 2: launch_fsr_batched_t<2>(bd, st); break;
+    case 8: launch_fsr_batched_t<8>(bd, st); break;
+    default: launch_fsr_batched_t<4>(bd, st); break;
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -515,7 +532,7 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
     if (e != cudaSuccess) return e;
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
-    fsr_kernel<<<tiles_fsr(t), WPB * 32, sizeof(Smem), st>>>(t);
+    fsr_kernel<<<tiles_fsr(t, WPB1), WPB1 * 32, sizeof(Smem<WPB1>), st>>>(t);
     count_launch();
     return cudaGetLastError();
 }

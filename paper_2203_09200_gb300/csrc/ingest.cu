@@ -57,26 +57,21 @@ __global__ void __launch_bounds__(kIngestThreads) ingest_kernel(FrameTask t)
     ingest_tile(t, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(kIngestThreads) ingest_batched_kernel(const BatchDesc *bd)
+__global__ void __launch_bounds__(kIngestThreads) ingest_batched_kernel(BatchDesc *bd)
 {
     __shared__ FrameTask task;
-    const int n = bd->ntiles[kPhIngest];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhIngest, tile);
-        __syncthreads();
-        load_task(task, bd->task[ti]);
-        ingest_tile(task, tile - bd->off[kPhIngest][ti]);
-    }
+    __shared__ int claim[2];
+    claim_tiles(bd, kPhIngest, task, claim, [](const FrameTask &t, int l) { ingest_tile(t, l); });
 }
 
 // start of a batched step: clear the status word of every task (ingest only ever sets bits)
-__global__ void batch_prologue_kernel(const BatchDesc *bd)
+__global__ void batch_prologue_kernel(BatchDesc *bd)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bd->ntasks; i += gridDim.x * blockDim.x)
         *bd->task[i].status = 0;
 }
 
-cudaError_t launch_batch_prologue(const BatchDesc *bd, cudaStream_t st)
+cudaError_t launch_batch_prologue(BatchDesc *bd, cudaStream_t st)
 {
     batch_prologue_kernel<<<1, kMaxBatch, 0, st>>>(bd);
     count_launch();
@@ -90,12 +85,10 @@ cudaError_t launch_ingest(const FrameTask &t, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ingest_batched(const BatchDesc *bd, cudaStream_t st)
+cudaError_t launch_ingest_batched(BatchDesc *bd, cudaStream_t st)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    ingest_batched_kernel<<<sms * 8, kIngestThreads, 0, st>>>(bd);
+    static const int grid = persistent_grid(ingest_batched_kernel, kIngestThreads, 0);
+    ingest_batched_kernel<<<grid, kIngestThreads, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

@@ -157,14 +157,15 @@ __device__ __forceinline__ void me_tile(Smem &sm, const FrameTask &t, int tbx, i
 // run in tie order with strict improvement, so the first minimum in tie order wins.  Lanes 0 and
 // 31 only feed their neighbours: a strip yields 120 output columns.
 // ---------------------------------------------------------------------------------------------
+// The template tile of a CTA is WARPS strips of 8 rows x 120 columns; its search window (the
+// staged past-frame rows) is the tile plus the template half and the radius on each side.
 constexpr int S_ROWS = 8;                  // output rows per warp
-constexpr int S_WARPS = 8;
-constexpr int S_NT = 32 * S_WARPS;
 constexpr int S_OUTW = 120;                // output columns per CTA
-constexpr int S_OUTH = S_ROWS * S_WARPS;   // output rows per CTA
 constexpr int S_DROWS = S_ROWS + 8;        // D rows per warp (T = 9)
-constexpr int S_RROWS = S_OUTH + 8 + 2 * kMaxRadius;            // past-frame rows staged
 constexpr int S_RWORDS = (128 + 2 * kMaxRadius + 3) / 4 + 1;   // words per staged row
+template <int WARPS> __host__ __device__ constexpr int s_nt() { return 32 * WARPS; }
+template <int WARPS> __host__ __device__ constexpr int s_outh() { return S_ROWS * WARPS; }          // tile rows
+template <int WARPS> __host__ __device__ constexpr int s_rrows() { return S_ROWS * WARPS + 8 + 2 * kMaxRadius; }
 
 // lane masks from the guard bits of a packed pair: 0xffff in each 16-bit lane whose bit 15 (lo)
 // or bit 31 (hi) is set (prmt's default mode replicates the sign bit when a selector's msb is set)
@@ -175,13 +176,16 @@ __device__ __forceinline__ uint32_t lane_mask(uint32_t t)
     return m;
 }
 
+template <int WARPS>
 struct Smem9 {
-    uint32_t rf[S_RROWS * S_RWORDS];
+    uint32_t rf[s_rrows<WARPS>() * S_RWORDS];
     short2 vord[NVMAX];
 };
 
-__device__ __forceinline__ void me9_tile(Smem9 &sm, const FrameTask &t, int tbx, int tby, int k)
+template <int WARPS>
+__device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, int tbx, int tby, int k)
 {
+    constexpr int S_NT = s_nt<WARPS>(), S_OUTH = s_outh<WARPS>();
     const int x0 = tbx * S_OUTW, y0 = tby * S_OUTH;
     const int H = t.H, W = t.W, R = t.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -316,49 +320,43 @@ __global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
     me_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(S_NT, 2) me9_kernel(FrameTask t)
+__global__ void __launch_bounds__(s_nt<8>(), 2) me9_kernel(FrameTask t)
 {
-    __shared__ Smem9 sm;
-    me9_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
+    __shared__ Smem9<8> sm;
+    me9_tile<8>(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// persistent batched forms: tiles flattened as (k, by, bx), bx fastest
-__global__ void __launch_bounds__(NT) me_batched_kernel(const BatchDesc *bd)
+// batched forms on the tile queue: tiles of a task flattened as (k, by, bx), bx fastest
+__global__ void __launch_bounds__(NT) me_batched_kernel(BatchDesc *bd)
 {
     __shared__ Smem sm;
     __shared__ FrameTask task;
-    const int n = bd->ntiles[kPhMe];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhMe, tile);
-        __syncthreads();
-        load_task(task, bd->task[ti]);
-        const int tx = (task.W + TW - 1) / TW, ty = (task.H + TH - 1) / TH;
-        const int l = tile - bd->off[kPhMe][ti];
-        me_tile(sm, task, l % tx, (l / tx) % ty, l / (tx * ty));
-    }
+    __shared__ int claim[2];
+    claim_tiles(bd, kPhMe, task, claim, [&](const FrameTask &t, int l) {
+        const int tx = (t.W + TW - 1) / TW, ty = (t.H + TH - 1) / TH;
+        me_tile(sm, t, l % tx, (l / tx) % ty, l / (tx * ty));
+    });
 }
 
-__global__ void __launch_bounds__(S_NT, 2) me9_batched_kernel(const BatchDesc *bd)
+template <int WARPS>
+__global__ void __launch_bounds__(s_nt<WARPS>(), 16 / WARPS) me9_batched_kernel(BatchDesc *bd)
 {
-    __shared__ Smem9 sm;
+    __shared__ Smem9<WARPS> sm;
     __shared__ FrameTask task;
-    const int n = bd->ntiles[kPhMe];
-    for (int tile = blockIdx.x; tile < n; tile += gridDim.x) {
-        const int ti = batch_task(bd, kPhMe, tile);
-        __syncthreads();
-        load_task(task, bd->task[ti]);
-        const int tx = (task.W + S_OUTW - 1) / S_OUTW, ty = (task.H + S_OUTH - 1) / S_OUTH;
-        const int l = tile - bd->off[kPhMe][ti];
-        me9_tile(sm, task, l % tx, (l / tx) % ty, l / (tx * ty));
-    }
+    __shared__ int claim[2];
+    claim_tiles(bd, kPhMe, task, claim, [&](const FrameTask &t, int l) {
+        const int tx = (t.W + S_OUTW - 1) / S_OUTW, ty = (t.H + s_outh<WARPS>() - 1) / s_outh<WARPS>();
+        me9_tile<WARPS>(sm, t, l % tx, (l / tx) % ty, l / (tx * ty));
+    });
 }
 
 }  // namespace
 
-int tiles_me(const FrameTask &t)
+int tiles_me(const FrameTask &t, int me_warps)
 {
     if (t.K <= 0) return 0;
-    if (t.T == 9) return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + S_OUTH - 1) / S_OUTH) * t.K;
+    const int outh = S_ROWS * me_warps;
+    if (t.T == 9) return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + outh - 1) / outh) * t.K;
     return ((t.W + TW - 1) / TW) * ((t.H + TH - 1) / TH) * t.K;
 }
 
@@ -366,8 +364,8 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
 {
     if (t.K <= 0) return cudaSuccess;
     if (t.T == 9) {
-        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + S_OUTH - 1) / S_OUTH, t.K);
-        me9_kernel<<<grid, S_NT, 0, st>>>(t);
+        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + s_outh<8>() - 1) / s_outh<8>(), t.K);
+        me9_kernel<<<grid, s_nt<8>(), 0, st>>>(t);
     } else {
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);
@@ -376,13 +374,18 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_me_batched(const BatchDesc *bd, int T, cudaStream_t st)
+cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, cudaStream_t st)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (T == 9) me9_batched_kernel<<<sms * 2, S_NT, 0, st>>>(bd);
-    else me_batched_kernel<<<sms * 4, NT, 0, st>>>(bd);
+    if (T == 9 && me_warps == 4) {
+        static const int grid = persistent_grid(me9_batched_kernel<4>, s_nt<4>(), 0);
+        me9_batched_kernel<4><<<grid, s_nt<4>(), 0, st>>>(bd);
+    } else if (T == 9) {
+        static const int grid = persistent_grid(me9_batched_kernel<8>, s_nt<8>(), 0);
+        me9_batched_kernel<8><<<grid, s_nt<8>(), 0, st>>>(bd);
+    } else {
+        static const int grid = persistent_grid(me_batched_kernel, NT, 0);
+        me_batched_kernel<<<grid, NT, 0, st>>>(bd);
+    }
     count_launch();
     return cudaGetLastError();
 }

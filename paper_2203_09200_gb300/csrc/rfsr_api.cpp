@@ -120,6 +120,12 @@ int wait_event(cudaEvent_t ev, int timeout_ms, Clock::time_point t0 = Clock::now
 
 int rfsr::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
+bool rfsr::shape_valid(const BatchShape &s)
+{
+    return (s.me_warps == 4 || s.me_warps == 8) &&
+           (s.fsr_blocks == 2 || s.fsr_blocks == 4 || s.fsr_blocks == 8);
+}
+
 struct Slot {
     uint8_t *h_in = nullptr;    // pinned, mapped: samples | mask
     uint8_t *h_in_dev = nullptr;
@@ -144,9 +150,30 @@ struct BatchSet {                      // one of two alternating batch buffers
     BatchDesc *d = nullptr;            // device copy the kernels read
     cudaEvent_t done = nullptr;        // recorded after the batch's last kernel
     cudaEvent_t t0 = nullptr, t1 = nullptr;   // timing events around the batch (profile)
+    cudaEvent_t ph[4] = {};            // tuning: before / after ME, before / after FSR
     std::map<int, cudaGraphExec_t> graphs;    // key 2*T + rme
     std::map<int, int> graph_kernels;
     bool used = false;
+    bool tune_pending = false;         // a tuning measurement waits in ph[]
+    int tune_me = -1, tune_fsr = -1;   // candidates it measured (-1: phase not measured)
+    double me_units = 0, fsr_units = 0;
+};
+
+// Online autotuner of the batched tile shapes.  Every shape gives bit-identical results, so the
+// first batched steps of an engine serve as the measurements: tuning step i runs ME (T = 9) with
+// candidate i mod 2 and FSR with candidate i mod 3, directly launched with events around the two
+// phases.  Once every candidate has kSamples measurements the engine keeps, per phase, the one
+// with the least device time per unit of work (ME: pixel x reference, FSR: 4x4 block); from then
+// on its steps are captured and replayed as CUDA graphs.
+struct Tuner {
+    static constexpr int kMe = 2, kFsr = 3, kSamples = 2, kMaxSteps = 32;
+    static constexpr int me_cand[kMe] = {8, 4};          // warp strips per ME tile (64 / 32 rows)
+    static constexpr int fsr_cand[kFsr] = {4, 2, 8};     // FSR blocks per CTA
+    bool active = false;
+    int steps = 0;                                       // tuning steps launched
+    int measured = 0;                                    // tuning steps harvested
+    double me_ns[kMe] = {}, fsr_ns[kFsr] = {};           // sums of ns per unit
+    int me_n[kMe] = {}, fsr_n[kFsr] = {};
 };
 
 struct rfsr_engine {
@@ -160,6 +187,8 @@ struct rfsr_engine {
     BatchSet sets[2];
     int next_set = 0;
     bool graphs_ok = true;
+    BatchShape shape;                          // tile shapes of the batched launches
+    Tuner tune;
     long long staged = 0;                      // frames pushed but not launched (batched)
     long long batches = 0;
     int last_batch_set = -1, last_batch_frames = 0;
@@ -393,16 +422,63 @@ int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint
     return RFSR_OK;
 }
 
-// launch the phases of one batch (captured into a graph, or directly)
-cudaError_t launch_batch_phases(const BatchDesc *d, int T, bool rme, cudaStream_t st)
+// launch the phases of one batch (captured into a graph, or directly); ph (tuning only): events
+// recorded before / after ME and before / after FSR
+cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape &sh, cudaStream_t st,
+                                cudaEvent_t *ph = nullptr)
 {
     cudaError_t e = launch_batch_prologue(d, st);
     if (e == cudaSuccess) e = launch_ingest_batched(d, st);
-    if (e == cudaSuccess) e = launch_me_batched(d, T, st);
+    if (e == cudaSuccess && ph) e = cudaEventRecord(ph[0], st);
+    if (e == cudaSuccess) e = launch_me_batched(d, T, sh.me_warps, st);
+    if (e == cudaSuccess && ph) e = cudaEventRecord(ph[1], st);
     if (e == cudaSuccess && rme) e = launch_rme_batched(d, st);
     if (e == cudaSuccess) e = launch_cc_batched(d, T, st);
-    if (e == cudaSuccess) e = launch_fsr_batched(d, st);
+    if (e == cudaSuccess && ph) e = cudaEventRecord(ph[2], st);
+    if (e == cudaSuccess) e = launch_fsr_batched(d, sh.fsr_blocks, st);
+    if (e == cudaSuccess && ph) e = cudaEventRecord(ph[3], st);
     return e;
+}
+
+// fold a finished tuning measurement of set into the tuner and decide once every candidate is
+// measured (engine lock held; the set's batch must be complete)
+int harvest_tuning(rfsr_engine *e, BatchSet &set)
+{
+    if (!set.tune_pending) return RFSR_OK;
+    set.tune_pending = false;
+    Tuner &tu = e->tune;
+    float me_ms = 0.f, fsr_ms = 0.f;
+    CK(cudaEventElapsedTime(&me_ms, set.ph[0], set.ph[1]));
+    CK(cudaEventElapsedTime(&fsr_ms, set.ph[2], set.ph[3]));
+    if (set.tune_me >= 0 && set.me_units > 0) {
+        tu.me_ns[set.tune_me] += 1e6 * me_ms / set.me_units;
+        tu.me_n[set.tune_me]++;
+    }
+    if (set.tune_fsr >= 0 && set.fsr_units > 0) {
+        tu.fsr_ns[set.tune_fsr] += 1e6 * fsr_ms / set.fsr_units;
+        tu.fsr_n[set.tune_fsr]++;
+    }
+    tu.measured++;
+    if (!tu.active) return RFSR_OK;
+    bool all = true;
+    for (int i = 0; i < Tuner::kFsr; ++i) all = all && tu.fsr_n[i] >= Tuner::kSamples;
+    const bool me_seen = tu.me_n[0] + tu.me_n[1] > 0;    // no T = 9 work: ME keeps its default
+    for (int i = 0; i < Tuner::kMe && me_seen; ++i) all = all && tu.me_n[i] >= Tuner::kSamples;
+    if (!all && tu.steps < Tuner::kMaxSteps) return RFSR_OK;
+    auto pick = [](const double *ns, const int *cnt, const int *cand, int n, int dflt) {
+        int best = dflt;
+        double bv = -1.0;
+        for (int i = 0; i < n; ++i)
+            if (cnt[i] > 0 && (bv < 0.0 || ns[i] / cnt[i] < bv)) {
+                bv = ns[i] / cnt[i];
+                best = cand[i];
+            }
+        return best;
+    };
+    e->shape.me_warps = pick(tu.me_ns, tu.me_n, Tuner::me_cand, Tuner::kMe, e->shape.me_warps);
+    e->shape.fsr_blocks = pick(tu.fsr_ns, tu.fsr_n, Tuner::fsr_cand, Tuner::kFsr, e->shape.fsr_blocks);
+    tu.active = false;
+    return RFSR_OK;
 }
 
 // one batched step over at most kMaxBatch streams sharing one template size (engine lock held).
@@ -414,6 +490,8 @@ int step_batch_locked(rfsr_engine *e)
     if (set.used) {                                  // its previous batch must be done
         cudaError_t er = cudaEventSynchronize(set.done);
         if (er != cudaSuccess) return cuda_fail(er, "cudaEventSynchronize");
+        const int rc = harvest_tuning(e, set);
+        if (rc != RFSR_OK) return rc;
     }
     BatchDesc *bd = set.h;
     int T = -1, n = 0;
@@ -434,16 +512,32 @@ int step_batch_locked(rfsr_engine *e)
         ++n;
     }
     if (n == 0) return 0;
+    // tile shape of this step: a tuning candidate while the tuner measures, else the engine's
+    Tuner &tu = e->tune;
+    const bool tuning = tu.active;
+    BatchShape sh = e->shape;
+    int cme = -1, cfsr = -1;
+    if (tuning) {
+        cfsr = tu.steps % Tuner::kFsr;
+        sh.fsr_blocks = Tuner::fsr_cand[cfsr];
+        if (T == 9) {
+            cme = tu.steps % Tuner::kMe;
+            sh.me_warps = Tuner::me_cand[cme];
+        }
+    }
     bd->ntasks = n;
     int tot[kPhases] = {0, 0, 0, 0, 0};
+    double me_units = 0, fsr_units = 0;
     for (int i = 0; i < n; ++i) {
         const FrameTask &t = bd->task[i];
-        const int c[kPhases] = {tiles_ingest(t), tiles_me(t), tiles_rme(t), tiles_cc(t),
-                                tiles_fsr(t)};
+        const int c[kPhases] = {tiles_ingest(t), tiles_me(t, sh.me_warps), tiles_rme(t), tiles_cc(t),
+                                tiles_fsr(t, sh.fsr_blocks)};
         for (int p = 0; p < kPhases; ++p) {
             bd->off[p][i] = tot[p];
             tot[p] += c[p];
         }
+        me_units += (double)t.H * t.W * t.K;
+        fsr_units += (double)((t.H + kFsrB - 1) / kFsrB) * ((t.W + kFsrB - 1) / kFsrB);
     }
     for (int p = 0; p < kPhases; ++p) {
         bd->off[p][n] = tot[p];
@@ -454,7 +548,7 @@ int step_batch_locked(rfsr_engine *e)
     if (prof) CK(cudaEventRecord(set.t0, e->stream));
     const int key = 2 * T + (rme ? 1 : 0);
     bool launched = false;
-    if (e->graphs_ok) {
+    if (e->graphs_ok && !tuning) {
         auto it = set.graphs.find(key);
         if (it == set.graphs.end()) {
             const long long before = launches();
@@ -463,7 +557,7 @@ int step_batch_locked(rfsr_engine *e)
             cudaError_t er = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
             if (er == cudaSuccess) {
                 cudaError_t er2 = cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream);
-                if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, e->stream);
+                if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, sh, e->stream);
                 er = cudaStreamEndCapture(e->stream, &g);
                 if (er == cudaSuccess) er = er2;
             }
@@ -487,7 +581,15 @@ int step_batch_locked(rfsr_engine *e)
     }
     if (!launched) {
         CK(cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream));
-        CK(launch_batch_phases(set.d, T, rme, e->stream));
+        CK(launch_batch_phases(set.d, T, rme, sh, e->stream, tuning ? set.ph : nullptr));
+    }
+    if (tuning) {
+        set.tune_pending = true;
+        set.tune_me = cme;
+        set.tune_fsr = cfsr;
+        set.me_units = me_units;
+        set.fsr_units = fsr_units;
+        tu.steps++;
     }
     if (prof) CK(cudaEventRecord(set.t1, e->stream));
     CK(cudaEventRecord(set.done, e->stream));
@@ -530,6 +632,7 @@ void rfsr_engine_config_default(rfsr_engine_config *c)
     std::memset(c, 0, sizeof(*c));
     c->device = 0;
     c->max_inflight = 4;
+    c->autotune = 1;
 }
 
 void rfsr_stream_config_default(rfsr_stream_config *c)
@@ -575,6 +678,8 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
             if (set.done) cudaEventDestroy(set.done);
             if (set.t0) cudaEventDestroy(set.t0);
             if (set.t1) cudaEventDestroy(set.t1);
+            for (auto &ev : set.ph)
+                if (ev) cudaEventDestroy(ev);
         }
         if (e->own_stream) cudaStreamDestroy(e->stream);
         delete e;
@@ -596,6 +701,8 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
             if (er == cudaSuccess) er = cudaEventCreateWithFlags(&set.done, cudaEventDisableTiming);
             if (er == cudaSuccess) er = cudaEventCreate(&set.t0);
             if (er == cudaSuccess) er = cudaEventCreate(&set.t1);
+            for (auto &ev : set.ph)
+                if (er == cudaSuccess) er = cudaEventCreate(&ev);
             if (er != cudaSuccess) return bail(er, "batch buffers");
             std::memset(set.h, 0, sizeof(BatchDesc));
         }
@@ -604,6 +711,7 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     cudaError_t er = cudaMemGetInfo(&fr, &tot);
     if (er != cudaSuccess) return bail(er, "cudaMemGetInfo");
     e->budget = cfg->memory_budget ? cfg->memory_budget : (size_t)(0.8 * (double)fr);
+    e->tune.active = batched(e) && cfg->autotune != 0;
     if (cfg->serve) e->server = std::thread(serve_loop, e);
     *out = e;
     return RFSR_OK;
@@ -672,6 +780,8 @@ int rfsr_engine_destroy(rfsr_engine *e)
         if (set.done) cudaEventDestroy(set.done);
         if (set.t0) cudaEventDestroy(set.t0);
         if (set.t1) cudaEventDestroy(set.t1);
+        for (auto &ev : set.ph)
+            if (ev) cudaEventDestroy(ev);
     }
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
@@ -711,6 +821,53 @@ int rfsr_engine_last_step_ms(rfsr_engine *e, float *ms, int *frames)
     CK(cudaEventSynchronize(set->t1));
     CK(cudaEventElapsedTime(ms, set->t0, set->t1));
     if (frames) *frames = nf;
+    return RFSR_OK;
+}
+
+int rfsr_engine_set_shape(rfsr_engine *e, const rfsr_batch_shape *shape)
+{
+    if (!e || !shape) return fail(RFSR_EINVAL, "engine_set_shape: NULL argument");
+    if (!batched(e)) return fail(RFSR_ESTATE, "engine_set_shape: engine is not batched");
+    BatchShape sh;
+    sh.me_warps = shape->me_tile_rows / 8;
+    sh.fsr_blocks = shape->fsr_blocks;
+    if ((shape->me_tile_rows != 32 && shape->me_tile_rows != 64) || !shape_valid(sh))
+        return fail(RFSR_EINVAL, "engine_set_shape: me_tile_rows must be 32 or 64, fsr_blocks 2, 4 or 8");
+    CK(cudaSetDevice(e->cfg.device));
+    std::lock_guard<std::mutex> g(e->mu);
+    for (auto &set : e->sets) {                      // graphs of the old shape go
+        if (set.used) CK(cudaEventSynchronize(set.done));
+        const int rc = harvest_tuning(e, set);
+        if (rc != RFSR_OK) return rc;
+        for (auto &kv : set.graphs) cudaGraphExecDestroy(kv.second);
+        set.graphs.clear();
+        set.graph_kernels.clear();
+    }
+    e->shape = sh;
+    e->tune.active = false;
+    return RFSR_OK;
+}
+
+int rfsr_engine_get_tuning(rfsr_engine *e, rfsr_tuning *out)
+{
+    if (!e || !out) return fail(RFSR_EINVAL, "engine_get_tuning: NULL argument");
+    if (!batched(e)) return fail(RFSR_ESTATE, "engine_get_tuning: engine is not batched");
+    CK(cudaSetDevice(e->cfg.device));
+    std::lock_guard<std::mutex> g(e->mu);
+    for (auto &set : e->sets)                        // fold in measurements that have finished
+        if (set.tune_pending && cudaEventQuery(set.done) == cudaSuccess) {
+            const int rc = harvest_tuning(e, set);
+            if (rc != RFSR_OK) return rc;
+        }
+    const Tuner &tu = e->tune;
+    std::memset(out, 0, sizeof(*out));
+    out->tuned = tu.active ? 0 : 1;
+    out->steps = tu.measured;
+    out->shape.me_tile_rows = 8 * e->shape.me_warps;
+    out->shape.fsr_blocks = e->shape.fsr_blocks;
+    for (int i = 0; i < Tuner::kMe; ++i) out->me_ns[i] = tu.me_n[i] ? (float)(tu.me_ns[i] / tu.me_n[i]) : 0.f;
+    for (int i = 0; i < Tuner::kFsr; ++i)
+        out->fsr_ns[i] = tu.fsr_n[i] ? (float)(tu.fsr_ns[i] / tu.fsr_n[i]) : 0.f;
     return RFSR_OK;
 }
 

@@ -62,7 +62,9 @@ struct FrameTask {
 
 // A batched frame step: up to kMaxBatch frame tasks (one per stream) run by one persistent
 // launch per phase.  Each phase flattens its tiles over the tasks: task i owns the tiles
-// [off[phase][i], off[phase][i+1]) and a CTA finds the task of a tile by binary search.
+// [off[phase][i], off[phase][i+1]).  The tiles of a phase form a queue: CTAs claim them in
+// increasing order with an atomic on the phase's queue head and find the task of a tile by binary
+// search over the offsets.
 constexpr int kMaxBatch = 256;
 enum Phase { kPhIngest = 0, kPhMe = 1, kPhRme = 2, kPhCc = 3, kPhFsr = 4, kPhases = 5 };
 
@@ -74,12 +76,20 @@ struct BatchDesc {
     FrameTask task[kMaxBatch];
 };
 
-// tiles of a task in each phase (the single-stream launches use the same decomposition)
+// Tile shapes of the batched launches.  Every shape computes bit-identical results; they differ
+// only in how the work is cut, so the engine may choose among them by measurement.
+struct BatchShape {
+    int me_warps = 8;                      // ME (T = 9): 8-row warp strips stacked per CTA (4 | 8)
+    int fsr_blocks = 4;                    // FSR: 4x4 blocks (one per warp) per CTA (2 | 4 | 8)
+};
+bool shape_valid(const BatchShape &s);
+
+// tiles of a task in each phase (the single-stream launches use the default shape)
 int tiles_ingest(const FrameTask &t);
-int tiles_me(const FrameTask &t);
+int tiles_me(const FrameTask &t, int me_warps = 8);
 int tiles_rme(const FrameTask &t);
 int tiles_cc(const FrameTask &t);
-int tiles_fsr(const FrameTask &t);         // CTAs of WPB blocks (single-stream launch)
+int tiles_fsr(const FrameTask &t, int fsr_blocks = 4);
 
 // task of flattened tile `tile` of phase ph (binary search over the offsets)
 __device__ __forceinline__ int batch_task(const BatchDesc *bd, int ph, int tile)
@@ -102,14 +112,57 @@ __device__ __forceinline__ void load_task(FrameTask &dst, const FrameTask &src)
     __syncthreads();
 }
 
-// batched launchers: one persistent launch per phase over all tasks of bd (device pointer);
-// the grid sizes depend only on the device, so the sequence can be captured in a CUDA graph
-cudaError_t launch_batch_prologue(const BatchDesc *bd, cudaStream_t st);
-cudaError_t launch_ingest_batched(const BatchDesc *bd, cudaStream_t st);
-cudaError_t launch_me_batched(const BatchDesc *bd, int T, cudaStream_t st);
-cudaError_t launch_rme_batched(const BatchDesc *bd, cudaStream_t st);
-cudaError_t launch_cc_batched(const BatchDesc *bd, int T, cudaStream_t st);
-cudaError_t launch_fsr_batched(const BatchDesc *bd, cudaStream_t st);
+// The claim loop of a CTA-granular batched kernel (all threads of the CTA call it): tiles of
+// phase ph are claimed from the queue in increasing order, the next claim is issued before the
+// current tile's work (its latency overlaps the work), the tile's task is copied to shared memory
+// when it changes, and fn(task, tile index within the task) runs once per claimed tile.  claim is
+// a 2-int shared buffer; a barrier separates consecutive tiles.
+template <typename Fn>
+__device__ __forceinline__ void claim_tiles(BatchDesc *bd, int ph, FrameTask &task, int *claim, Fn &&fn)
+{
+    int *queue = &bd->queue[ph];
+    const int n = bd->ntiles[ph];
+    if (threadIdx.x == 0) claim[0] = atomicAdd(queue, 1);
+    __syncthreads();
+    int cached = -1;
+    for (int it = 0;; ++it) {
+        const int c = claim[it & 1];
+        if (c >= n) break;                             // uniform over the CTA
+        int nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(queue, 1);
+        const int ti = batch_task(bd, ph, c);
+        if (ti != cached) {
+            load_task(task, bd->task[ti]);             // the previous tile ended with a barrier
+            cached = ti;
+        }
+        fn(static_cast<const FrameTask &>(task), c - bd->off[ph][ti]);
+        // slot (it+1)&1 was last read before the previous barrier, so it may be rewritten now
+        if (threadIdx.x == 0) claim[(it + 1) & 1] = nxt;
+        __syncthreads();
+    }
+}
+
+// Resident CTAs per SM x SMs for a batched kernel (its persistent grid).
+template <typename K>
+int persistent_grid(K kernel, int threads, size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1)
+        per = 1;
+    return sms * per;
+}
+
+// batched launchers: one persistent launch per phase over all tasks of bd (device pointer; the
+// kernels advance its queue heads); the grid sizes depend only on the device and the shape, so
+// the sequence can be captured in a CUDA graph
+cudaError_t launch_batch_prologue(BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_ingest_batched(BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, cudaStream_t st);
+cudaError_t launch_rme_batched(BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_cc_batched(BatchDesc *bd, int T, cudaStream_t st);
+cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, cudaStream_t st);
 
 // FSR tables computed on the host (no device transcendentals): spatial weights rho^d over the
 // support, frequency weights over the stored half spectrum and the DFT twiddles.

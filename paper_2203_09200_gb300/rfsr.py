@@ -36,7 +36,7 @@ class RfsrError(RuntimeError):
 class rfsr_engine_config(C.Structure):
     _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
                 ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int),
-                ("serve", C.c_int)]
+                ("serve", C.c_int), ("autotune", C.c_int)]
 
 
 class rfsr_stream_config(C.Structure):
@@ -46,6 +46,15 @@ class rfsr_stream_config(C.Structure):
                 ("fsr_iterations", C.c_int), ("fsr_rho", C.c_float), ("fsr_gamma", C.c_float),
                 ("fsr_proj_weight", C.c_float), ("fsr_overwrite_projected", C.c_int),
                 ("keep_f32", C.c_int)]
+
+
+class rfsr_batch_shape(C.Structure):
+    _fields_ = [("me_tile_rows", C.c_int), ("fsr_blocks", C.c_int)]
+
+
+class rfsr_tuning(C.Structure):
+    _fields_ = [("tuned", C.c_int), ("steps", C.c_int), ("shape", rfsr_batch_shape),
+                ("me_ns", C.c_float * 2), ("fsr_ns", C.c_float * 3)]
 
 
 class rfsr_stream_info(C.Structure):
@@ -64,6 +73,8 @@ SYMBOLS = {
     "rfsr_engine_step": ([_VP], _I),
     "rfsr_engine_sync": ([_VP, _I], _I),
     "rfsr_engine_last_step_ms": ([_VP, C.POINTER(C.c_float), C.POINTER(C.c_int)], _I),
+    "rfsr_engine_set_shape": ([_VP, C.POINTER(rfsr_batch_shape)], _I),
+    "rfsr_engine_get_tuning": ([_VP, C.POINTER(rfsr_tuning)], _I),
     "rfsr_create_stream": ([_VP, C.POINTER(rfsr_stream_config), C.POINTER(_VP)], _I),
     "rfsr_push_frame": ([_VP, _VP, _VP], _I),
     "rfsr_push_frame_device": ([_VP, _VP, _VP], _I),
@@ -148,14 +159,14 @@ class Engine:
 
     def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
                  max_inflight: int = 4, batched: bool = False, profile: bool = False,
-                 serve: bool = False):
+                 serve: bool = False, autotune: bool = True):
         lib = load()
         cfg = rfsr_engine_config()
         lib.rfsr_engine_config_default(C.byref(cfg))
         cfg.device, cfg.memory_budget = device, memory_budget
         cfg.cuda_stream = cuda_stream
         cfg.max_inflight, cfg.batched, cfg.profile = max_inflight, int(batched), int(profile)
-        cfg.serve = int(serve)
+        cfg.serve, cfg.autotune = int(serve), int(autotune)
         h = C.c_void_p()
         _check(lib.rfsr_engine_create(C.byref(cfg), C.byref(h)))
         self.handle = h
@@ -181,6 +192,21 @@ class Engine:
 
     def step(self) -> int:
         return _check(load().rfsr_engine_step(self.handle))
+
+    def set_shape(self, me_tile_rows: int = 64, fsr_blocks: int = 4):
+        """rfsr_engine_set_shape: fix the batched tile shape (ends autotuning)."""
+        sh = rfsr_batch_shape(me_tile_rows, fsr_blocks)
+        _check(load().rfsr_engine_set_shape(self.handle, C.byref(sh)))
+
+    def tuning(self) -> dict:
+        """rfsr_engine_get_tuning as a dict."""
+        t = rfsr_tuning()
+        _check(load().rfsr_engine_get_tuning(self.handle, C.byref(t)))
+        return {"tuned": bool(t.tuned), "steps": t.steps,
+                "shape": {"me_tile_rows": t.shape.me_tile_rows, "fsr_blocks": t.shape.fsr_blocks},
+                "me_ns_per_pixel_ref": {"64": round(t.me_ns[0], 5), "32": round(t.me_ns[1], 5)},
+                "fsr_ns_per_block": {"4": round(t.fsr_ns[0], 3), "2": round(t.fsr_ns[1], 3),
+                                     "8": round(t.fsr_ns[2], 3)}}
 
     def sync(self, timeout_ms: int = -1):
         _check(load().rfsr_engine_sync(self.handle, timeout_ms))

@@ -62,7 +62,37 @@ def test_struct_layouts_match_header(lib):
     assert c.fsr_iterations == 100 and abs(c.fsr_rho - 0.7) < 1e-7 and c.keep_f32 == 0
     e = rfsr.rfsr_engine_config()
     lib.rfsr_engine_config_default(ctypes.byref(e))
-    assert e.max_inflight == 4 and e.batched == 0
+    assert e.max_inflight == 4 and e.batched == 0 and e.autotune == 1
+
+
+def test_struct_sizes_match_a_c_compiler(tmp_path):
+    """sizeof / offsetof of every public struct as a C compiler sees the header, against ctypes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rfsr_engine_config": rfsr.rfsr_engine_config,
+               "rfsr_stream_config": rfsr.rfsr_stream_config,
+               "rfsr_stream_info": rfsr.rfsr_stream_info,
+               "rfsr_batch_shape": rfsr.rfsr_batch_shape,
+               "rfsr_tuning": rfsr.rfsr_tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rfsr.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(out[f"{name}.{fname}"]) == getattr(cls, fname).offset, f"{name}.{fname}"
 
 
 def test_errors_without_gpu_are_loud(lib):

@@ -89,6 +89,53 @@ def test_batched_steps_equal_streams_alone(built):
                     np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PCNT), pcnt)
 
 
+@pytest.mark.parametrize("rows,blocks", [(64, 4), (32, 4), (64, 2), (32, 2), (64, 8), (32, 8)])
+def test_every_batch_shape_equals_streams_alone(built, rows, blocks):
+    """Each tile shape the autotuner can choose gives the same bits as the streams run alone."""
+    F = 4
+    seqs = sequences(F)
+    alone = run_alone(seqs, F, planes=False)
+    with rfsr.Engine(device=0, batched=True, autotune=False) as eng:
+        eng.set_shape(me_tile_rows=rows, fsr_blocks=blocks)
+        assert eng.tuning()["shape"] == {"me_tile_rows": rows, "fsr_blocks": blocks}
+        sts = [eng.create_stream(height=H, width=W, cc_mode=mode, keep_f32=True)
+               for H, W, _, mode, _ in SPECS]
+        for t in range(F):
+            for st, seq in zip(sts, seqs):
+                st.push_frame(seq.samples[t], seq.masks[t])
+            eng.step()
+            for i, st in enumerate(sts):
+                rec, f32 = st.get_frame(timeout_ms=60000, f32=True)
+                np.testing.assert_array_equal(rec, alone[i][t][0], err_msg=f"stream {i} t {t}")
+                np.testing.assert_array_equal(f32, alone[i][t][1], err_msg=f"stream {i} t {t}")
+
+
+def test_autotuner_measures_every_candidate_and_settles(built):
+    F = 12
+    seqs = sequences(F)
+    alone = run_alone(seqs, F, planes=False)
+    with rfsr.Engine(device=0, batched=True) as eng:
+        assert not eng.tuning()["tuned"]
+        sts = [eng.create_stream(height=H, width=W, cc_mode=mode, keep_f32=True)
+               for H, W, _, mode, _ in SPECS]
+        for t in range(F):
+            for st, seq in zip(sts, seqs):
+                st.push_frame(seq.samples[t], seq.masks[t])
+            eng.step()
+            for i, st in enumerate(sts):
+                rec, f32 = st.get_frame(timeout_ms=60000, f32=True)
+                np.testing.assert_array_equal(rec, alone[i][t][0])
+                np.testing.assert_array_equal(f32, alone[i][t][1])
+        tu = eng.tuning()
+        assert tu["tuned"] and tu["steps"] >= 6
+        assert all(v > 0 for v in tu["fsr_ns_per_block"].values())
+        assert all(v > 0 for v in tu["me_ns_per_pixel_ref"].values())
+        assert tu["shape"]["me_tile_rows"] in (32, 64) and tu["shape"]["fsr_blocks"] in (2, 4, 8)
+        with pytest.raises(rfsr.RfsrError) as e:
+            eng.set_shape(me_tile_rows=48)
+        assert e.value.code == rfsr.RFSR_EINVAL
+
+
 def test_batched_streams_join_and_leave(built):
     """Streams start at different steps and leave early; device and host pushes mixed."""
     F = 6
