@@ -76,6 +76,36 @@ def fsr_flops_per_block(iters=ITERS):
     return dft + iters * per_iter
 
 
+# committed ncu summaries: DRAM bytes per launch of a kernel, valid while its sources are unchanged
+CSRC = os.path.join(ROOT, "paper_2203_09200_gb300", "csrc")
+KERNEL_PROFILES = {"fsr_kernel": ("fsr_kernel_1080p.md", ["fsr.cu", "rfsr_internal.h"]),
+                   "me9_kernel": ("me9_kernel_1080p.md", ["me.cu", "rfsr_internal.h"]),
+                   "cc_project_kernel": ("cc_project_kernel_1080p.md", ["cc.cu", "rfsr_internal.h"])}
+
+
+def kernel_source_sha(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_PROFILES[kernel][1]:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """dram__bytes_read.sum + dram__bytes_write.sum of one launch from the kernel's ncu summary in
+    profiles/, or None when there is none or it was taken on other kernel sources."""
+    import re
+    path = os.path.join(ROOT, "profiles", KERNEL_PROFILES[kernel][0])
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    sha = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    tb = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", txt)
+    if not sha or not tb or sha.group(1) != kernel_source_sha(kernel):
+        return None
+    return int(tb.group(1))
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -136,11 +166,12 @@ def crop_history(seq, t, y0, x0, size):
 
 
 def oracle_crop_rate(seq, steps, size=(96, 96), seed=0):
-    """Mpixel/s of the CPU oracle's full frame step on crops of the workload."""
+    """CPU oracle on crops of the workload: (ME+CC+PR Mpixel/s, full-step Mpixel/s, seconds).
+    Each crop runs the oracle's frame step without FSR (the metric's scope) and then in full."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
-    tot = 0.0
+    t_mecc = t_full = 0.0
     px = 0
     for i in range(steps):
         t = 3 + (i % (len(seq) - 3))
@@ -148,10 +179,14 @@ def oracle_crop_rate(seq, steps, size=(96, 96), seed=0):
         x0 = int(rng.integers(0, W - size[1] + 1)) & ~1
         smp, msk, hist = crop_history(seq, t, y0, x0, size)
         t0 = time.perf_counter()
+        oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NNC_FRMC, T=T, R=R, run_fsr=False)
+        t1 = time.perf_counter()
         oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NNC_FRMC, T=T, R=R)
-        tot += time.perf_counter() - t0
+        t2 = time.perf_counter()
+        t_mecc += t1 - t0
+        t_full += t2 - t1
         px += size[0] * size[1]
-    return px / tot / 1e6, tot
+    return px / t_mecc / 1e6, px / t_full / 1e6, t_mecc + t_full
 
 
 def run_reference(args, rank, world):
@@ -160,21 +195,23 @@ def run_reference(args, rank, world):
     seq = synth.config3(F=16)
     size = (48, 48)
     oracle_crop_rate(seq, args.warmup, size, seed=1)
-    rate, tot = oracle_crop_rate(seq, args.steps, size, seed=2)
+    rate, full, tot = oracle_crop_rate(seq, args.steps, size, seed=2)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(rate, 6), "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * tot / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{size[0]}x{size[1]} crop per step"},
+        "config": {"workload": WORKLOAD, "sample": f"{size[0]}x{size[1]} crop per step",
+                   "value_scope": "oracle ME + checks + projection (frame step without FSR)"},
+        "full_step": {"value": round(full, 6), "unit": UNIT},
         "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"full oracle frame step on one {size[0]}x{size[1]} crop "
-                                   "of the 1080p workload per step, single thread"},
+                         "sample": f"oracle frame step on one {size[0]}x{size[1]} crop of the "
+                                   "1080p workload per step (3 past frames), single thread: "
+                                   "without FSR (value), then with FSR (full_step)"},
         "e2e": {"value": round(rate, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
 
 
 SIZES4 = [(240, 320), (480, 640), (720, 1280), (1080, 1920)]
@@ -204,11 +241,23 @@ def crop_streams(base: "synth.VideoSequence", specs, frames):
     return out
 
 
-def run_batching(rfsr, torch, n_streams=64, frames=16):
-    """64 uneven streams: one batched step per round against a per-stream launch loop.  The
-    batched engine's autotuner settles on a calibration pass over the same streams first; the
-    timed pass then runs with the shape it chose (new streams, same engine)."""
-    specs = synth.config4_streams(n_streams=n_streams, frames=frames)
+def small_streams(n_streams=256, frames=16, seed=6):
+    """n streams of 320x240 (the smallest size of the 64-stream mix), half fixed / half dynamic."""
+    rng = np.random.default_rng(seed)
+    return [synth.StreamSpec(240, 320, synth.MASK_FIXED if i < n_streams // 2 else synth.MASK_DYNAMIC,
+                             frames, int(rng.integers(0, 2 ** 31 - 1))) for i in range(n_streams)]
+
+
+def run_batching(rfsr, torch, specs=None, frames=16, what=None):
+    """Many streams: one batched step per round against a per-stream launch loop (both with
+    device-resident inputs, the same frames, bit-identical outputs).  The batched engine's
+    autotuner settles on a calibration pass over the same streams first; the timed pass then
+    runs with the shape it chose (new streams, same engine)."""
+    if specs is None:
+        specs = synth.config4_streams(n_streams=64, frames=frames)
+        what = ("64 streams, sizes from 320x240/640x480/1280x720/1920x1080, half fixed / half "
+                "dynamic masks")
+    n_streams = len(specs)
     base = synth.config2(seed=44, H=1080, W=1920, F=frames)
     streams = crop_streams(base, specs, frames)
     d_in = [[(torch.from_numpy(s).cuda(), torch.from_numpy(m).cuda()) for s, m in zip(smp, msk)]
@@ -250,9 +299,8 @@ def run_batching(rfsr, torch, n_streams=64, frames=16):
                      "launches_per_round": round((rfsr.kernel_launches() - launches0) / frames, 1)}
         eng.destroy()
     res["speedup"] = round(res["batched"]["mpix_s"] / res["loop"]["mpix_s"], 3)
-    res["workload"] = (f"{n_streams} streams, sizes from 320x240/640x480/1280x720/1920x1080, half fixed "
-                       f"/ half dynamic masks, {frames} frames each, band-limited panned texture + "
-                       f"moving rectangles (crops of one sequence), device-resident inputs; timed "
+    res["workload"] = (f"{what}, {frames} frames each, band-limited panned texture + moving "
+                       f"rectangles (crops of one 1080p sequence), device-resident inputs; timed "
                        f"rounds 3..{frames - 1} (3 past frames)")
     return res
 
@@ -394,8 +442,14 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     ph = np.array(phases)                       # (steps, 4): ingest, ME, checks+PR, FSR
     ph_mean = ph.mean(axis=0)
+    mecc_s = float(ph[:, :3].sum()) / 1e3       # ingest + ME + checks + projection, all steps
+    if world > 1:
+        t = torch.tensor([mecc_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mecc_s = float(t.item())
     frames_total = args.steps * world
-    value = frames_total * HW / tot_s / 1e6
+    value = frames_total * HW / mecc_s / 1e6    # the metric: ME+CC+projection
+    full_value = frames_total * HW / tot_s / 1e6
 
     # e2e: host buffers through the public API, copies inside the timed region
     st2 = eng.create_stream(height=H, width=W, cc_mode="nnc_frmc", template_size=T,
@@ -425,6 +479,8 @@ def run_ours(args, rank, world, local_rank):
     batching = serving = None
     if not args.no_serving:
         batching = run_batching(rfsr, torch)
+        batching["small_frames"] = run_batching(
+            rfsr, torch, small_streams(), what="256 streams of 320x240, half fixed / half dynamic masks")
         serving = run_serving(rfsr, torch)
 
     if rank != 0:
@@ -440,9 +496,10 @@ def run_ours(args, rank, world, local_rank):
             "fsr": (fsr_flops / fsr_s / 1e12, fp32_peak / 1e12, "TFLOP/s (fp32)")}
     dom = "me" if me_s >= fsr_s else "fsr"
     ach, peak, unit = kern[dom]
-    roof = {"kernel": {"me": "me_kernel", "fsr": "fsr_kernel"}[dom], "bound": "alu",
+    roof = {"kernel": {"me": "me9_kernel", "fsr": "fsr_kernel"}[dom], "bound": "alu",
             "achieved": round(ach, 3), "peak": round(peak, 3), "unit": unit,
-            "frac": round(ach / peak, 4), "traffic": None,
+            "frac": round(ach / peak, 4),
+            "traffic": profiled_traffic({"me": "me9_kernel", "fsr": "fsr_kernel"}[dom]),
             "peak_source": f"derived: {SMS} SMs x "
                            f"{INT32_LANES_PER_SM if dom == 'me' else FP32_LANES_PER_SM * 2} "
                            f"ops/clk x {mhz:.0f} MHz ({src} max clock)",
@@ -450,35 +507,103 @@ def run_ours(args, rank, world, local_rank):
                           "frac": round(v[0] / v[1], 4)} for k, v in kern.items() if k != dom}}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, tot = oracle_crop_rate(seq, 8, (96, 96), seed=5)
+        rate, full, tot = oracle_crop_rate(seq, 8, (96, 96), seed=5)
         cpu = {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"full oracle frame step (ME+CC+PR+FSR, NNC+FRMC) on eight 96x96 crops of "
-                         f"frames 3..10 of the 1080p workload with 3 past frames each, {tot:.1f} s "
-                         "on one host core"}
+               "full_step_value": round(full, 6),
+               "sample": f"oracle frame step (NNC+FRMC) on eight 96x96 crops of frames 3..10 of "
+                         f"the 1080p workload with 3 past frames each: ME+CC+PR alone (value), "
+                         f"then with FSR (full_step_value); {tot:.1f} s on one host core"}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * tot_s / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "value_scope": "full frame step (ingest, ME, checks, "
-                   "projection, FSR, 8-bit reconstruction) per HR pixel",
+        "config": {"workload": WORKLOAD, "value_scope": "ingest + ME + checks + projection: device "
+                   "time between the phase events of each timed full frame step (same stream); "
+                   "ms_per_step and full_step cover the whole step with FSR",
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "breakdown": {"ingest_ms": round(ph_mean[0], 4), "me_ms": round(ph_mean[1], 4),
                       "cc_pr_ms": round(ph_mean[2], 4), "fsr_ms": round(ph_mean[3], 4),
-                      "me_cc_pr_mpix_s": round(HW / ((ph_mean[0] + ph_mean[1] + ph_mean[2]) / 1e3)
-                                               / 1e6, 3),
                       "wall_ms_per_step": round(1e3 * wall / args.steps, 4)},
+        "full_step": {"value": round(full_value, 3), "unit": UNIT,
+                      "scope": "ingest, ME, checks, projection, FSR, 8-bit reconstruction"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": 2 * HW,
-                "d2h_bytes_per_step": HW},
+                "d2h_bytes_per_step": HW,
+                "scope": "full frame step through rfsr_push_frame / rfsr_get_frame with host "
+                         "buffers (copies inside the timed region); the public stream API always "
+                         "runs the whole step, so this is the full-step metric"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "batching": batching,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
+
+
+def summarize_launches(path):
+    """Markdown table of an ncu launch list (--metrics gpu__time_duration.sum --csv): launches,
+    total and mean device time and share of each kernel."""
+    import collections
+    import csv
+    rows = list(csv.reader(open(path)))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, vi, ui = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Unit")
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0}
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi:
+            continue
+        name = r[ki].split("(")[0]
+        for pre in ("rfsr::<unnamed>::", "<unnamed>::", "unnamed>::", "rfsr::", "void "):
+            name = name.replace(pre, "")
+        agg[name][0] += 1
+        agg[name][1] += float(r[vi].replace(",", "")) * scale[r[ui]]
+    tot = sum(v[1] for v in agg.values())
+    out = ["| kernel | launches | total ms | mean ms | share |", "|---|---|---|---|---|"]
+    for n, (c, t) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        out.append(f"| {n[:70]} | {c} | {t:.3f} | {t / c:.3f} | {100 * t / tot:.1f}% |")
+    return "\n".join(out)
+
+
+def run_ncu_case(args):
+    """A short, untimed kernel sequence for an ncu capture: 'frame_step' runs `frames` frames of
+    the 1080p workload on one unbatched stream (device-resident inputs); 'batched' runs `frames`
+    batched steps of the 64-stream mix (default tile shape, no autotuning)."""
+    import torch
+    from paper_2203_09200_gb300 import build as pbuild
+    from paper_2203_09200_gb300 import rfsr
+    torch.cuda.set_device(0)
+    pbuild.build()
+    nf = args.frames
+    if args.ncu_case == "frame_step":
+        seq = synth.config3(seed=3, F=nf)
+        d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
+        with rfsr.Engine(device=0) as eng:
+            st = eng.create_stream(height=H, width=W, cc_mode="nnc_frmc", template_size=T,
+                                   search_radius=R, num_refs=KREF, fsr_iterations=ITERS)
+            for f in range(nf):
+                st.push_frame_device(d_smp[f], d_msk[f])
+                st.get_frame_device(timeout_ms=120000)
+    else:
+        specs = synth.config4_streams(n_streams=64, frames=nf)
+        streams = crop_streams(synth.config2(seed=44, H=1080, W=1920, F=nf), specs, nf)
+        d_in = [[(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in zip(sm, mk)]
+                for _, sm, mk in streams]
+        with rfsr.Engine(device=0, batched=True, autotune=False) as eng:
+            sts = [eng.create_stream(height=sp.H, width=sp.W, mask_type=sp.mask_type)
+                   for sp, _, _ in streams]
+            for f in range(nf):
+                for i, st in enumerate(sts):
+                    st.push_frame_device(*d_in[i][f])
+                eng.step()
+                for st in sts:
+                    st.get_frame_device(timeout_ms=120000)
+    torch.cuda.synchronize()
+    print(f"ncu case {args.ncu_case}: {nf} frames done", flush=True)
 
 
 def main():
@@ -490,7 +615,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the batching and serving measurements")
+    ap.add_argument("--ncu-case", choices=["frame_step", "batched"],
+                    help="run only a short untimed kernel sequence (for ncu captures)")
+    ap.add_argument("--frames", type=int, default=6, help="frames of --ncu-case")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="print the per-kernel table of an ncu launch list and exit")
     args = ap.parse_args()
+    if args.summarize_launches:
+        print(summarize_launches(args.summarize_launches))
+        return
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

@@ -27,7 +27,9 @@
 //   * Selection: one pass per lane keeps its maximum and the R value there, the warp maximum
 //     comes from __reduce_max_sync on the (non-negative) float bits and the lowest canonical index
 //     among the lanes that reach it from __reduce_min_sync; the owner lane's R value arrives by one
-//     shuffle pair.  The rank-2 residual update is eight fused multiply-adds per bin.
+//     shuffle pair.  The rank-2 residual update works on (Re, Im) as packed FP32 pairs
+//     (R -= dr (a + c) + di (c.y - a.y, a.x - c.x)): one pair add, two scalar subtractions and two
+//     pair FMAs per bin.
 //   * The per-warp shared memory is one 12.5 KB union (support, row spectra, W).
 #include <cmath>
 #include <type_traits>
@@ -276,14 +278,13 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
 
     // 4. lane k takes R(k, 0..16) into registers; W goes to the full padded layout
     const int k = lane;
-    float Rre[NH], Rim[NH];
+    float2 Rr[NH];                                     // (Re, Im) of R(k, l)
     {
         float2 Wt[NH];
 #pragma unroll
         for (int l = 0; l < NH; ++l) {
             const float2 r = ws.dft.f[k * NH + l];
-            Rre[l] = r.x;
-            Rim[l] = r.y;
+            Rr[l] = r;
             Wt[l] = ws.dft.w[k * NH + l];
         }
         __syncwarp();
@@ -325,11 +326,11 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
         int bl = -1;
 #pragma unroll
         for (int l = 0; l < NH; ++l) {
-            const float e = wfr[l] * fmaf(Rre[l], Rre[l], Rim[l] * Rim[l]);
+            const float e = wfr[l] * fmaf(Rr[l].x, Rr[l].x, Rr[l].y * Rr[l].y);
             const bool take = (int)(__float_as_uint(e) + bias) > (int)__float_as_uint(be);
             be = take ? e : be;
-            sr = take ? Rre[l] : sr;
-            si = take ? Rim[l] : si;
+            sr = take ? Rr[l].x : sr;
+            si = take ? Rr[l].y : si;
             bl = take ? l : bl;
         }
         const float m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(be)));
@@ -354,26 +355,18 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
         // W(k-u) at column l - u_l + 32, W(k+u) at column l + u_l of the wrapped rows
         const float2 *pa = ws.W + ((k - uk) & (N - 1)) * WS + (N - ul);
         const float2 *pc = ws.W + ((k + uk) & (N - 1)) * WS + ul;
+        // packed FP32 pairs: R -= dr (a + c) + di (c.y - a.y, a.x - c.x), or R -= dr a (self)
+        const float2 ndr = make_float2(-dr, -dr), ndi = make_float2(-di, -di);
         if (self) {
 #pragma unroll
-            for (int l = 0; l < NH; ++l) {
-                const float2 a = pa[l];
-                Rre[l] = fmaf(-dr, a.x, Rre[l]);
-                Rim[l] = fmaf(-dr, a.y, Rim[l]);
-            }
+            for (int l = 0; l < NH; ++l) Rr[l] = __ffma2_rn(ndr, pa[l], Rr[l]);
         } else {
 #pragma unroll
             for (int l = 0; l < NH; ++l) {
                 const float2 a = pa[l], c = pc[l];
-                // R -= dc * a + conj(dc) * c
-                float xr = fmaf(-dr, a.x, Rre[l]);
-                xr = fmaf(di, a.y, xr);
-                xr = fmaf(-dr, c.x, xr);
-                Rre[l] = fmaf(-di, c.y, xr);
-                float xi = fmaf(-dr, a.y, Rim[l]);
-                xi = fmaf(-di, a.x, xi);
-                xi = fmaf(-dr, c.y, xi);
-                Rim[l] = fmaf(di, c.x, xi);
+                const float2 s = __fadd2_rn(a, c);
+                const float2 q = make_float2(c.y - a.y, a.x - c.x);
+                Rr[l] = __ffma2_rn(ndi, q, __ffma2_rn(ndr, s, Rr[l]));
             }
         }
         // model at the block pixel of this lane: g += (1 or 2) Re(dc phi_u)
