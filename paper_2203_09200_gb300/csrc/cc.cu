@@ -41,23 +41,91 @@ constexpr int NW = NT / 32;                   // warps per CTA
 constexpr int HC = 16;                        // staged halo: |d| <= 9 plus template half <= 5,
                                               // rounded up so the region starts word aligned
 constexpr int RS = TP + 2 * HC;               // staged region side (64)
-constexpr int RWD = RS / 4 + 1;               // words per staged row (+1 feeds the shifted copies)
+constexpr int NWD = RS / 4 + 1;               // data words per staged row (+1 feeds the shifted copies)
+constexpr int RWD = NWD;                      // past frame: row stride (words)
+constexpr int CPY = RS * RWD + 8;             // past frame: words per shifted copy
+// Current frame (the templates the reverse checks slide): row stride 26 and copy stride 3 (mod
+// 32) words.  With the FRMC lane order below, the 32 lanes of a warp, each scoring one offset d
+// of the same pixel, then read 32 distinct banks for every template word.
+constexpr int RWDC = 26;
+constexpr int CPYC = RS * RWDC + 3;
 constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +- 9)
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
-constexpr int CPY = RS * RWD + 8;             // words per shifted copy; the pad puts the four
-                                              // copies of a word in different banks
+
+// FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
+__host__ __device__ constexpr int frmc_offset(int i)
+{
+    return i == 3 ? 0 : (i < 3 ? -((1 << (3 - i)) - 1) : (1 << (i - 3)) - 1);
+}
+
+// Lane order of the 49 FRMC candidates (index 7 iy + ix) in two rounds of 32 lanes, per column
+// phase (px + HC - h) & 3 of the checked pixel; 255 = no candidate.  The centre d = 0 comes first
+// (lane 0 of round 0).  A candidate goes to round 0 unless its bank -- (copy, row, word) of its
+// template start in the current-frame layout -- is taken there already.
+struct FrmcOrder {
+    uint8_t lane[4][2][32];
+};
+
+__host__ __device__ constexpr int frmc_bank(int c, int ph)
+{
+    const int v = ph + frmc_offset(c % 7), dy = frmc_offset(c / 7);
+    return ((((v & 3) * CPYC + dy * RWDC + (v >> 2)) % 32) + 32) % 32;
+}
+
+__host__ __device__ constexpr FrmcOrder build_frmc_order()
+{
+    FrmcOrder o{};
+    for (int ph = 0; ph < 4; ++ph) {
+        bool taken[32] = {};
+        int n[2] = {0, 0};
+        for (int i = 0; i < 2; ++i)
+            for (int l = 0; l < 32; ++l) o.lane[ph][i][l] = 255;
+        for (int k = 0; k < 49; ++k) {
+            const int c = (k + 24) % 49;                   // the centre (24) first
+            const int b = frmc_bank(c, ph), rd = taken[b] ? 1 : 0;
+            taken[b] = true;
+            if (n[rd] < 32) o.lane[ph][rd][n[rd]++] = (uint8_t)c;
+        }
+    }
+    return o;
+}
+
+// every candidate placed, and the candidates of each round in distinct banks
+__host__ __device__ constexpr bool frmc_order_conflict_free(const FrmcOrder &o)
+{
+    for (int ph = 0; ph < 4; ++ph) {
+        int placed = 0;
+        for (int rd = 0; rd < 2; ++rd) {
+            bool seen[32] = {};
+            for (int l = 0; l < 32; ++l) {
+                const int c = o.lane[ph][rd][l];
+                if (c == 255) continue;
+                ++placed;
+                if (seen[frmc_bank(c, ph)]) return false;
+                seen[frmc_bank(c, ph)] = true;
+            }
+        }
+        if (placed != 49 || o.lane[ph][0][0] != 24) return false;
+    }
+    return true;
+}
+
+__constant__ FrmcOrder c_frmc_order = build_frmc_order();
+static_assert(frmc_order_conflict_free(build_frmc_order()), "FRMC lane order has bank conflicts");
+static_assert(sizeof(FrmcOrder) == NT, "the order table is staged one byte per thread");
 
 struct Smem {
-    uint32_t cs[4 * CPY];         // masked samples, byte-shifted copies
-    uint32_t cm[4 * CPY];         // byte masks, byte-shifted copies
+    uint32_t cs[4 * CPYC];        // masked samples, byte-shifted copies
+    uint32_t cm[4 * CPYC];        // byte masks, byte-shifted copies
     uint32_t rf[4 * CPY];         // past frame (clamped coordinates), byte-shifted copies
     uint8_t nsrc[NS][NS];         // measured pixels in the template around each source
     char2 mv[MT][MT];
     char2 md[MD][MD];
     uint16_t list[TP * TP];       // tile pixels that need a reverse check
     uint8_t rej[TP * TP];
+    FrmcOrder ford;
     int nlist;
 };
 
@@ -85,20 +153,15 @@ __device__ __forceinline__ int median9(int p0, int p1, int p2, int p3, int p4, i
     return med3(lo, med3(p1, p4, p7), hi);
 }
 
-// FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
-__device__ __forceinline__ int frmc_offset(int i)
-{
-    return i == 3 ? 0 : (i < 3 ? -((1 << (3 - i)) - 1) : (1 << (i - 3)) - 1);
-}
-
 // Stage a frame region (rows y0-HC.., cols x0-HC..) into four byte-shifted copies: copy j, word w
-// of a row holds region bytes 4w+j .. 4w+j+3.  MODE 0: masked samples and 1: byte mask (both 0
-// outside the frame); MODE 2: past frame with clamped coordinates.
-template <int MODE>
+// of a row holds region bytes 4w+j .. 4w+j+3 (row stride RW, copy stride CP words).  MODE 0:
+// masked samples and 1: byte mask (both 0 outside the frame); MODE 2: past frame with clamped
+// coordinates.
+template <int MODE, int RW, int CP>
 __device__ void stage(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
 {
-    for (int i = threadIdx.x; i < RS * RWD; i += NT) {
-        const int r = i / RWD, w = i - r * RWD;
+    for (int i = threadIdx.x; i < RS * NWD; i += NT) {
+        const int r = i / NWD, w = i - r * NWD;
         const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
         uint32_t v = 0;
         if (MODE == 2) {
@@ -115,14 +178,14 @@ __device__ void stage(uint32_t *dst, const uint8_t *__restrict__ src, int H, int
                     v |= (uint32_t)(*reinterpret_cast<const uint16_t *>(row + x)) << (8 * b);
             }
         }
-        dst[r * RWD + w] = v;
+        dst[r * RW + w] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * RS * (RWD - 1); i += NT) {
-        const int j = 1 + i / (RS * (RWD - 1));
-        const int rem = i - (j - 1) * RS * (RWD - 1);
-        const int r = rem / (RWD - 1), w = rem - r * (RWD - 1);
-        dst[j * CPY + r * RWD + w] = __funnelshift_r(dst[r * RWD + w], dst[r * RWD + w + 1], 8 * j);
+    for (int i = threadIdx.x; i < 3 * RS * (NWD - 1); i += NT) {
+        const int j = 1 + i / (RS * (NWD - 1));
+        const int rem = i - (j - 1) * RS * (NWD - 1);
+        const int r = rem / (NWD - 1), w = rem - r * (NWD - 1);
+        dst[j * CP + r * RW + w] = __funnelshift_r(dst[r * RW + w], dst[r * RW + w + 1], 8 * j);
     }
 }
 
@@ -138,8 +201,8 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     int acc = 0;
 #pragma unroll
     for (int r = 0; r < T; ++r) {
-        const uint32_t *cs = sm.cs + j * CPY + (sy + r) * RWD + w;
-        const uint32_t *cm = sm.cm + j * CPY + (sy + r) * RWD + w;
+        const uint32_t *cs = sm.cs + j * CPYC + (sy + r) * RWDC + w;
+        const uint32_t *cm = sm.cm + j * CPYC + (sy + r) * RWDC + w;
         acc += __vsadu4(cs[0] & w0, P[r][0] & cm[0] & w0);
         if (w1) acc += __vsadu4(cs[1] & w1, P[r][1] & cm[1] & w1);
         if (w2) acc += __vsadu4(cs[2] & w2, P[r][2] & cm[2] & w2);
@@ -160,8 +223,9 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
     const bool rmc = t.cc_mode == 2;
     const bool rme = t.cc_mode == 1;
 
-    stage<0>(sm.cs, t.cur_smp, H, W, y0, x0);
-    stage<1>(sm.cm, t.cur_msk, H, W, y0, x0);
+    stage<0, RWDC, CPYC>(sm.cs, t.cur_smp, H, W, y0, x0);
+    stage<1, RWDC, CPYC>(sm.cm, t.cur_msk, H, W, y0, x0);
+    reinterpret_cast<uint8_t *>(&sm.ford)[tid] = reinterpret_cast<const uint8_t *>(&c_frmc_order)[tid];
     __syncthreads();
     // template counts n around every source position of the tile +- 9 (current mask, 0 outside)
     for (int i = tid; i < NS * NS; i += NT) {
@@ -169,7 +233,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         const int ry = sy + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
         int n = 0;
         for (int r = 0; r < T; ++r) {
-            const uint32_t *cm = sm.cm + (rx & 3) * CPY + (ry + r) * RWD + (rx >> 2);
+            const uint32_t *cm = sm.cm + (rx & 3) * CPYC + (ry + r) * RWDC + (rx >> 2);
 #pragma unroll
             for (int b = 0; b < (T + 3) / 4; ++b) {
                 uint32_t m = cm[b];
@@ -193,7 +257,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             sm.mv[r][c] = mvk[(size_t)gy * W + gx];
         }
         if (tid == 0) sm.nlist = 0;
-        if (frmc || rmc) stage<2>(sm.rf, t.ref_rec[k], H, W, y0, x0);
+        if (frmc || rmc) stage<2, RWD, CPY>(sm.rf, t.ref_rec[k], H, W, y0, x0);
         __syncthreads();
         if (use_nnc) {
             for (int i = tid; i < MD * MD; i += NT) {
@@ -239,7 +303,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             const size_t gi = (size_t)y * W + x;
             reinterpret_cast<char2 *>(t.fmv[k])[gi] = make_char2((signed char)fy, (signed char)fx);
             const int qy = y + fy, qx = x + fx;
-            const uint32_t mword = sm.cm[(py + HC) * RWD + ((px + HC) >> 2)];
+            const uint32_t mword = sm.cm[(py + HC) * RWDC + ((px + HC) >> 2)];
             const bool measured = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
             if (measured) {
                 dec[i] = 0;
@@ -284,13 +348,21 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             }
             int s0 = 0, n0 = 0;
             bool rej = false;
-            // candidate order starts at d = 0 (lane 0 of the first round)
-            for (int c0 = 0; c0 < ncand; c0 += 32) {
-                const int ci = c0 + lane;
+            // round 0, lane 0 scores d = 0; FRMC takes the bank-spread lane order of its phase
+            const int ph = (px + HC - h) & 3;
+            const int nround = frmc ? 2 : (ncand + 31) / 32;
+            for (int rd = 0; rd < nround; ++rd) {
+                int cc = -1;                               // candidate, row-major in the window
+                if (frmc) {
+                    const int e = sm.ford.lane[ph][rd][lane];
+                    cc = e == 255 ? -1 : e;
+                } else {
+                    const int ci = 32 * rd + lane;
+                    if (ci < ncand) cc = ci + centre < ncand ? ci + centre : ci + centre - ncand;
+                }
                 int s = 0, n = 0;
                 bool valid = false;
-                if (ci < ncand) {
-                    const int cc = ci + centre < ncand ? ci + centre : ci + centre - ncand;
+                if (cc >= 0) {
                     const int dy = frmc ? frmc_offset(cc / 7) : cc / side - t.Rc;
                     const int dx = frmc ? frmc_offset(cc % 7) : cc % side - t.Rc;
                     const int sy = y0 + py + dy, sx = x0 + px + dx;
@@ -300,7 +372,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                         valid = true;
                     }
                 }
-                if (c0 == 0) {
+                if (rd == 0) {
                     s0 = __shfl_sync(0xffffffffu, s, 0);
                     n0 = __shfl_sync(0xffffffffu, n, 0);
                     if (lane == 0) valid = false;
