@@ -305,7 +305,39 @@ def run_batching(rfsr, torch, specs=None, frames=16, what=None):
     return res
 
 
-def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=5):
+MODES = ("rme", "rmc", "frmc", "nnc", "nnc_frmc", "none")
+
+
+def run_check_modes(rfsr, torch, steps=8):
+    """The 1280x720 dynamic-mask recipe under each consistency-check mode: device time of ME and
+    of checks + projection (with the RME reverse field), the ME+CC+PR throughput and the fraction
+    of missing pixels that receive a projection, over frames with 3 past frames."""
+    seq = synth.config2(seed=2, F=3 + steps)
+    h, w = seq.shape
+    d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
+    out = {}
+    for mode in MODES:
+        with rfsr.Engine(device=torch.cuda.current_device(), profile=True) as eng:
+            st = eng.create_stream(height=h, width=w, cc_mode=mode, template_size=T,
+                                   search_radius=R, num_refs=KREF)
+            ph, proj = [], []
+            for f in range(3 + steps):
+                st.push_frame_device(d_smp[f], d_msk[f])
+                st.get_frame_device(timeout_ms=120000)
+                if f >= 3:
+                    ph.append(st.phase_ms())
+                    miss = seq.masks[f] == 0
+                    proj.append(float((st.debug_get(rfsr.DBG_PCNT)[miss] > 0).mean()))
+            a = np.array(ph).mean(axis=0)
+            out[mode] = {"me_ms": round(float(a[1]), 4), "cc_pr_ms": round(float(a[2]), 4),
+                         "me_cc_pr_mpix_s": round(h * w / ((a[0] + a[1] + a[2]) / 1e3) / 1e6, 3),
+                         "projected_frac": round(float(np.mean(proj)), 4)}
+    out["workload"] = (f"1280x720 dynamic-mask recipe (band-limited pan + 4 rectangles), K=3, "
+                       f"T=9, R=Rc=8, frames 3..{2 + steps}, device-resident inputs, one stream")
+    return out
+
+
+def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=5, memory_budget=0):
     """Poisson arrivals on a serving engine, closed loop with <= 2 frames in flight per stream:
     per-frame latency (push returned -> result collected) and aggregate throughput."""
     import time as _t
@@ -330,7 +362,9 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             cls[(H, W, mt)] = (sm, ms)
     masks = {i: cls[(a.spec.H, a.spec.W, a.spec.mask_type)][1] for i, a in enumerate(arr)}
     samples = {i: cls[(a.spec.H, a.spec.W, a.spec.mask_type)][0] for i, a in enumerate(arr)}
-    eng = rfsr.Engine(device=torch.cuda.current_device(), serve=True, max_inflight=2)
+    eng = rfsr.Engine(device=torch.cuda.current_device(), serve=True, max_inflight=2,
+                      memory_budget=memory_budget)
+    n_queued, max_queue = 0, 0
     active, lat, done_px = {}, [], 0
     nxt = 0
     t_start = _t.perf_counter()
@@ -345,6 +379,8 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
                 active[nxt] = [st, 0, []]
             else:
                 queued.append((nxt, st))
+                n_queued += 1
+                max_queue = max(max_queue, len(queued))
             nxt += 1
         for q in list(queued):
             if q[1].live:
@@ -376,11 +412,14 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
             "mpix_s": round(done_px / wall / 1e6, 3), "frames": int(len(lat)),
             "wall_s": round(wall, 2),
+            "memory_budget": memory_budget or "80% of free device memory",
+            "streams_queued": n_queued, "max_queue": max_queue,
             "workload": (f"{n_streams} streams arriving Poisson at {rate_hz:g}/s, sizes "
                          "320x240..3840x2160, fixed or dynamic mask 50/50, 1/f^2 texture + "
                          f"moving objects, frames U{{30..300}} x {frame_scale:g}, closed loop "
                          "with <= 2 frames in flight per stream, host buffers, serving engine "
                          "(continuous batching, memory admission)")}
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -476,12 +515,14 @@ def run_ours(args, rank, world, local_rank):
     e2e = frames_total * HW / e_s / 1e6
     eng.destroy()
     del d_smp, d_msk, flush
-    batching = serving = None
+    batching = serving = check_modes = None
     if not args.no_serving:
         batching = run_batching(rfsr, torch)
         batching["small_frames"] = run_batching(
             rfsr, torch, small_streams(), what="256 streams of 320x240, half fixed / half dynamic masks")
         serving = run_serving(rfsr, torch)
+        serving["budget_2gb"] = run_serving(rfsr, torch, memory_budget=2 << 30)
+        check_modes = run_check_modes(rfsr, torch)
 
     if rank != 0:
         return
@@ -539,6 +580,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "batching": batching,
         "serving": serving,
+        "check_modes": check_modes,
     }
     print(json.dumps(line), flush=True)
 

@@ -240,8 +240,9 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
                     uint8_t *d_out_u8, void *cuda_stream);
 
 /* Device time of the phases of the most recently pushed frame of s (waits for it), measured with
- * CUDA events on the engine's stream around each kernel: ms[0] ingest, ms[1] motion estimation
- * (and the RME reverse field), ms[2] checks + projection, ms[3] FSR + 8-bit reconstruction.
+ * CUDA events on the engine's stream around each kernel: ms[0] ingest, ms[1] motion estimation,
+ * ms[2] consistency checks (with the RME reverse field) + projection, ms[3] FSR + 8-bit
+ * reconstruction.
  * Needs an engine created with profile = 1 (else ESTATE). */
 int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4]);
 

@@ -60,61 +60,92 @@ __host__ __device__ constexpr int frmc_offset(int i)
     return i == 3 ? 0 : (i < 3 ? -((1 << (3 - i)) - 1) : (1 << (i - 3)) - 1);
 }
 
-// Lane order of the 49 FRMC candidates (index 7 iy + ix) in two rounds of 32 lanes, per column
-// phase (px + HC - h) & 3 of the checked pixel; 255 = no candidate.  The centre d = 0 comes first
-// (lane 0 of round 0).  A candidate goes to round 0 unless its bank -- (copy, row, word) of its
-// template start in the current-frame layout -- is taken there already.
-struct FrmcOrder {
-    uint8_t lane[4][2][32];
-};
+// Lane order of the reverse-check candidates.  Candidates are indexed row-major in their window
+// (FRMC: 7 iy + ix over the offsets above; RMC: side iy + ix, d = (iy - Rc, ix - Rc)).  For each
+// column phase (px + HC - h) & 3 of the checked pixel they are dealt into rounds of 32 lanes so
+// that no two candidates of a round start their template word in the same bank of the
+// current-frame layout: taken in increasing |d|_1 (row-major within a distance), the i-th
+// candidate of bank b goes to round i.  A round then reads every template word in one
+// shared-memory wavefront; the centre d = 0 is lane 0 of round 0, and the nearest offsets -- the
+// likeliest to beat it when the vector is wrong -- fill round 0, so rejections end early.
+constexpr int MAXROUND = 16;                  // RMC with Rc = 9 needs 14
+constexpr uint16_t NOCAND = 0xffff;
+constexpr int NORDER = 1 + kMaxRadius;        // FRMC, then RMC with Rc = 1..9
 
-__host__ __device__ constexpr int frmc_bank(int c, int ph)
+struct alignas(16) CandOrder {            // copied to shared memory in 16-byte words
+    uint16_t lane[4][MAXROUND][32];
+    uint32_t nround[4];
+};
+static_assert(sizeof(CandOrder) % 16 == 0, "CandOrder is copied in 16-byte words");
+
+__host__ __device__ constexpr int cand_dy(int c, bool frmc, int Rc)
 {
-    const int v = ph + frmc_offset(c % 7), dy = frmc_offset(c / 7);
+    return frmc ? frmc_offset(c / 7) : c / (2 * Rc + 1) - Rc;
+}
+
+__host__ __device__ constexpr int cand_dx(int c, bool frmc, int Rc)
+{
+    return frmc ? frmc_offset(c % 7) : c % (2 * Rc + 1) - Rc;
+}
+
+constexpr int cand_bank(int c, int ph, bool frmc, int Rc)
+{
+    const int v = ph + cand_dx(c, frmc, Rc), dy = cand_dy(c, frmc, Rc);
     return ((((v & 3) * CPYC + dy * RWDC + (v >> 2)) % 32) + 32) % 32;
 }
 
-__host__ __device__ constexpr FrmcOrder build_frmc_order()
+constexpr void build_order(CandOrder &o, bool frmc, int Rc)
 {
-    FrmcOrder o{};
+    const int side = frmc ? 7 : 2 * Rc + 1, n = side * side, lmax = frmc ? 14 : 2 * Rc;
     for (int ph = 0; ph < 4; ++ph) {
-        bool taken[32] = {};
-        int n[2] = {0, 0};
-        for (int i = 0; i < 2; ++i)
-            for (int l = 0; l < 32; ++l) o.lane[ph][i][l] = 255;
-        for (int k = 0; k < 49; ++k) {
-            const int c = (k + 24) % 49;                   // the centre (24) first
-            const int b = frmc_bank(c, ph), rd = taken[b] ? 1 : 0;
-            taken[b] = true;
-            if (n[rd] < 32) o.lane[ph][rd][n[rd]++] = (uint8_t)c;
-        }
+        uint8_t taken[32] = {}, fill[MAXROUND] = {};
+        for (int r = 0; r < MAXROUND; ++r)
+            for (int l = 0; l < 32; ++l) o.lane[ph][r][l] = NOCAND;
+        uint32_t nr = 0;
+        for (int L = 0; L <= lmax; ++L)
+            for (int c = 0; c < n; ++c) {
+                const int dy = cand_dy(c, frmc, Rc), dx = cand_dx(c, frmc, Rc);
+                if ((dy < 0 ? -dy : dy) + (dx < 0 ? -dx : dx) != L) continue;
+                const int b = cand_bank(c, ph, frmc, Rc), r = taken[b]++;
+                o.lane[ph][r][fill[r]++] = (uint16_t)c;
+                nr = (uint32_t)r + 1 > nr ? (uint32_t)r + 1 : nr;
+            }
+        o.nround[ph] = nr;
     }
-    return o;
 }
 
-// every candidate placed, and the candidates of each round in distinct banks
-__host__ __device__ constexpr bool frmc_order_conflict_free(const FrmcOrder &o)
+// every candidate placed once, the centre first, distinct banks in every round
+constexpr bool order_ok(const CandOrder &o, bool frmc, int Rc)
 {
+    const int side = frmc ? 7 : 2 * Rc + 1, n = side * side;
     for (int ph = 0; ph < 4; ++ph) {
+        if (o.nround[ph] > MAXROUND || o.lane[ph][0][0] != n / 2) return false;
         int placed = 0;
-        for (int rd = 0; rd < 2; ++rd) {
+        for (int r = 0; r < MAXROUND; ++r) {
             bool seen[32] = {};
             for (int l = 0; l < 32; ++l) {
-                const int c = o.lane[ph][rd][l];
-                if (c == 255) continue;
+                const int c = o.lane[ph][r][l];
+                if (c == NOCAND) continue;
                 ++placed;
-                if (seen[frmc_bank(c, ph)]) return false;
-                seen[frmc_bank(c, ph)] = true;
+                if (seen[cand_bank(c, ph, frmc, Rc)]) return false;
+                seen[cand_bank(c, ph, frmc, Rc)] = true;
             }
         }
-        if (placed != 49 || o.lane[ph][0][0] != 24) return false;
+        if (placed != n) return false;
     }
     return true;
 }
 
-__constant__ FrmcOrder c_frmc_order = build_frmc_order();
-static_assert(frmc_order_conflict_free(build_frmc_order()), "FRMC lane order has bank conflicts");
-static_assert(sizeof(FrmcOrder) == NT, "the order table is staged one byte per thread");
+constexpr bool frmc_order_ok()
+{
+    CandOrder o{};
+    build_order(o, true, 0);
+    return order_ok(o, true, 0) && o.nround[0] == 2 && o.nround[1] == 2 && o.nround[2] == 2 &&
+           o.nround[3] == 2;
+}
+static_assert(frmc_order_ok(), "FRMC lane order: a round has two candidates in one bank");
+
+__device__ CandOrder g_order[NORDER];      // written once per device by init_cc
 
 struct Smem {
     uint32_t cs[4 * CPYC];        // masked samples, byte-shifted copies
@@ -125,9 +156,11 @@ struct Smem {
     char2 md[MD][MD];
     uint16_t list[TP * TP];       // tile pixels that need a reverse check
     uint8_t rej[TP * TP];
-    FrmcOrder ford;
+    CandOrder ord;                // reverse-check lane order of this tile's mode
     int nlist;
 };
+
+static_assert(offsetof(Smem, ord) % 16 == 0, "the lane order is written in 16-byte words");
 
 __device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
 
@@ -223,9 +256,13 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
     const bool rmc = t.cc_mode == 2;
     const bool rme = t.cc_mode == 1;
 
+    if (frmc || rmc) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&g_order[frmc ? 0 : t.Rc]);
+        uint4 *dst = reinterpret_cast<uint4 *>(&sm.ord);
+        for (int i = tid; i < (int)(sizeof(CandOrder) / sizeof(uint4)); i += NT) dst[i] = src[i];
+    }
     stage<0, RWDC, CPYC>(sm.cs, t.cur_smp, H, W, y0, x0);
     stage<1, RWDC, CPYC>(sm.cm, t.cur_msk, H, W, y0, x0);
-    reinterpret_cast<uint8_t *>(&sm.ford)[tid] = reinterpret_cast<const uint8_t *>(&c_frmc_order)[tid];
     __syncthreads();
     // template counts n around every source position of the tile +- 9 (current mask, 0 outside)
     for (int i = tid; i < NS * NS; i += NT) {
@@ -329,8 +366,6 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         __syncthreads();
         // reverse checks: one warp per listed pixel
         const int nl = sm.nlist;
-        const int side = frmc ? 7 : 2 * t.Rc + 1;
-        const int ncand = side * side, centre = ncand / 2;
         for (int li = warp; li < nl; li += NW) {
             const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
             const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
@@ -348,23 +383,16 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             }
             int s0 = 0, n0 = 0;
             bool rej = false;
-            // round 0, lane 0 scores d = 0; FRMC takes the bank-spread lane order of its phase
+            // round 0, lane 0 scores d = 0; the lane order of the pixel's column phase
             const int ph = (px + HC - h) & 3;
-            const int nround = frmc ? 2 : (ncand + 31) / 32;
+            const int nround = sm.ord.nround[ph];
             for (int rd = 0; rd < nround; ++rd) {
-                int cc = -1;                               // candidate, row-major in the window
-                if (frmc) {
-                    const int e = sm.ford.lane[ph][rd][lane];
-                    cc = e == 255 ? -1 : e;
-                } else {
-                    const int ci = 32 * rd + lane;
-                    if (ci < ncand) cc = ci + centre < ncand ? ci + centre : ci + centre - ncand;
-                }
+                const int e = sm.ord.lane[ph][rd][lane];
+                const int cc = e == NOCAND ? -1 : e;         // candidate, row-major in the window
                 int s = 0, n = 0;
                 bool valid = false;
                 if (cc >= 0) {
-                    const int dy = frmc ? frmc_offset(cc / 7) : cc / side - t.Rc;
-                    const int dx = frmc ? frmc_offset(cc % 7) : cc % side - t.Rc;
+                    const int dy = cand_dy(cc, frmc, t.Rc), dx = cand_dx(cc, frmc, t.Rc);
                     const int sy = y0 + py + dy, sx = x0 + px + dx;
                     if ((unsigned)sy < (unsigned)H && (unsigned)sx < (unsigned)W) {
                         s = sad_against<T>(sm, py + dy + HC - h, px + dx + HC - h, P);
@@ -506,6 +534,8 @@ __global__ void __launch_bounds__(NT) rme_batched_kernel(BatchDesc *bd)
     });
 }
 
+int g_order_ready[64];
+
 template <typename K>
 cudaError_t set_smem(K kernel, bool &done)
 {
@@ -542,15 +572,42 @@ cudaError_t launch_cc_batched_t(BatchDesc *bd, cudaStream_t st)
 
 int tiles_cc(const FrameTask &t) { return ((t.W + TP - 1) / TP) * ((t.H + TP - 1) / TP); }
 
+cudaError_t init_cc(int dev)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (g_order_ready[dev]) return cudaSuccess;
+    struct Orders {
+        CandOrder o[NORDER];
+        bool ok;
+    };
+    static const Orders *host = [] {            // built once (thread-safe static initialisation)
+        auto *r = new Orders();
+        r->ok = true;
+        for (int i = 0; i < NORDER; ++i) {
+            build_order(r->o[i], i == 0, i);
+            r->ok = r->ok && order_ok(r->o[i], i == 0, i);
+        }
+        return r;
+    }();
+    if (!host->ok) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(g_order, host->o, sizeof(host->o));
+    if (e == cudaSuccess) g_order_ready[dev] = 1;
+    return e;
+}
+
 int tiles_rme(const FrameTask &t)
 {
     if (t.K <= 0 || t.cc_mode != 1) return 0;
+    if (t.T == 9) return tiles_rme9(t);
     return ((t.W + 31) / 32) * ((t.H + NT / 32 - 1) / (NT / 32)) * t.K;
 }
 
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st)
 {
-    cudaError_t e;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = init_cc(dev);
+    if (e != cudaSuccess) return e;
     switch (t.T) {
     case 1: e = launch_cc_t<1>(t, st); break;
     case 3: e = launch_cc_t<3>(t, st); break;
@@ -583,14 +640,16 @@ cudaError_t launch_cc_batched(BatchDesc *bd, int T, cudaStream_t st)
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st)
 {
     if (t.K <= 0) return cudaSuccess;
+    if (t.T == 9) return launch_rme9(t, st);
     dim3 grid((t.W + 31) / 32, (t.H + NT / 32 - 1) / (NT / 32), t.K);
     rme_field_kernel<<<grid, NT, 0, st>>>(t);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_rme_batched(BatchDesc *bd, cudaStream_t st)
+cudaError_t launch_rme_batched(BatchDesc *bd, int T, cudaStream_t st)
 {
+    if (T == 9) return launch_rme9_batched(bd, st);
     static const int grid = persistent_grid(rme_batched_kernel, NT, 0);
     rme_batched_kernel<<<grid, NT, 0, st>>>(bd);
     count_launch();

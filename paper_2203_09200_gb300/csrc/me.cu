@@ -350,6 +350,195 @@ __global__ void __launch_bounds__(s_nt<WARPS>(), 16 / WARPS) me9_batched_kernel(
     });
 }
 
+// ---------------------------------------------------------------------------------------------
+// RME reverse field (Sec. 2.2) for T = 9: at every past-frame pixel q the reverse vector
+//     w*(q) = argmin over w in [-R, R]^2 with q + w inside the frame of C(q + w, -w),
+// costs compared as exact mean costs SAD/n (cross multiplication), the tie order applied to w.
+// C(q + w, -w) = sum over o of b_t(q+w+o) |f_sub_t(q+w+o) - rec(clamp(q+o))|: the past-frame patch
+// around q stays fixed and the current frame slides, so the warp-strip layout above applies with
+// the roles swapped.  A lane keeps 16 rows of the past frame (clamped) in registers; the current
+// masked samples and byte masks are staged in shared memory and read shifted by w.  The template
+// count n(q + w) differs between candidates: a count plane over the sources of the tile is built
+// once from the staged mask, with n = 0 where the source lies outside the frame (so those
+// candidates never win).  The running best of an output is one word:
+//     SAD (15 bits) | tie position of w (9 bits) << 15 | n (7 bits) << 24.
+// ---------------------------------------------------------------------------------------------
+constexpr int R9_OUTH = S_ROWS * 8;                        // tile rows (8 warps)
+constexpr int R9_NT = 256;
+constexpr int R9_SROWS = R9_OUTH + 8 + 2 * kMaxRadius;     // staged current-frame rows
+constexpr int R9_NROWS = R9_OUTH + 2 * kMaxRadius;         // count-plane rows (source rows)
+constexpr int R9_RB = 4 * S_RWORDS;                        // bytes per staged row
+
+struct SmemR9 {
+    union {
+        uint32_t c[R9_SROWS * S_RWORDS];                   // current masked samples
+        uint8_t hs[R9_SROWS * R9_RB];                      // horizontal mask sums (set-up only)
+    };
+    uint32_t m[R9_SROWS * S_RWORDS];                       // current byte masks
+    uint32_t n[R9_NROWS * S_RWORDS];                       // template counts at the sources
+    short2 vord[NVMAX];
+};
+
+// staged row r, byte b of word w = pixel (ry0 + r, rx0 + 4w + b) of src, 0 outside the frame
+__device__ __forceinline__ void stage_current(uint32_t *dst, const uint8_t *__restrict__ src, int H,
+                                              int W, int ry0, int rx0, int nrows)
+{
+    for (int i = threadIdx.x; i < nrows * S_RWORDS; i += R9_NT) {
+        const int r = i / S_RWORDS, w = i - r * S_RWORDS;
+        const int y = ry0 + r, gx = rx0 + 4 * w;
+        uint32_t v = 0;
+        if (y >= 0 && y < H) {
+            const uint8_t *row = src + (size_t)y * W;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int x = gx + b;
+                if (x >= 0 && x < W) v |= (uint32_t)row[x] << (8 * b);
+            }
+        }
+        dst[i] = v;
+    }
+}
+
+__device__ __forceinline__ void rme9_tile(SmemR9 &sm, const FrameTask &t, int tbx, int tby, int k)
+{
+    const int x0 = tbx * S_OUTW, y0 = tby * R9_OUTH;
+    const int H = t.H, W = t.W, R = t.R;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (*t.status) return;
+    const uint8_t *__restrict__ ref = t.ref_rec[k];
+    const int rx0 = x0 - 4 - R, ry0 = y0 - 4 - R;            // staged origin
+    const int nrows = R9_OUTH + 8 + 2 * R, ncnt = R9_OUTH + 2 * R;
+
+    // 1. byte masks of the current frame around the tile, and the tie order
+    stage_current(sm.m, t.cur_msk, H, W, ry0, rx0, nrows);
+    build_tie_order(sm.vord, R);
+    __syncthreads();
+    // 2. horizontal 9-sums of the mask bits at staged columns 4 .. R9_RB - 5
+    const uint8_t *mb = reinterpret_cast<const uint8_t *>(sm.m);
+    for (int i = tid; i < nrows * (R9_RB - 8); i += R9_NT) {
+        const int r = i / (R9_RB - 8), col = 4 + i - r * (R9_RB - 8);
+        int s = 0;
+#pragma unroll
+        for (int dx = -4; dx <= 4; ++dx) s += mb[r * R9_RB + col + dx] & 1;
+        sm.hs[r * R9_RB + col] = (uint8_t)s;
+    }
+    __syncthreads();
+    // 3. template counts n at the sources (row y0 - R + rr, column rx0 + col); 0 outside the frame
+    uint8_t *nb = reinterpret_cast<uint8_t *>(sm.n);
+    for (int i = tid; i < R9_NROWS * R9_RB; i += R9_NT) {
+        const int rr = i / R9_RB, col = i - rr * R9_RB;
+        const int sy = y0 - R + rr, sx = rx0 + col;
+        int v = 0;
+        if (rr < ncnt && col >= 4 && col < R9_RB - 4 && sy >= 0 && sy < H && sx >= 0 && sx < W) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) v += sm.hs[(rr + j) * R9_RB + col];
+        }
+        nb[i] = (uint8_t)v;
+    }
+    __syncthreads();
+    // 4. masked samples of the current frame (over the horizontal sums)
+    stage_current(sm.c, t.cur_smp, H, W, ry0, rx0, nrows);
+    // 5. this lane's 16 past-frame rows of 4 columns, clamped coordinates
+    const int cx = x0 - 4 + 4 * lane;
+    const int cy0 = y0 + S_ROWS * warp - 4;
+    uint32_t fr[S_DROWS];
+#pragma unroll
+    for (int i = 0; i < S_DROWS; ++i) {
+        const uint8_t *row = ref + (size_t)min(max(cy0 + i, 0), H - 1) * W;
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(cx + b, 0), W - 1)] << (8 * b);
+        fr[i] = v;
+    }
+    __syncthreads();
+
+    uint32_t best[S_ROWS][4];
+#pragma unroll
+    for (int j = 0; j < S_ROWS; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) best[j][c] = 0x7fffu | (1u << 24);   // "infinite", n = 1
+    const int nv = (2 * R + 1) * (2 * R + 1);
+    for (int o = 0; o < nv; ++o) {
+        const short2 w = sm.vord[o];
+        const int wy = w.x, wx = w.y;
+        const int sh = (wx + R) & 3, q = (wx + R) >> 2;
+        const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)sh;
+        const int base = (S_ROWS * warp + wy + R) * S_RWORDS + lane + q;
+        const uint32_t *crow = sm.c + base, *mrow = sm.m + base, *nrow = sm.n + base;
+        const uint32_t o15 = (uint32_t)o << 15;
+        uint32_t lo = 0, hi = 0;
+        uint32_t dlo[S_DROWS], dhi[S_DROWS];
+#pragma unroll
+        for (int i = 0; i < S_DROWS; ++i) {
+            const uint32_t c4 = __byte_perm(crow[i * S_RWORDS], crow[i * S_RWORDS + 1], sel);
+            const uint32_t m4 = __byte_perm(mrow[i * S_RWORDS], mrow[i * S_RWORDS + 1], sel);
+            const uint32_t d4 = __vabsdiffu4(fr[i], c4) & m4;
+            dlo[i] = __byte_perm(d4, 0u, 0x4240);
+            dhi[i] = __byte_perm(d4, 0u, 0x4341);
+            lo += dlo[i];
+            hi += dhi[i];
+            if (i >= 9) {
+                lo -= dlo[i - 9];
+                hi -= dhi[i - 9];
+            }
+            if (i >= 8) {
+                const int j = i - 8;                       // output row of this window
+                const uint32_t Q = lo + hi;
+                const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
+                const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
+                const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
+                const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
+                const uint32_t A = __byte_perm(Ql, Q, 0x5432);
+                const uint32_t B = __byte_perm(Q, Qr, 0x5432);
+                const uint32_t h02 = Ql + A + Q + B + lor;   // SADs of columns 0, 2
+                const uint32_t h13 = h02 + Qr - lol - lor;   // SADs of columns 1, 3
+                const uint32_t n4 = __byte_perm(nrow[j * S_RWORDS], nrow[j * S_RWORDS + 1], sel);
+                const uint32_t sad[4] = {h02 & 0xffffu, h13 & 0xffffu, h02 >> 16, h13 >> 16};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint32_t n = (n4 >> (8 * c)) & 0xffu;
+                    const uint32_t b = best[j][c];
+                    const bool take = sad[c] * (b >> 24) < (b & 0x7fffu) * n;
+                    best[j][c] = take ? (sad[c] | o15 | (n << 24)) : b;
+                }
+            }
+        }
+    }
+    if (lane == 0 || lane == 31) return;
+    char2 *rmv = reinterpret_cast<char2 *>(t.rmv[k]);
+    const int oy = y0 + S_ROWS * warp;
+#pragma unroll
+    for (int j = 0; j < S_ROWS; ++j) {
+        const int y = oy + j;
+        if (y >= H) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int x = cx + c;
+            if (x < W) {
+                const short2 w = sm.vord[(best[j][c] >> 15) & 0x1ffu];
+                rmv[(size_t)y * W + x] = make_char2((signed char)w.x, (signed char)w.y);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(R9_NT, 2) rme9_kernel(FrameTask t)
+{
+    __shared__ SmemR9 sm;
+    rme9_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(R9_NT, 2) rme9_batched_kernel(BatchDesc *bd)
+{
+    __shared__ SmemR9 sm;
+    __shared__ FrameTask task;
+    __shared__ int claim[2];
+    claim_tiles(bd, kPhRme, task, claim, [&](const FrameTask &t, int l) {
+        const int tx = (t.W + S_OUTW - 1) / S_OUTW, ty = (t.H + R9_OUTH - 1) / R9_OUTH;
+        rme9_tile(sm, t, l % tx, (l / tx) % ty, l / (tx * ty));
+    });
+}
+
 }  // namespace
 
 int tiles_me(const FrameTask &t, int me_warps)
@@ -370,6 +559,29 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);
     }
+    count_launch();
+    return cudaGetLastError();
+}
+
+int tiles_rme9(const FrameTask &t)
+{
+    if (t.K <= 0) return 0;
+    return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + R9_OUTH - 1) / R9_OUTH) * t.K;
+}
+
+cudaError_t launch_rme9(const FrameTask &t, cudaStream_t st)
+{
+    if (t.K <= 0) return cudaSuccess;
+    dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + R9_OUTH - 1) / R9_OUTH, t.K);
+    rme9_kernel<<<grid, R9_NT, 0, st>>>(t);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st)
+{
+    static const int grid = persistent_grid(rme9_batched_kernel, R9_NT, 0);
+    rme9_batched_kernel<<<grid, R9_NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
 }

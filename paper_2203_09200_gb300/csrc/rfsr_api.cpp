@@ -412,8 +412,9 @@ int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint
     CK(launch_ingest(t, e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[1], e->stream));
     CK(launch_me(t, e->stream));
-    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
+    // the reverse field of RME belongs to the consistency check (Sec. 2.2), so it is timed there
+    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
     CK(launch_cc_project(t, e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[3], e->stream));
     CK(launch_fsr(t, e->stream));
@@ -432,7 +433,7 @@ cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape 
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[0], st);
     if (e == cudaSuccess) e = launch_me_batched(d, T, sh.me_warps, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[1], st);
-    if (e == cudaSuccess && rme) e = launch_rme_batched(d, st);
+    if (e == cudaSuccess && rme) e = launch_rme_batched(d, T, st);
     if (e == cudaSuccess) e = launch_cc_batched(d, T, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[2], st);
     if (e == cudaSuccess) e = launch_fsr_batched(d, sh.fsr_blocks, st);
@@ -694,6 +695,8 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     }
     cudaError_t ie = init_fsr(cfg->device);
     if (ie != cudaSuccess) return bail(ie, "FSR set-up");
+    ie = init_cc(cfg->device);
+    if (ie != cudaSuccess) return bail(ie, "check set-up");
     if (batched(e)) {
         for (auto &set : e->sets) {
             cudaError_t er = cudaHostAlloc((void **)&set.h, sizeof(BatchDesc), cudaHostAllocPortable);

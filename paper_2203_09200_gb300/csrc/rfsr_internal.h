@@ -160,7 +160,11 @@ int persistent_grid(K kernel, int threads, size_t smem)
 cudaError_t launch_batch_prologue(BatchDesc *bd, cudaStream_t st);
 cudaError_t launch_ingest_batched(BatchDesc *bd, cudaStream_t st);
 cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, cudaStream_t st);
-cudaError_t launch_rme_batched(BatchDesc *bd, cudaStream_t st);
+cudaError_t launch_rme_batched(BatchDesc *bd, int T, cudaStream_t st);
+// RME reverse field for T = 9 (tiled; other T use the direct search of cc.cu)
+int tiles_rme9(const FrameTask &t);
+cudaError_t launch_rme9(const FrameTask &t, cudaStream_t st);
+cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st);
 cudaError_t launch_cc_batched(BatchDesc *bd, int T, cudaStream_t st);
 cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, cudaStream_t st);
 
@@ -181,6 +185,8 @@ cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st);
 // one-time per-device set-up of the FSR kernel (constant twiddles, shared-memory limit)
 cudaError_t init_fsr(int device);
+// one-time per-device set-up of the check kernel (reverse-check lane orders)
+cudaError_t init_cc(int device);
 
 // set the calling thread's rfsr_last_error() message; returns code
 int set_error(int code, const std::string &msg);

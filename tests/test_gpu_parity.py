@@ -110,6 +110,39 @@ def test_config1_frames(engine, t):
 
 
 # --------------------------------------------------------------------------------------------
+# RME reverse field for T = 9 (tiled kernel): every past-frame pixel against the oracle
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,R,seed,levels", [(150, 250, 8, 1, 0), (130, 124, 9, 2, 0),
+                                               (70, 246, 3, 3, 0), (66, 130, 8, 4, 3)])
+def test_rme_reverse_field_t9(engine, H, W, R, seed, levels):
+    """Several 64 x 120 tiles with ragged edges; levels > 0 quantises the content to a few grey
+    levels so that equal mean costs with different template counts (ties) are common."""
+    seq = synth.config2(seed=200 + seed, H=H, W=W, F=3)
+    frames = seq.frames.copy()
+    if levels:
+        frames = (frames // (256 // levels) * (256 // levels)).astype(np.uint8)
+    t = 2
+    msk = seq.masks[t]
+    smp = (frames[t] * msk).astype(np.uint8)
+    hist = [(frames[t - k], (frames[t - k] * seq.masks[t - k]).astype(np.uint8), seq.masks[t - k])
+            for k in (1, 2)]
+    st = engine.create_stream(height=H, width=W, cc_mode="rme", template_size=9, search_radius=R,
+                              check_radius=R)
+    try:
+        st.set_history(hist)
+        st.push_frame(smp, msk)
+        st.get_frame(timeout_ms=120000)
+        rmv = [st.debug_get(rfsr.DBG_RMV, k) for k in (1, 2)]
+    finally:
+        st.destroy()
+    for k in (1, 2):
+        ref = hist[k - 1][0]
+        exp = np.array([[oracle.rme_vector(smp, msk, ref, 9, R, qy, qx) for qx in range(W)]
+                        for qy in range(H)], dtype=np.int8)
+        np.testing.assert_array_equal(rmv[k - 1], exp, err_msg=f"reverse field k={k}")
+
+
+# --------------------------------------------------------------------------------------------
 # ragged tiles, every consistency-check mode, several template sizes / radii
 # --------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", MODES)
