@@ -24,8 +24,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rfsr_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "librfsr_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "librfsr_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threads = 1
 
 # decision labels and consistency-check modes (same numbering as the C file)
 DEC_MEASURED, DEC_NOT_PROJECTABLE, DEC_NNC_REJECT, DEC_CHECK_REJECT, DEC_ACCEPT = range(5)
@@ -34,16 +36,30 @@ CC_NAMES = {"none": CC_NONE, "rme": CC_RME, "rmc": CC_RMC, "frmc": CC_FRMC, "nnc
             "nnc_frmc": CC_NNC_FRMC}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (plain C, -O2, single-threaded)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library: plain C, -O2, single-threaded; with omp, the same source
+    with -fopenmp (frame-level loops over independent pixels and blocks on several threads)."""
+    path = _OMP_PATH if omp else _LIB_PATH
     with _lock:
-        if force or not os.path.exists(_LIB_PATH) or \
-                os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-            tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-            subprocess.run(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                            "-o", tmp, _SRC, "-lm"], check=True)
-            os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".{os.getpid()}.tmp"
+            cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared"]
+            cmd += ["-fopenmp"] if omp else []
+            subprocess.run(cmd + ["-o", tmp, _SRC, "-lm"], check=True)
+            os.replace(tmp, path)
+    return path
+
+
+def set_threads(n: int) -> None:
+    """Run the frame-level oracle calls on n threads (n > 1: the OpenMP build; same results)."""
+    global _threads
+    _threads = max(1, int(n))
+    if _threads > 1:
+        _load().orc_set_threads(_threads)
+
+
+def threads() -> int:
+    return _threads
 
 
 class _FsrParams(C.Structure):
@@ -70,10 +86,10 @@ class FsrParams:
 
 
 def _load():
-    global _lib
-    if _lib is None:
-        build()
-        lib = C.CDLL(_LIB_PATH)
+    omp = _threads > 1
+    lib = _libs.get(omp)
+    if lib is None:
+        lib = C.CDLL(build(omp=omp))
         u8p, i8p, u16p = C.POINTER(C.c_uint8), C.POINTER(C.c_int8), C.POINTER(C.c_uint16)
         dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
         I = C.c_int
@@ -97,8 +113,11 @@ def _load():
                                           I, dp, dp, dp, dp, dp, dp, ip, dp, dp, I]
         lib.orc_fsr_frame.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, dp, dp]
         lib.orc_quantize.argtypes = [dp, u8p, u8p, I, I, u8p]
-        _lib = lib
-    return _lib
+        lib.orc_set_threads.argtypes = [I]
+        if omp:
+            lib.orc_set_threads(_threads)
+        _libs[omp] = lib
+    return lib
 
 
 def _p(a: Optional[np.ndarray], ct):

@@ -1,7 +1,7 @@
 /*
  * rfsr_oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded CPU restatement of the per-frame hot path of recursive
+ * A plain, slow CPU restatement of the per-frame hot path of recursive
  * frequency-selective reconstruction of quarter-sampled video (Grosche, Seiler, Kaup,
  * "Novel Consistency Check for Fast Recursive Reconstruction of Non-Regularly Sampled Video
  * Data", ICIP 2021, arXiv 2203.09200).  Only the tests, __graft_entry__.smoke() and the
@@ -21,6 +21,10 @@
  *                     overwrite rule of Sec. 3.2 and concealed weighting zero (Sec. 4)
  *   orc_quantize .... 8-bit reconstruction that becomes the next frame's reference
  *
+ * Built plainly it is single-threaded.  Built with -fopenmp (a second library), the frame-level
+ * loops over pixels and blocks -- each of which writes only its own outputs -- run on several
+ * threads; the arithmetic and the results are the same.
+ *
  * The paper leaves several details open.  The readings taken here (the cost function, the tie
  * order, border handling, the FSR model and its constants) are listed in the design notes and
  * repeated at each function.  Parity status: every function is pinned by tests/test_oracle_*.py
@@ -33,7 +37,21 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORC_VERSION 1
+
+/* threads of the OpenMP build (no effect in the single-threaded build) */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
 
 /* decision labels per pixel and reference frame */
 enum { DEC_MEASURED = 0, DEC_NOT_PROJECTABLE = 1, DEC_NNC_REJECT = 2, DEC_CHECK_REJECT = 3,
@@ -116,6 +134,7 @@ void orc_me_pixel(const uint8_t *smp, const uint8_t *msk, const uint8_t *ref, in
 void orc_me_field(const uint8_t *smp, const uint8_t *msk, const uint8_t *ref, int H, int W,
                   int T, int R, int8_t *mv)
 {
+#pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             orc_me_pixel(smp, msk, ref, H, W, T, R, y, x, &mv[2 * ((size_t)y * W + x)],
@@ -154,6 +173,7 @@ static void median_vector(const int8_t *mv, int H, int W, int y, int x, int *my,
 
 void orc_nnc_field(const int8_t *mv, int H, int W, int8_t *fmv, uint8_t *pass)
 {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             int my, mx;
@@ -162,6 +182,7 @@ void orc_nnc_field(const int8_t *mv, int H, int W, int8_t *fmv, uint8_t *pass)
             fmv[2 * ((size_t)y * W + x) + 1] = (int8_t)mx;
         }
     static const int NB[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             int ok = 1;
@@ -278,6 +299,7 @@ void orc_cc_project(int cc_mode, int T, int R, int Rc, const uint8_t *smp, const
         memcpy(fmv, mv, (size_t)H * W * 2);
         memset(pass, 1, (size_t)H * W);
     }
+#pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             size_t i = (size_t)y * W + x;
@@ -429,7 +451,7 @@ static void twiddles(int N, double *c, double *s)
 static void dft2_real(const double *a, int N, const double *tc, const double *ts, double *re,
                       double *im)
 {
-    static double tr[ORC_NMAX * ORC_NMAX], ti[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double tr[ORC_NMAX * ORC_NMAX], ti[ORC_NMAX * ORC_NMAX];
     for (int m = 0; m < N; ++m)
         for (int l = 0; l < N; ++l) {
             double sr = 0.0, si = 0.0;
@@ -468,11 +490,12 @@ void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_
                        int second_at)
 {
     const int N = P->N, B = P->B, o = (P->N - P->B) / 2;
-    static double w[ORC_NMAX * ORC_NMAX], f[ORC_NMAX * ORC_NMAX], wf[ORC_NMAX * ORC_NMAX];
-    static double Wre[ORC_NMAX * ORC_NMAX], Wim[ORC_NMAX * ORC_NMAX];
-    static double Rre[ORC_NMAX * ORC_NMAX], Rim[ORC_NMAX * ORC_NMAX];
-    static double g[ORC_NMAX * ORC_NMAX], fw[ORC_NMAX * ORC_NMAX];
-    static double tc[ORC_NMAX], ts[ORC_NMAX];
+    static _Thread_local double w[ORC_NMAX * ORC_NMAX], f[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double wf[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double Wre[ORC_NMAX * ORC_NMAX], Wim[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double Rre[ORC_NMAX * ORC_NMAX], Rim[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double g[ORC_NMAX * ORC_NMAX], fw[ORC_NMAX * ORC_NMAX];
+    static _Thread_local double tc[ORC_NMAX], ts[ORC_NMAX];
     const double c = (N - 1) / 2.0;
     twiddles(N, tc, ts);
 
@@ -585,9 +608,10 @@ void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *m
                    double *min_gap)
 {
     int B = P->B, nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
-    double blk[ORC_NMAX * ORC_NMAX];
+#pragma omp parallel for schedule(dynamic, 1)
     for (int by = 0; by < nby; ++by)
         for (int bx = 0; bx < nbx; ++bx) {
+            double blk[ORC_NMAX * ORC_NMAX];
             double gap;
             orc_fsr_block(P, smp, msk, psum, pcnt, H, W, by, bx, blk, &gap);
             if (min_gap) min_gap[by * nbx + bx] = gap;

@@ -11,6 +11,8 @@ near ties the other way (oracle.fsr_block_valid), and such blocks must stay rare
 Past frames are injected with rfsr_set_history from the generator (ground-truth frames), so
 both sides see identical inputs; no oracle input ever comes from the GPU.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -67,10 +69,17 @@ def assert_fsr_close(got, smp, msk, psum, pcnt, ref_out, params=None, B=4, max_f
     pad[:H, :W] = err
     eb = pad.reshape(nby, B, nbx, B).max(axis=(1, 3))
     bad = np.argwhere(eb > FSR_TOL)
-    for by, bx in bad:
-        blk = got[B * by:B * by + B, B * bx:B * bx + B]
-        ok, e0, it = oracle.fsr_block_valid(params, smp, msk, psum, pcnt, int(by), int(bx), blk)
-        assert ok, f"FSR block ({by},{bx}) off by {e0} and not a near-tie continuation"
+
+    def valid(b):
+        by, bx = int(b[0]), int(b[1])
+        blk = np.ascontiguousarray(got[B * by:B * by + B, B * bx:B * bx + B])
+        return (by, bx) + tuple(oracle.fsr_block_valid(params, smp, msk, psum, pcnt, by, bx, blk))
+
+    # the oracle's C calls release the GIL and keep per-thread scratch, so threads help here
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        for by, bx, ok, e0, it in ex.map(valid, bad):
+            assert ok, f"FSR block ({by},{bx}) off by {e0} and not a near-tie continuation"
     assert len(bad) <= max(2, max_frac * nby * nbx), f"{len(bad)} near-tie blocks"
     return len(bad)
 
@@ -224,6 +233,22 @@ def test_full_size_sampled(engine, cfg, mode, t):
     # sizes and stand-alone FSR at full size below.  Measured pixels must be exact.
     m = msk == 1
     np.testing.assert_array_equal(got["rec"][m], smp[m])
+
+
+def test_full_frame_1080p_every_pixel(engine):
+    """One whole 1920x1080 frame of the NNC+FRMC workload (three past frames) against the oracle
+    at every pixel and block, the oracle's frame loops on all host cores (OpenMP build)."""
+    t = 12
+    seq = synth.config3(F=t + 1)
+    smp, msk = seq.samples[t], seq.masks[t]
+    hist = [(seq.frames[t - k], seq.samples[t - k], seq.masks[t - k]) for k in (1, 2, 3)]
+    got = gpu_step(engine, smp, msk, hist, cc_mode="nnc_frmc")
+    try:
+        oracle.set_threads(os.cpu_count() or 1)
+        ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NNC_FRMC, T=9, R=8)
+    finally:
+        oracle.set_threads(1)
+    compare(got, ref, msk, smp)
 
 
 def test_fsr_device_full_hd_sampled(engine):

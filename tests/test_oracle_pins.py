@@ -540,3 +540,30 @@ def test_masks_quarter_sampling():
     np.testing.assert_array_equal(m[0], m[per])
     f = synth.config1(seed=1, F=3)
     np.testing.assert_array_equal(f.masks[0], f.masks[2])
+
+
+def test_openmp_build_gives_identical_results():
+    """The -fopenmp build (frame loops over independent pixels and blocks on several threads)
+    returns bit-identical fields, decisions, projections and FSR output."""
+    seq = synth.config2(seed=9, H=48, W=64, F=4)
+    t = 3
+    smp, msk = seq.samples[t], seq.masks[t]
+    hist = [(seq.frames[t - k], seq.samples[t - k], seq.masks[t - k]) for k in (1, 2, 3)]
+    fsr = oracle.FsrParams(iterations=20)
+    out = {}
+    try:
+        for n in (1, 4):
+            oracle.set_threads(n)
+            out[n] = [oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NAMES[m], T=7, R=4,
+                                        fsr=fsr) for m in ("nnc_frmc", "rmc", "rme")]
+    finally:
+        oracle.set_threads(1)
+    for a, b in zip(out[1], out[4]):
+        for k in range(3):
+            np.testing.assert_array_equal(a.mv[k], b.mv[k])
+            np.testing.assert_array_equal(a.fmv[k], b.fmv[k])
+            np.testing.assert_array_equal(a.dec[k], b.dec[k])
+        np.testing.assert_array_equal(a.psum, b.psum)
+        np.testing.assert_array_equal(a.pcnt, b.pcnt)
+        np.testing.assert_array_equal(a.fsr, b.fsr)
+        np.testing.assert_array_equal(a.rec, b.rec)
