@@ -80,7 +80,8 @@ def fsr_flops_per_block(iters=ITERS):
 CSRC = os.path.join(ROOT, "paper_2203_09200_gb300", "csrc")
 KERNEL_PROFILES = {"fsr_kernel": ("fsr_kernel_1080p.md", ["fsr.cu", "rfsr_internal.h"]),
                    "me9_kernel": ("me9_kernel_1080p.md", ["me.cu", "rfsr_internal.h"]),
-                   "cc_project_kernel": ("cc_project_kernel_1080p.md", ["cc.cu", "rfsr_internal.h"])}
+                   "cc_project_kernel": ("cc_project_kernel_1080p.md", ["cc.cu", "rfsr_internal.h"]),
+                   "rme9_kernel": ("rme9_kernel_1080p.md", ["me.cu", "rfsr_internal.h"])}
 
 
 def kernel_source_sha(kernel):
@@ -430,6 +431,83 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
                          "(continuous batching, memory admission)")}
 
 
+# ---------------------------------------------------------------------------------------------
+# reconstruction quality (frame-wise PSNR / SSIM against the ground-truth frames)
+# ---------------------------------------------------------------------------------------------
+def border_px(h, w):
+    """The paper omits a 40-pixel border at 1280x720; scaled to the frame size (at least 2)."""
+    return max(2, int(round(40 * min(h / 720.0, w / 1280.0))))
+
+
+def psnr(a, b, border):
+    d = a[border:-border, border:-border].astype(np.float64) - b[border:-border, border:-border]
+    mse = float(np.mean(d * d))
+    return 99.0 if mse == 0 else 10.0 * np.log10(255.0 ** 2 / mse)
+
+
+def ssim(a, b, border):
+    """Mean SSIM (Wang et al. 2004: 11x11 Gaussian window, sigma 1.5, K1 0.01, K2 0.03, L 255)."""
+    import scipy.ndimage as nd
+    x, y = a.astype(np.float64), b.astype(np.float64)
+    f = lambda z: nd.gaussian_filter(z, 1.5, truncate=3.5)
+    mx, my = f(x), f(y)
+    sxx, syy, sxy = f(x * x) - mx * mx, f(y * y) - my * my, f(x * y) - mx * my
+    c1, c2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+    m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return float(m[border:-border, border:-border].mean())
+
+
+QUALITY_METHODS = [
+    ("fsr_single_frame", dict(num_refs=0, cc_mode="none")),
+    ("rfsr_rme", dict(cc_mode="rme", fsr_overwrite_projected=1)),
+    ("dfsr_rme", dict(cc_mode="rme")),
+    ("dfsr_rmc", dict(cc_mode="rmc")),
+    ("dfsr_frmc", dict(cc_mode="frmc")),
+    ("dfsr_nnc", dict(cc_mode="nnc")),
+    ("dfsr_nnc_frmc", dict(cc_mode="nnc_frmc")),
+    ("dfsr_no_check", dict(cc_mode="none")),
+]
+
+
+def quality_run(rfsr, seq, method_kw, with_ssim=True):
+    """Free-running recursion through the stream API; per frame (PSNR, SSIM) of the 8-bit output."""
+    h, w = seq.shape
+    b = border_px(h, w)
+    out = []
+    with rfsr.Engine(device=0) as eng:
+        st = eng.create_stream(height=h, width=w, mask_type=seq.mask_type, **method_kw)
+        for t in range(len(seq)):
+            st.push_frame(seq.samples[t], seq.masks[t])
+            rec = st.get_frame(timeout_ms=120000)
+            out.append((psnr(rec, seq.frames[t], b), ssim(rec, seq.frames[t], b) if with_ssim else None))
+    return out
+
+
+def run_quality(rfsr, torch):
+    seqs = [("1280x720 dynamic", synth.config2(seed=2, F=32)),
+            ("1280x720 fixed", synth.config2(seed=2, F=32, mask_type=synth.MASK_FIXED)),
+            ("1920x1080 dynamic", synth.config3(seed=3, F=24)),
+            ("64x64 fixed translation", synth.config1(seed=1))]
+    res = {}
+    for name, seq in seqs:
+        r = {}
+        for m, kw in QUALITY_METHODS:
+            q = quality_run(rfsr, seq, kw)
+            p = np.array([a for a, _ in q])
+            s_ = np.array([b for _, b in q])
+            r[m] = {"psnr_db": round(float(p.mean()), 3), "ssim": round(float(s_.mean()), 4),
+                    "psnr_db_frames_10_on": round(float(p[10:].mean()), 3) if len(p) > 10 else None}
+        base = r["fsr_single_frame"]["psnr_db"]
+        for m in r:
+            r[m]["gain_vs_single_frame_db"] = round(r[m]["psnr_db"] - base, 3)
+        res[name] = r
+    res["protocol"] = ("free-running recursion through rfsr_push_frame / rfsr_get_frame, K=3, T=9, "
+                       "R=Rc=8, FSR 100 iterations; frame-wise PSNR and mean SSIM of the 8-bit "
+                       "output against the generator's ground truth with the paper's 40-pixel "
+                       "border (scaled to the frame size) omitted, averaged over all frames")
+    return res
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -627,7 +705,8 @@ def summarize_launches(path):
 
 def run_ncu_case(args):
     """A short, untimed kernel sequence for an ncu capture: 'frame_step' runs `frames` frames of
-    the 1080p workload on one unbatched stream (device-resident inputs); 'batched' runs `frames`
+    the 1080p workload on one unbatched stream (device-resident inputs, check mode --cc-mode);
+    'batched' runs `frames`
     batched steps of the 64-stream mix (default tile shape, no autotuning)."""
     import torch
     from paper_2203_09200_gb300 import build as pbuild
@@ -639,7 +718,7 @@ def run_ncu_case(args):
         seq = synth.config3(seed=3, F=nf)
         d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
         with rfsr.Engine(device=0) as eng:
-            st = eng.create_stream(height=H, width=W, cc_mode="nnc_frmc", template_size=T,
+            st = eng.create_stream(height=H, width=W, cc_mode=args.cc_mode, template_size=T,
                                    search_radius=R, num_refs=KREF, fsr_iterations=ITERS)
             for f in range(nf):
                 st.push_frame_device(d_smp[f], d_msk[f])
@@ -674,6 +753,10 @@ def main():
     ap.add_argument("--ncu-case", choices=["frame_step", "batched"],
                     help="run only a short untimed kernel sequence (for ncu captures)")
     ap.add_argument("--frames", type=int, default=6, help="frames of --ncu-case")
+    ap.add_argument("--cc-mode", default="nnc_frmc", choices=list(MODES),
+                    help="consistency-check mode of --ncu-case frame_step")
+    ap.add_argument("--quality", action="store_true",
+                    help="print the reconstruction-quality table (PSNR / SSIM per method) and exit")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print the per-kernel table of an ncu launch list and exit")
     args = ap.parse_args()
@@ -682,6 +765,14 @@ def main():
         return
     if args.ncu_case:
         run_ncu_case(args)
+        return
+    if args.quality:
+        import torch
+        from paper_2203_09200_gb300 import build as pbuild
+        from paper_2203_09200_gb300 import rfsr
+        torch.cuda.set_device(0)
+        pbuild.build()
+        print(json.dumps({"quality": run_quality(rfsr, torch)}), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
