@@ -24,10 +24,10 @@
 //     full weight spectrum W (read at shifts k -+ u) lives in shared memory as rows of 49 columns
 //     (0..31 and 0..16 again), so both shifted reads are immediate offsets from one pointer and
 //     the 32 lanes' row-shifted reads fall in distinct banks.
-//   * Selection: one pass per lane keeps its maximum and the R value there, the warp maximum
-//     comes from __reduce_max_sync on the (non-negative) float bits and the lowest canonical index
-//     among the lanes that reach it from __reduce_min_sync; the owner lane's R value arrives by one
-//     shuffle pair.  The rank-2 residual update works on (Re, Im) as packed FP32 pairs
+//   * Selection: one pass per lane keeps its maximum and its bin, the warp maximum comes from
+//     __reduce_max_sync on the (non-negative) float bits and the lowest canonical index among the
+//     lanes that reach it from __reduce_min_sync.  The winning bin is the same in every lane, so
+//     the owner lane reads R there through one uniform switch and a shuffle pair sends it out.  The rank-2 residual update works on (Re, Im) as packed FP32 pairs
 //     (R -= dr (a + c) + di (c.y - a.y, a.x - c.x)): one pair add, two scalar subtractions and two
 //     pair FMAs per bin.
 //   * The per-warp shared memory is one 12.5 KB union (support, row spectra, W).
@@ -322,15 +322,13 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     float g = 0.f;
     const float gscale = W0 > 0.f ? gamma / W0 : 0.f;
     for (int it = 0; it < iters && W0 > 0.f; ++it) {
-        float be = 0.f, sr = 0.f, si = 0.f;
+        float be = 0.f;
         int bl = -1;
 #pragma unroll
         for (int l = 0; l < NH; ++l) {
             const float e = wfr[l] * fmaf(Rr[l].x, Rr[l].x, Rr[l].y * Rr[l].y);
             const bool take = (int)(__float_as_uint(e) + bias) > (int)__float_as_uint(be);
             be = take ? e : be;
-            sr = take ? Rr[l].x : sr;
-            si = take ? Rr[l].y : si;
             bl = take ? l : bl;
         }
         const float m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(be)));
@@ -347,8 +345,18 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
             uk = (N - uk) & (N - 1);
             ul = N - ul;
         }
-        const float ure = __shfl_sync(0xffffffffu, sr, uk);
-        const float uim = __shfl_sync(0xffffffffu, si, uk);
+        // R(uk, ul) from its owner lane: ul is the same in every lane, so one switch branch
+        float2 rv = Rr[0];
+        switch (ul) {
+#define RFSR_CASE(c) case c: rv = Rr[c]; break;
+            RFSR_CASE(1) RFSR_CASE(2) RFSR_CASE(3) RFSR_CASE(4) RFSR_CASE(5) RFSR_CASE(6)
+            RFSR_CASE(7) RFSR_CASE(8) RFSR_CASE(9) RFSR_CASE(10) RFSR_CASE(11) RFSR_CASE(12)
+            RFSR_CASE(13) RFSR_CASE(14) RFSR_CASE(15) RFSR_CASE(16)
+#undef RFSR_CASE
+            default: break;
+        }
+        const float ure = __shfl_sync(0xffffffffu, rv.x, uk);
+        const float uim = __shfl_sync(0xffffffffu, rv.y, uk);
         const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
         const float dr = gscale * ure;
         const float di = self ? 0.f : gscale * uim;
