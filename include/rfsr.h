@@ -239,6 +239,47 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
                     const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
                     uint8_t *d_out_u8, void *cuda_stream);
 
+/* ---- stream state: checkpoint / resume and migration between engines -------------------- */
+/* (No counterpart in the paper: serving infrastructure.)  The recursion state of a stream is
+ * its configuration and the reconstructed frame, sample plane and mask of its last K frames
+ * (Sec. 2.2: the past frames that ME and projection read).  rfsr_stream_export writes it to a
+ * caller-owned host buffer; rfsr_stream_import creates a stream from it on any engine (another
+ * GPU included), whose next frame then gives exactly the result the original stream would have.
+ * Buffer layout: rfsr_state_header, then for k = 1..hist the planes of frame t-k
+ * (reconstruction, samples, 0/1 mask; H x W bytes each, row-major). */
+typedef struct {
+    uint32_t magic;              /* RFSR_STATE_MAGIC                                               */
+    uint32_t version;            /* RFSR_STATE_VERSION                                             */
+    uint64_t bytes;              /* size of the whole buffer                                       */
+    rfsr_stream_config config;   /* the stream's configuration                                     */
+    int32_t hist;                /* past frames stored (0..num_refs)                               */
+    int32_t reserved;
+    int64_t frames;              /* frames the exported stream had processed                       */
+} rfsr_state_header;
+#define RFSR_STATE_MAGIC 0x54534652u   /* "RFST" */
+#define RFSR_STATE_VERSION 1u
+
+/* Export s into buf (cap bytes); *bytes receives the size needed (buf == NULL: size query).
+ * Taken between frames: every pushed frame must have been collected.
+ * Errors: EINVAL (NULL bytes, cap too small), EAGAIN (stream still queued), ESTATE (frames not
+ * yet collected, or the stream had a bad mask), EDEVICE. */
+int rfsr_stream_export(rfsr_stream *s, void *buf, size_t cap, size_t *bytes);
+/* Create a stream on eng from an exported state.  *out is owned by the library until
+ * rfsr_destroy.  Errors: EINVAL (not a state buffer of this version, inconsistent size or
+ * configuration), ENOMEM, EAGAIN (the engine's memory budget is full now: nothing is created,
+ * retry later), EMASK, EDEVICE. */
+int rfsr_stream_import(rfsr_engine *eng, const void *buf, size_t bytes, rfsr_stream **out);
+
+/* Engine occupancy for placement decisions (rfsr_engine_get_info). */
+typedef struct {
+    int device;
+    size_t memory_budget;        /* bytes of device memory streams may use                         */
+    size_t memory_used;          /* bytes held by live streams                                     */
+    int streams_live;
+    int streams_queued;
+} rfsr_engine_info;
+int rfsr_engine_get_info(rfsr_engine *eng, rfsr_engine_info *info);
+
 /* Device time of the phases of the most recently pushed frame of s (waits for it), measured with
  * CUDA events on the engine's stream around each kernel: ms[0] ingest, ms[1] motion estimation,
  * ms[2] consistency checks (with the RME reverse field) + projection, ms[3] FSR + 8-bit

@@ -1190,6 +1190,101 @@ int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
     return RFSR_OK;
 }
 
+int rfsr_stream_export(rfsr_stream *s, void *buf, size_t cap, size_t *bytes)
+{
+    if (!s || !bytes) return fail(RFSR_EINVAL, "stream_export: NULL argument");
+    if (!s->live) return fail(RFSR_EAGAIN, "stream_export: stream is queued for admission");
+    const size_t HW = (size_t)s->H * s->W;
+    int hist;
+    long long frames;
+    {
+        std::lock_guard<std::mutex> g(s->eng->mu);
+        if (s->collected != s->pushed)
+            return fail(RFSR_ESTATE, "stream_export: collect every pushed frame first");
+        if (s->poisoned) return fail(RFSR_ESTATE, "stream_export: the stream had a bad mask");
+        hist = s->hist;
+        frames = s->pushed;
+    }
+    const size_t need = sizeof(rfsr_state_header) + (size_t)hist * 3 * HW;
+    *bytes = need;
+    if (!buf) return RFSR_OK;
+    if (cap < need) return fail(RFSR_EINVAL, "stream_export: buffer too small");
+    CK(cudaSetDevice(s->eng->cfg.device));
+    int rc = wait_all(s);
+    if (rc) return rc;
+    rfsr_state_header h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = RFSR_STATE_MAGIC;
+    h.version = RFSR_STATE_VERSION;
+    h.bytes = need;
+    h.config = s->cfg;
+    h.hist = hist;
+    h.frames = frames;
+    uint8_t *p = static_cast<uint8_t *>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const int R1 = s->K + 1;
+    for (int k = 1; k <= hist; ++k) {
+        const int rr = ((s->ring_head - k) % R1 + R1) % R1;
+        CK(cudaMemcpy(p, s->ring_rec[rr], HW, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(p + HW, s->ring_smp[rr], HW, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(p + 2 * HW, s->ring_msk[rr], HW, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < HW; ++i) p[2 * HW + i] = p[2 * HW + i] ? 1 : 0;   // byte mask -> 0/1
+        p += 3 * HW;
+    }
+    return RFSR_OK;
+}
+
+int rfsr_stream_import(rfsr_engine *e, const void *buf, size_t bytes, rfsr_stream **out)
+{
+    if (!e || !buf || !out) return fail(RFSR_EINVAL, "stream_import: NULL argument");
+    if (bytes < sizeof(rfsr_state_header)) return fail(RFSR_EINVAL, "stream_import: buffer too small");
+    rfsr_state_header h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != RFSR_STATE_MAGIC || h.version != RFSR_STATE_VERSION)
+        return fail(RFSR_EINVAL, "stream_import: not a stream state of this version");
+    int rc = check_stream_config(&h.config);
+    if (rc) return rc;
+    const size_t HW = (size_t)h.config.height * h.config.width;
+    if (h.hist < 0 || h.hist > h.config.num_refs || h.bytes != bytes ||
+        bytes != sizeof(h) + (size_t)h.hist * 3 * HW)
+        return fail(RFSR_EINVAL, "stream_import: inconsistent state size or history");
+    rfsr_stream *s = nullptr;
+    rc = rfsr_create_stream(e, &h.config, &s);
+    if (rc == RFSR_EAGAIN) {
+        rfsr_destroy(s);
+        return fail(RFSR_EAGAIN, "stream_import: the engine's memory budget is full; retry later");
+    }
+    if (rc) return rc;
+    std::vector<const uint8_t *> rec(h.hist), smp(h.hist), msk(h.hist);
+    const uint8_t *p = static_cast<const uint8_t *>(buf) + sizeof(h);
+    for (int k = 0; k < h.hist; ++k, p += 3 * HW) {
+        rec[k] = p;
+        smp[k] = p + HW;
+        msk[k] = p + 2 * HW;
+    }
+    rc = rfsr_set_history(s, h.hist, rec.data(), smp.data(), msk.data());
+    if (rc) {
+        const std::string msg = g_err;
+        rfsr_destroy(s);
+        return fail(rc, msg);
+    }
+    *out = s;
+    return RFSR_OK;
+}
+
+int rfsr_engine_get_info(rfsr_engine *e, rfsr_engine_info *info)
+{
+    if (!e || !info) return fail(RFSR_EINVAL, "engine_get_info: NULL argument");
+    std::lock_guard<std::mutex> g(e->mu);
+    info->device = e->cfg.device;
+    info->memory_budget = e->budget;
+    info->memory_used = e->used;
+    info->streams_queued = (int)e->queued.size();
+    info->streams_live = (int)e->streams.size() - info->streams_queued;
+    return RFSR_OK;
+}
+
 int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
 {
     if (!s || !dst) return fail(RFSR_EINVAL, "debug_get: NULL argument");

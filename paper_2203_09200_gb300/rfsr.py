@@ -57,6 +57,17 @@ class rfsr_tuning(C.Structure):
                 ("me_ns", C.c_float * 2), ("fsr_ns", C.c_float * 3)]
 
 
+class rfsr_state_header(C.Structure):
+    _fields_ = [("magic", C.c_uint32), ("version", C.c_uint32), ("bytes", C.c_uint64),
+                ("config", rfsr_stream_config), ("hist", C.c_int32), ("reserved", C.c_int32),
+                ("frames", C.c_int64)]
+
+
+class rfsr_engine_info(C.Structure):
+    _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("memory_used", C.c_size_t),
+                ("streams_live", C.c_int), ("streams_queued", C.c_int)]
+
+
 class rfsr_stream_info(C.Structure):
     _fields_ = [("height", C.c_int), ("width", C.c_int), ("live", C.c_int),
                 ("frames_pushed", C.c_longlong), ("frames_collected", C.c_longlong),
@@ -74,6 +85,9 @@ SYMBOLS = {
     "rfsr_engine_sync": ([_VP, _I], _I),
     "rfsr_engine_last_step_ms": ([_VP, C.POINTER(C.c_float), C.POINTER(C.c_int)], _I),
     "rfsr_engine_set_shape": ([_VP, C.POINTER(rfsr_batch_shape)], _I),
+    "rfsr_engine_get_info": ([_VP, C.POINTER(rfsr_engine_info)], _I),
+    "rfsr_stream_export": ([_VP, _VP, C.c_size_t, C.POINTER(C.c_size_t)], _I),
+    "rfsr_stream_import": ([_VP, _VP, C.c_size_t, C.POINTER(_VP)], _I),
     "rfsr_engine_get_tuning": ([_VP, C.POINTER(rfsr_tuning)], _I),
     "rfsr_create_stream": ([_VP, C.POINTER(rfsr_stream_config), C.POINTER(_VP)], _I),
     "rfsr_push_frame": ([_VP, _VP, _VP], _I),
@@ -184,6 +198,23 @@ class Engine:
         self.streams.append(s)
         return s
 
+    def import_stream(self, state: bytes) -> "Stream":
+        """rfsr_stream_import: a stream on this engine from rfsr_stream_export's bytes."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        h = C.c_void_p()
+        _check(load().rfsr_stream_import(self.handle, buf, len(state), C.byref(h)))
+        cfg = rfsr_state_header.from_buffer_copy(bytes(state)[:C.sizeof(rfsr_state_header)]).config
+        st = Stream(self, h, cfg)
+        self.streams.append(st)
+        return st
+
+    def info(self) -> dict:
+        """rfsr_engine_get_info."""
+        i = rfsr_engine_info()
+        _check(load().rfsr_engine_get_info(self.handle, C.byref(i)))
+        return {"device": i.device, "memory_budget": i.memory_budget, "memory_used": i.memory_used,
+                "streams_live": i.streams_live, "streams_queued": i.streams_queued}
+
     def last_step_ms(self):
         """(device ms, frames) of the most recent batched step (profile engines)."""
         ms, n = C.c_float(), C.c_int()
@@ -251,6 +282,14 @@ class Stream:
     def get_frame_device(self, d_out_u8=None, d_out_f32=None, timeout_ms: int = -1):
         _check(load().rfsr_get_frame_device(self.handle, _ptr(d_out_u8), _ptr(d_out_f32),
                                             timeout_ms))
+
+    def export_state(self) -> bytes:
+        """rfsr_stream_export: the stream's configuration and last K frames (checkpoint)."""
+        n = C.c_size_t()
+        _check(load().rfsr_stream_export(self.handle, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().rfsr_stream_export(self.handle, buf, n.value, C.byref(n)))
+        return buf.raw[:n.value]
 
     def set_history(self, history: Sequence[Tuple[np.ndarray, np.ndarray, np.ndarray]]):
         """history[k-1] = (reconstruction, samples, 0/1 mask) of frame t-k."""
@@ -337,3 +376,28 @@ def kernel_launches() -> int:
 # C-ABI names, for callers who prefer the flat interface
 rfsr_fsr_device = fsr_device
 rfsr_kernel_launches = kernel_launches
+
+
+class Router:
+    """Streams over several engines (replicas, for example one per GPU; streams are independent,
+    so nothing is exchanged between them).  A new stream goes to the engine with the most free
+    memory budget; migrate() moves a stream between engines through its exported state, so its
+    next frame gives exactly the result it would have given where it was."""
+
+    def __init__(self, engines: Sequence[Engine]):
+        self.engines = list(engines)
+
+    def place(self) -> Engine:
+        free = [(e.info()["memory_budget"] - e.info()["memory_used"], -i)
+                for i, e in enumerate(self.engines)]
+        return self.engines[-max(free)[1]]
+
+    def create_stream(self, **kw) -> Stream:
+        return self.place().create_stream(**kw)
+
+    def migrate(self, stream: Stream, to: Engine) -> Stream:
+        """Export, create on ``to``, then destroy the original (between frames)."""
+        state = stream.export_state()
+        moved = to.import_stream(state)
+        stream.destroy()
+        return moved

@@ -76,7 +76,9 @@ def test_struct_sizes_match_a_c_compiler(tmp_path):
                "rfsr_stream_config": rfsr.rfsr_stream_config,
                "rfsr_stream_info": rfsr.rfsr_stream_info,
                "rfsr_batch_shape": rfsr.rfsr_batch_shape,
-               "rfsr_tuning": rfsr.rfsr_tuning}
+               "rfsr_tuning": rfsr.rfsr_tuning,
+               "rfsr_state_header": rfsr.rfsr_state_header,
+               "rfsr_engine_info": rfsr.rfsr_engine_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rfsr.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
