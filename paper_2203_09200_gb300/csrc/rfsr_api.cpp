@@ -61,18 +61,27 @@ int cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
     } while (0)
 
-// host-side quarter-sampling check (Sec. 1): values 0/1 and exactly one 1 per 2x2 block
+// host-side quarter-sampling check (Sec. 1): values 0/1 and exactly one 1 per 2x2 block.  Eight
+// columns of two rows at a time: every byte <= 1, and each 2x2 block sums to one.
 bool mask_ok(const uint8_t *m, int H, int W)
 {
+    constexpr uint64_t kHigh = 0xfefefefefefefefeull, kLow = 0x00ff00ff00ff00ffull;
+    constexpr uint64_t kOne = 0x0001000100010001ull;
     for (int y = 0; y < H; y += 2) {
         const uint8_t *r0 = m + (size_t)y * W, *r1 = r0 + W;
-        unsigned bad = 0;
-        for (int x = 0; x < W; x += 2) {
-            const unsigned a = r0[x], b = r0[x + 1], c = r1[x], d = r1[x + 1];
-            bad |= (a | b | c | d) & ~1u;
-            bad |= (a + b + c + d) ^ 1u;
+        int x = 0;
+        for (; x + 8 <= W; x += 8) {
+            uint64_t a, b;
+            std::memcpy(&a, r0 + x, 8);
+            std::memcpy(&b, r1 + x, 8);
+            if ((a | b) & kHigh) return false;                    // a byte other than 0 / 1
+            const uint64_t s = a + b;                             // column sums 0..2 per byte
+            if (((s + (s >> 8)) & kLow) != kOne) return false;    // pairs of columns: one each
         }
-        if (bad) return false;
+        for (; x < W; x += 2) {
+            const unsigned a = r0[x], b = r0[x + 1], c = r1[x], d = r1[x + 1];
+            if (((a | b | c | d) & ~1u) || a + b + c + d != 1) return false;
+        }
     }
     return true;
 }
