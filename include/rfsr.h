@@ -93,6 +93,13 @@ typedef struct {
     int autotune;          /* batched engines, 1 (default): the first batched steps measure the
                               tile shapes (rfsr_batch_shape) and keep the fastest; 0: default
                               shape.  Results are identical for every shape.                    */
+    /* Optional device allocator for the engine's device memory (stream state, batch tables), for
+     * a caller that manages GPU memory itself (e.g. a framework's caching allocator).  NULL:
+     * cudaMalloc / cudaFree.  Set both or neither.  dev_alloc returns NULL on failure (ENOMEM);
+     * memory is released with dev_free only after every frame that used it has finished. */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;       /* passed to both callbacks                                          */
 } rfsr_engine_config;
 
 /* Tile shapes of the batched launches (a performance choice only; no counterpart in the paper,
@@ -163,6 +170,8 @@ int rfsr_engine_set_shape(rfsr_engine *eng, const rfsr_batch_shape *shape);
 int rfsr_engine_get_tuning(rfsr_engine *eng, rfsr_tuning *out);
 
 /* ---- streams (the four calls of the serving interface) ---------------------------------- */
+/* Every call below that takes an engine accepts NULL for a process-wide default engine (default
+ * configuration, created on first use on the calling thread's current device). */
 /* Create a video stream.  The stream owns its device state: K+1 ring slots of reconstruction,
  * sample plane and mask, the motion fields, decisions, projection sums and FSR output.  If that
  * state does not fit the engine's memory budget now, the stream is queued: *out is set and the
@@ -182,11 +191,14 @@ int rfsr_create_stream(rfsr_engine *eng, const rfsr_stream_config *cfg, rfsr_str
 int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask);
 
 /* As rfsr_push_frame, but samples and mask are DEVICE buffers (2-byte aligned, else EINVAL) that
- * must stay unchanged until the
- * frame has been collected (rfsr_get_frame / rfsr_get_frame_device returned it).  The mask is
- * validated on the GPU; a bad mask is reported as EMASK by the call that collects the frame, and
- * the frame then leaves the stream's history unchanged. */
-int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask);
+ * must stay unchanged until the frame has been collected (rfsr_get_frame / rfsr_get_frame_device
+ * returned it).  producer_stream is the cudaStream_t on which the caller wrote them: the engine's
+ * work waits for what was enqueued there up to this call (an event, no host wait); NULL means
+ * the buffers are already complete.  The mask is validated on the GPU; a bad mask is reported as
+ * EMASK by the call that collects the frame, and the frame then leaves the stream's history
+ * unchanged. */
+int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask,
+                           void *producer_stream);
 
 /* Collect the oldest uncollected frame (FIFO): out_u8 = 8-bit reconstruction (H x W host),
  * out_f32 = FSR output on the [0, 1] scale before quantisation (H x W host, may be NULL; needs

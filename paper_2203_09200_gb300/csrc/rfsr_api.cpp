@@ -148,6 +148,8 @@ struct Slot {
     int *h_status = nullptr;    // pinned, mapped
     int *h_status_dev = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t ready = nullptr;  // device pushes: recorded on the producer's stream
+    bool wait_ready = false;      // the engine's stream must wait for `ready` before this frame
     cudaEvent_t phase[5] = {};  // profile: before ingest, after ingest / ME / checks / FSR
     bool host_push = false;
     const uint8_t *in_smp = nullptr;   // staged input of a batched engine (device-visible)
@@ -231,8 +233,15 @@ struct rfsr_stream {
 
     int dev_alloc(void **p, size_t n)
     {
-        cudaError_t e = cudaMalloc(p, n);
-        if (e != cudaSuccess) return fail(RFSR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        const rfsr_engine_config &c = eng->cfg;
+        if (c.dev_alloc) {
+            *p = c.dev_alloc(n, c.alloc_ctx);
+            if (!*p) return fail(RFSR_ENOMEM, "dev_alloc callback returned NULL");
+        } else {
+            cudaError_t e = cudaMalloc(p, n);
+            if (e != cudaSuccess)
+                return fail(RFSR_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
         dev_allocs.push_back(*p);
         bytes += n;
         return RFSR_OK;
@@ -248,10 +257,14 @@ struct rfsr_stream {
     {
         for (auto &s : slots) {
             if (s.done) cudaEventDestroy(s.done);
+            if (s.ready) cudaEventDestroy(s.ready);
             for (auto &ev : s.phase)
                 if (ev) cudaEventDestroy(ev);
         }
-        for (void *p : dev_allocs) cudaFree(p);
+        for (void *p : dev_allocs) {
+            if (eng->cfg.dev_free) eng->cfg.dev_free(p, eng->cfg.alloc_ctx);
+            else cudaFree(p);
+        }
         for (void *p : host_allocs) cudaFreeHost(p);
         dev_allocs.clear();
         host_allocs.clear();
@@ -332,6 +345,7 @@ int admit(rfsr_stream *s)
         if (er != cudaSuccess) return bail(cuda_fail(er, "cudaHostGetDevicePointer"));
         *sl.h_status = 0;
         er = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (er == cudaSuccess) er = cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming);
         if (er != cudaSuccess) return bail(cuda_fail(er, "cudaEventCreate"));
         if (e->cfg.profile)
             for (auto &ev : sl.phase) {
@@ -432,6 +446,22 @@ int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint
     return RFSR_OK;
 }
 
+// device memory of the engine itself (batch tables): the caller's allocator when given
+cudaError_t engine_alloc(rfsr_engine *e, void **p, size_t n)
+{
+    if (e->cfg.dev_alloc) {
+        *p = e->cfg.dev_alloc(n, e->cfg.alloc_ctx);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, n);
+}
+
+void engine_free(rfsr_engine *e, void *p)
+{
+    if (e->cfg.dev_free) e->cfg.dev_free(p, e->cfg.alloc_ctx);
+    else cudaFree(p);
+}
+
 // launch the phases of one batch (captured into a graph, or directly); ph (tuning only): events
 // recorded before / after ME and before / after FSR
 cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape &sh, cudaStream_t st,
@@ -522,6 +552,13 @@ int step_batch_locked(rfsr_engine *e)
         ++n;
     }
     if (n == 0) return 0;
+    for (auto &p : taken) {                          // device pushes: their producers' work first
+        Slot &sl = p.first->slots[p.second];
+        if (sl.wait_ready) {
+            CK(cudaStreamWaitEvent(e->stream, sl.ready, 0));
+            sl.wait_ready = false;
+        }
+    }
     // tile shape of this step: a tuning candidate while the tuner measures, else the engine's
     Tuner &tu = e->tune;
     const bool tuning = tu.active;
@@ -677,6 +714,8 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     if (cfg->device < 0 || cfg->device >= ndev) return fail(RFSR_EINVAL, "engine_create: no such device");
     if (cfg->max_inflight < 0 || cfg->max_inflight > 64)
         return fail(RFSR_EINVAL, "engine_create: max_inflight out of range");
+    if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr))
+        return fail(RFSR_EINVAL, "engine_create: set both dev_alloc and dev_free, or neither");
     CK(cudaSetDevice(cfg->device));
     auto *e = new rfsr_engine();
     e->cfg = *cfg;
@@ -684,7 +723,7 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     auto bail = [&](cudaError_t er, const char *what) {
         for (auto &set : e->sets) {
             if (set.h) cudaFreeHost(set.h);
-            if (set.d) cudaFree(set.d);
+            if (set.d) engine_free(e, set.d);
             if (set.done) cudaEventDestroy(set.done);
             if (set.t0) cudaEventDestroy(set.t0);
             if (set.t1) cudaEventDestroy(set.t1);
@@ -709,7 +748,7 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     if (batched(e)) {
         for (auto &set : e->sets) {
             cudaError_t er = cudaHostAlloc((void **)&set.h, sizeof(BatchDesc), cudaHostAllocPortable);
-            if (er == cudaSuccess) er = cudaMalloc((void **)&set.d, sizeof(BatchDesc));
+            if (er == cudaSuccess) er = engine_alloc(e, (void **)&set.d, sizeof(BatchDesc));
             if (er == cudaSuccess) er = cudaEventCreateWithFlags(&set.done, cudaEventDisableTiming);
             if (er == cudaSuccess) er = cudaEventCreate(&set.t0);
             if (er == cudaSuccess) er = cudaEventCreate(&set.t1);
@@ -788,7 +827,7 @@ int rfsr_engine_destroy(rfsr_engine *e)
     for (auto &set : e->sets) {
         for (auto &kv : set.graphs) cudaGraphExecDestroy(kv.second);
         if (set.h) cudaFreeHost(set.h);
-        if (set.d) cudaFree(set.d);
+        if (set.d) engine_free(e, set.d);
         if (set.done) cudaEventDestroy(set.done);
         if (set.t0) cudaEventDestroy(set.t0);
         if (set.t1) cudaEventDestroy(set.t1);
@@ -904,9 +943,37 @@ static int check_stream_config(const rfsr_stream_config *c)
     return RFSR_OK;
 }
 
+// the process-wide engine used when a stream call passes NULL (created once, on the device that
+// is current for the first such call; it lives until the process ends)
+static rfsr_engine *default_engine(int *rc)
+{
+    static std::mutex m;
+    static rfsr_engine *eng = nullptr;
+    std::lock_guard<std::mutex> g(m);
+    *rc = RFSR_OK;
+    if (!eng) {
+        rfsr_engine_config c;
+        rfsr_engine_config_default(&c);
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            *rc = fail(RFSR_EDEVICE, "default engine: no CUDA device");
+            return nullptr;
+        }
+        c.device = dev;
+        *rc = rfsr_engine_create(&c, &eng);
+        if (*rc) eng = nullptr;
+    }
+    return eng;
+}
+
 int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_stream **out)
 {
-    if (!e || !cfg || !out) return fail(RFSR_EINVAL, "create_stream: NULL argument");
+    if (!cfg || !out) return fail(RFSR_EINVAL, "create_stream: NULL argument");
+    if (!e) {
+        int rc = 0;
+        e = default_engine(&rc);
+        if (!e) return rc;
+    }
     int rc = check_stream_config(cfg);
     if (rc) return rc;
     CK(cudaSetDevice(e->cfg.device));
@@ -964,6 +1031,7 @@ int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask)
     std::memcpy(sl.h_in, samples, HW);
     std::memcpy(sl.h_in + HW, mask, HW);
     sl.host_push = true;
+    sl.wait_ready = false;
     if (batched(e)) {
         sl.in_smp = sl.h_in_dev;
         sl.in_msk = sl.h_in_dev + HW;
@@ -985,7 +1053,8 @@ int rfsr_push_frame(rfsr_stream *s, const uint8_t *samples, const uint8_t *mask)
     return RFSR_OK;
 }
 
-int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask)
+int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8_t *d_mask,
+                           void *producer_stream)
 {
     if (!s || !d_samples || !d_mask) return fail(RFSR_EINVAL, "push_frame: NULL argument");
     if (((uintptr_t)d_samples | (uintptr_t)d_mask) & 1u)
@@ -998,6 +1067,10 @@ int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8
     const int si = (int)(s->pushed % (long long)s->slots.size());
     Slot &sl = s->slots[si];
     sl.host_push = false;
+    // the engine's stream waits for the producer's work on these buffers (no host wait)
+    const cudaStream_t prod = (cudaStream_t)producer_stream;
+    sl.wait_ready = prod != nullptr && prod != e->stream;
+    if (sl.wait_ready) CK(cudaEventRecord(sl.ready, prod));
     if (batched(e)) {
         sl.in_smp = d_samples;
         sl.in_msk = d_mask;
@@ -1006,6 +1079,10 @@ int rfsr_push_frame_device(rfsr_stream *s, const uint8_t *d_samples, const uint8
         lk.unlock();
         e->cv.notify_one();
         return RFSR_OK;
+    }
+    if (sl.wait_ready) {
+        CK(cudaStreamWaitEvent(e->stream, sl.ready, 0));
+        sl.wait_ready = false;
     }
     rc = enqueue_step(s, si, d_samples, d_mask);
     if (rc) return rc;
@@ -1246,7 +1323,7 @@ int rfsr_stream_export(rfsr_stream *s, void *buf, size_t cap, size_t *bytes)
 
 int rfsr_stream_import(rfsr_engine *e, const void *buf, size_t bytes, rfsr_stream **out)
 {
-    if (!e || !buf || !out) return fail(RFSR_EINVAL, "stream_import: NULL argument");
+    if (!buf || !out) return fail(RFSR_EINVAL, "stream_import: NULL argument");
     if (bytes < sizeof(rfsr_state_header)) return fail(RFSR_EINVAL, "stream_import: buffer too small");
     rfsr_state_header h;
     std::memcpy(&h, buf, sizeof(h));

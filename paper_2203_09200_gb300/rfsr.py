@@ -33,10 +33,15 @@ class RfsrError(RuntimeError):
         self.code = code
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class rfsr_engine_config(C.Structure):
     _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
                 ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int),
-                ("serve", C.c_int), ("autotune", C.c_int)]
+                ("serve", C.c_int), ("autotune", C.c_int), ("dev_alloc", ALLOC_FN),
+                ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class rfsr_stream_config(C.Structure):
@@ -91,7 +96,7 @@ SYMBOLS = {
     "rfsr_engine_get_tuning": ([_VP, C.POINTER(rfsr_tuning)], _I),
     "rfsr_create_stream": ([_VP, C.POINTER(rfsr_stream_config), C.POINTER(_VP)], _I),
     "rfsr_push_frame": ([_VP, _VP, _VP], _I),
-    "rfsr_push_frame_device": ([_VP, _VP, _VP], _I),
+    "rfsr_push_frame_device": ([_VP, _VP, _VP, _VP], _I),
     "rfsr_get_frame": ([_VP, _VP, _VP, _I], _I),
     "rfsr_get_frame_device": ([_VP, _VP, _VP, _I], _I),
     "rfsr_destroy": ([_VP], _I),
@@ -124,6 +129,30 @@ def load(path: str = LIB_PATH):
             fn.restype = res
         _lib = lib
     return _lib
+
+
+def _producer(stream, like):
+    if stream is None:
+        if getattr(like, "is_cuda", False):
+            import torch
+            return torch.cuda.current_stream(like.device).cuda_stream
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _torch_allocator(device: int):
+    import torch
+
+    def alloc(n, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(n), device)
+        except Exception:          # reported by the library as ENOMEM
+            return None
+
+    def free(p, ctx):
+        torch.cuda.caching_allocator_delete(p)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
 
 
 def _check(rc: int):
@@ -173,7 +202,9 @@ class Engine:
 
     def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
                  max_inflight: int = 4, batched: bool = False, profile: bool = False,
-                 serve: bool = False, autotune: bool = True):
+                 serve: bool = False, autotune: bool = True, allocator: Optional[str] = None):
+        """allocator="torch": the engine's device memory comes from PyTorch's caching allocator
+        (through the dev_alloc / dev_free callbacks of the engine config)."""
         lib = load()
         cfg = rfsr_engine_config()
         lib.rfsr_engine_config_default(C.byref(cfg))
@@ -181,6 +212,12 @@ class Engine:
         cfg.cuda_stream = cuda_stream
         cfg.max_inflight, cfg.batched, cfg.profile = max_inflight, int(batched), int(profile)
         cfg.serve, cfg.autotune = int(serve), int(autotune)
+        self._callbacks = None
+        if allocator == "torch":
+            self._callbacks = _torch_allocator(device)
+            cfg.dev_alloc, cfg.dev_free = self._callbacks
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
         h = C.c_void_p()
         _check(lib.rfsr_engine_create(C.byref(cfg), C.byref(h)))
         self.handle = h
@@ -269,8 +306,11 @@ class Stream:
         assert s.shape == (self.H, self.W) and m.shape == (self.H, self.W)
         _check(load().rfsr_push_frame(self.handle, s.ctypes.data, m.ctypes.data))
 
-    def push_frame_device(self, d_samples, d_mask):
-        _check(load().rfsr_push_frame_device(self.handle, _ptr(d_samples), _ptr(d_mask)))
+    def push_frame_device(self, d_samples, d_mask, stream=None):
+        """stream: the CUDA stream that wrote the buffers (a torch.cuda.Stream, a cudaStream_t
+        handle or None; None with torch tensors = the tensors' current torch stream)."""
+        _check(load().rfsr_push_frame_device(self.handle, _ptr(d_samples), _ptr(d_mask),
+                                             _producer(stream, d_samples)))
 
     def get_frame(self, timeout_ms: int = -1, f32: bool = False):
         out = np.empty((self.H, self.W), np.uint8)
