@@ -508,6 +508,30 @@ def run_quality(rfsr, torch):
     return res
 
 
+# ---------------------------------------------------------------------------------------------
+# N > 1: one independent replica per rank (weak scaling), times reduced by maximum
+# ---------------------------------------------------------------------------------------------
+def replica_seed(rank: int) -> int:
+    """Each rank runs the 1080p recipe with its own content seed (independent replicas)."""
+    return 3 + rank
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The whole job's time is the slowest rank's (all_reduce MAX; identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(frames_per_rank: int, world: int, pixels: int, seconds: float) -> float:
+    """HR Mpixel/s of the whole job: every rank's frames over the slowest rank's time."""
+    return frames_per_rank * world * pixels / seconds / 1e6
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -517,7 +541,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     pbuild.build()
-    seq = synth.config3(seed=3 + rank, F=F)
+    seq = synth.config3(seed=replica_seed(rank), F=F)
     HW = H * W
     d_smp = torch.from_numpy(seq.samples).cuda()
     d_msk = torch.from_numpy(seq.masks).cuda()
@@ -560,22 +584,15 @@ def run_ours(args, rank, world, local_rank):
     launches = rfsr.kernel_launches() - launches0
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_s = sum(step_ms) / 1e3
+    tot_s = max_over_ranks(sum(step_ms) / 1e3, world)
     if world > 1:
-        t = torch.tensor([tot_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
         dist.barrier()
     ph = np.array(phases)                       # (steps, 4): ingest, ME, checks+PR, FSR
     ph_mean = ph.mean(axis=0)
-    mecc_s = float(ph[:, :3].sum()) / 1e3       # ingest + ME + checks + projection, all steps
-    if world > 1:
-        t = torch.tensor([mecc_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mecc_s = float(t.item())
-    frames_total = args.steps * world
-    value = frames_total * HW / mecc_s / 1e6    # the metric: ME+CC+projection
-    full_value = frames_total * HW / tot_s / 1e6
+    # ingest + ME + checks + projection over all steps
+    mecc_s = max_over_ranks(float(ph[:, :3].sum()) / 1e3, world)
+    value = job_rate(args.steps, world, HW, mecc_s)     # the metric: ME+CC+projection
+    full_value = job_rate(args.steps, world, HW, tot_s)
 
     # e2e: host buffers through the public API, copies inside the timed region
     st2 = eng.create_stream(height=H, width=W, cc_mode="nnc_frmc", template_size=T,
@@ -598,12 +615,8 @@ def run_ours(args, rank, world, local_rank):
             st2.push_frame(host_s[f], host_m[f])
         st2.get_frame(timeout_ms=120000)
     torch.cuda.synchronize()
-    e_s = time.perf_counter() - e0
-    if world > 1:
-        t = torch.tensor([e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_s = float(t.item())
-    e2e = frames_total * HW / e_s / 1e6
+    e_s = max_over_ranks(time.perf_counter() - e0, world)
+    e2e = job_rate(args.steps, world, HW, e_s)
     eng.destroy()
     del d_smp, d_msk, flush
     batching = serving = check_modes = None

@@ -221,6 +221,9 @@ typedef struct {
     size_t device_bytes;   /* device memory held by this stream                                   */
 } rfsr_stream_info;
 int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info);
+/* Admission state of s: 1 live, 0 queued for memory (rfsr_create_stream returned EAGAIN),
+ * negative on error (EINVAL: NULL stream). */
+int rfsr_stream_state(rfsr_stream *s);
 
 /* Replace the history seen by the next pushed frame: for k = 1..nrefs, rec[k-1], smp[k-1] and
  * msk[k-1] are the reconstruction, sample plane and 0/1 mask of frame t-k (HOST buffers, H x W,

@@ -1210,6 +1210,13 @@ int rfsr_destroy(rfsr_stream *s)
     return RFSR_OK;
 }
 
+int rfsr_stream_state(rfsr_stream *s)
+{
+    if (!s) return fail(RFSR_EINVAL, "stream_state: NULL stream");
+    std::lock_guard<std::mutex> g(s->eng->mu);
+    return s->live ? 1 : 0;
+}
+
 int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info)
 {
     if (!s || !info) return fail(RFSR_EINVAL, "stream_get_info: NULL argument");

@@ -100,6 +100,7 @@ SYMBOLS = {
     "rfsr_get_frame": ([_VP, _VP, _VP, _I], _I),
     "rfsr_get_frame_device": ([_VP, _VP, _VP, _I], _I),
     "rfsr_destroy": ([_VP], _I),
+    "rfsr_stream_state": ([_VP], _I),
     "rfsr_stream_get_info": ([_VP, C.POINTER(rfsr_stream_info)], _I),
     "rfsr_set_history": ([_VP, _I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP)], _I),
     "rfsr_debug_get": ([_VP, _I, _I, _VP], _I),
@@ -359,7 +360,7 @@ class Stream:
 
     @property
     def live(self) -> bool:
-        return bool(self.info().live)
+        return _check(load().rfsr_stream_state(self.handle)) == 1
 
     def info(self) -> rfsr_stream_info:
         i = rfsr_stream_info()
