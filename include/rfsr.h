@@ -108,6 +108,9 @@ typedef struct {
     int me_tile_rows;      /* ME (T = 9) template tile of a CTA: 32 or 64 rows x 120 columns; the
                               staged search window is the tile + (T - 1) + 2R rows (default 64)  */
     int fsr_blocks;        /* FSR 4x4 blocks per CTA (one per warp): 2, 4 or 8 (default 4)        */
+    int me_variant;        /* ME algorithm for T = 9: 0 warp-strip byte SIMD (default), 1 sliding-
+                              window box sums over 32x64 tiles (same vectors: both are the exact
+                              argmin with the same tie order)                                    */
 } rfsr_batch_shape;
 
 /* State of a batched engine's autotuner (rfsr_engine_get_tuning). */
@@ -115,8 +118,8 @@ typedef struct {
     int tuned;                 /* 1: the shape is final (measured, set, or tuning off)            */
     int steps;                 /* tuning steps measured so far                                    */
     rfsr_batch_shape shape;    /* the shape the batched steps use now                             */
-    float me_ns[2];            /* mean device ns per pixel x reference, me_tile_rows 64 / 32
-                                  (0: not measured)                                               */
+    float me_ns[3];            /* mean device ns per pixel x reference: strips of 64 rows, strips of
+                                  32 rows, box sums (0: not measured)                             */
     float fsr_ns[3];           /* mean device ns per 4x4 block, fsr_blocks 4 / 2 / 8              */
 } rfsr_tuning;
 
@@ -164,8 +167,8 @@ int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
  * listed values), ESTATE (engine not batched). */
 int rfsr_engine_set_shape(rfsr_engine *eng, const rfsr_batch_shape *shape);
 /* Batched engines: the autotuner's state and measurements (ESTATE: engine not batched).  The
- * autotuner runs tuning step i with ME candidate i mod 2 (64 / 32 rows) and FSR candidate i mod
- * 3 (4 / 2 / 8 blocks), timing those two phases with CUDA events per unit of work, and keeps per
+ * autotuner runs tuning step i with ME candidate i mod 3 (strips of 64 / 32 rows, box sums) and
+ * FSR candidate i mod 3 (4 / 2 / 8 blocks), timing those two phases with CUDA events per unit of work, and keeps per
  * phase the fastest once each candidate has two measurements (at most 32 tuning steps). */
 int rfsr_engine_get_tuning(rfsr_engine *eng, rfsr_tuning *out);
 

@@ -541,11 +541,11 @@ __global__ void __launch_bounds__(R9_NT, 2) rme9_batched_kernel(BatchDesc *bd)
 
 }  // namespace
 
-int tiles_me(const FrameTask &t, int me_warps)
+int tiles_me(const FrameTask &t, int me_warps, int me_box)
 {
     if (t.K <= 0) return 0;
     const int outh = S_ROWS * me_warps;
-    if (t.T == 9) return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + outh - 1) / outh) * t.K;
+    if (t.T == 9 && !me_box) return ((t.W + S_OUTW - 1) / S_OUTW) * ((t.H + outh - 1) / outh) * t.K;
     return ((t.W + TW - 1) / TW) * ((t.H + TH - 1) / TH) * t.K;
 }
 
@@ -586,8 +586,9 @@ cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, cudaStream_t st)
+cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, int me_box, cudaStream_t st)
 {
+    if (T == 9 && me_box) T = 0;                 // the box-sum kernel below handles any T
     if (T == 9 && me_warps == 4) {
         static const int grid = persistent_grid(me9_batched_kernel<4>, s_nt<4>(), 0);
         me9_batched_kernel<4><<<grid, s_nt<4>(), 0, st>>>(bd);

@@ -131,7 +131,7 @@ int rfsr::set_error(int code, const std::string &msg) { return fail(code, msg); 
 
 bool rfsr::shape_valid(const BatchShape &s)
 {
-    return (s.me_warps == 4 || s.me_warps == 8) &&
+    return (s.me_warps == 4 || s.me_warps == 8) && (s.me_box == 0 || s.me_box == 1) &&
            (s.fsr_blocks == 2 || s.fsr_blocks == 4 || s.fsr_blocks == 8);
 }
 
@@ -177,8 +177,9 @@ struct BatchSet {                      // one of two alternating batch buffers
 // with the least device time per unit of work (ME: pixel x reference, FSR: 4x4 block); from then
 // on its steps are captured and replayed as CUDA graphs.
 struct Tuner {
-    static constexpr int kMe = 2, kFsr = 3, kSamples = 2, kMaxSteps = 32;
-    static constexpr int me_cand[kMe] = {8, 4};          // warp strips per ME tile (64 / 32 rows)
+    static constexpr int kMe = 3, kFsr = 3, kSamples = 2, kMaxSteps = 32;
+    static constexpr int me_cand[kMe] = {8, 4, 0};       // warp strips per ME tile (64 / 32 rows);
+                                                         // 0: the sliding-window box-sum kernel
     static constexpr int fsr_cand[kFsr] = {4, 2, 8};     // FSR blocks per CTA
     bool active = false;
     int steps = 0;                                       // tuning steps launched
@@ -470,7 +471,7 @@ cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape 
     cudaError_t e = launch_batch_prologue(d, st);
     if (e == cudaSuccess) e = launch_ingest_batched(d, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[0], st);
-    if (e == cudaSuccess) e = launch_me_batched(d, T, sh.me_warps, st);
+    if (e == cudaSuccess) e = launch_me_batched(d, T, sh.me_warps, sh.me_box, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[1], st);
     if (e == cudaSuccess && rme) e = launch_rme_batched(d, T, st);
     if (e == cudaSuccess) e = launch_cc_batched(d, T, st);
@@ -515,7 +516,10 @@ int harvest_tuning(rfsr_engine *e, BatchSet &set)
             }
         return best;
     };
-    e->shape.me_warps = pick(tu.me_ns, tu.me_n, Tuner::me_cand, Tuner::kMe, e->shape.me_warps);
+    const int me = pick(tu.me_ns, tu.me_n, Tuner::me_cand, Tuner::kMe,
+                        e->shape.me_box ? 0 : e->shape.me_warps);
+    e->shape.me_box = me == 0 ? 1 : 0;
+    e->shape.me_warps = me == 0 ? 8 : me;
     e->shape.fsr_blocks = pick(tu.fsr_ns, tu.fsr_n, Tuner::fsr_cand, Tuner::kFsr, e->shape.fsr_blocks);
     tu.active = false;
     return RFSR_OK;
@@ -569,7 +573,8 @@ int step_batch_locked(rfsr_engine *e)
         sh.fsr_blocks = Tuner::fsr_cand[cfsr];
         if (T == 9) {
             cme = tu.steps % Tuner::kMe;
-            sh.me_warps = Tuner::me_cand[cme];
+            sh.me_warps = Tuner::me_cand[cme] ? Tuner::me_cand[cme] : 8;
+            sh.me_box = Tuner::me_cand[cme] ? 0 : 1;
         }
     }
     bd->ntasks = n;
@@ -577,7 +582,7 @@ int step_batch_locked(rfsr_engine *e)
     double me_units = 0, fsr_units = 0;
     for (int i = 0; i < n; ++i) {
         const FrameTask &t = bd->task[i];
-        const int c[kPhases] = {tiles_ingest(t), tiles_me(t, sh.me_warps), tiles_rme(t), tiles_cc(t),
+        const int c[kPhases] = {tiles_ingest(t), tiles_me(t, sh.me_warps, sh.me_box), tiles_rme(t), tiles_cc(t),
                                 tiles_fsr(t, sh.fsr_blocks)};
         for (int p = 0; p < kPhases; ++p) {
             bd->off[p][i] = tot[p];
@@ -881,9 +886,11 @@ int rfsr_engine_set_shape(rfsr_engine *e, const rfsr_batch_shape *shape)
     if (!batched(e)) return fail(RFSR_ESTATE, "engine_set_shape: engine is not batched");
     BatchShape sh;
     sh.me_warps = shape->me_tile_rows / 8;
+    sh.me_box = shape->me_variant;
     sh.fsr_blocks = shape->fsr_blocks;
     if ((shape->me_tile_rows != 32 && shape->me_tile_rows != 64) || !shape_valid(sh))
-        return fail(RFSR_EINVAL, "engine_set_shape: me_tile_rows must be 32 or 64, fsr_blocks 2, 4 or 8");
+        return fail(RFSR_EINVAL, "engine_set_shape: me_tile_rows must be 32 or 64, me_variant 0 or 1, "
+                                 "fsr_blocks 2, 4 or 8");
     CK(cudaSetDevice(e->cfg.device));
     std::lock_guard<std::mutex> g(e->mu);
     for (auto &set : e->sets) {                      // graphs of the old shape go
@@ -915,6 +922,7 @@ int rfsr_engine_get_tuning(rfsr_engine *e, rfsr_tuning *out)
     out->tuned = tu.active ? 0 : 1;
     out->steps = tu.measured;
     out->shape.me_tile_rows = 8 * e->shape.me_warps;
+    out->shape.me_variant = e->shape.me_box;
     out->shape.fsr_blocks = e->shape.fsr_blocks;
     for (int i = 0; i < Tuner::kMe; ++i) out->me_ns[i] = tu.me_n[i] ? (float)(tu.me_ns[i] / tu.me_n[i]) : 0.f;
     for (int i = 0; i < Tuner::kFsr; ++i)

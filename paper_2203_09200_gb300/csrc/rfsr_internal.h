@@ -80,13 +80,14 @@ struct BatchDesc {
 // only in how the work is cut, so the engine may choose among them by measurement.
 struct BatchShape {
     int me_warps = 8;                      // ME (T = 9): 8-row warp strips stacked per CTA (4 | 8)
+    int me_box = 0;                        // ME (T = 9): 1 = the sliding-window box-sum kernel
     int fsr_blocks = 4;                    // FSR: 4x4 blocks (one per warp) per CTA (2 | 4 | 8)
 };
 bool shape_valid(const BatchShape &s);
 
 // tiles of a task in each phase (the single-stream launches use the default shape)
 int tiles_ingest(const FrameTask &t);
-int tiles_me(const FrameTask &t, int me_warps = 8);
+int tiles_me(const FrameTask &t, int me_warps = 8, int me_box = 0);
 int tiles_rme(const FrameTask &t);
 int tiles_cc(const FrameTask &t);
 int tiles_fsr(const FrameTask &t, int fsr_blocks = 4);
@@ -159,7 +160,7 @@ int persistent_grid(K kernel, int threads, size_t smem)
 // the sequence can be captured in a CUDA graph
 cudaError_t launch_batch_prologue(BatchDesc *bd, cudaStream_t st);
 cudaError_t launch_ingest_batched(BatchDesc *bd, cudaStream_t st);
-cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, cudaStream_t st);
+cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, int me_box, cudaStream_t st);
 cudaError_t launch_rme_batched(BatchDesc *bd, int T, cudaStream_t st);
 // RME reverse field for T = 9 (tiled; other T use the direct search of cc.cu)
 int tiles_rme9(const FrameTask &t);

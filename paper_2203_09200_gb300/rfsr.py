@@ -54,12 +54,12 @@ class rfsr_stream_config(C.Structure):
 
 
 class rfsr_batch_shape(C.Structure):
-    _fields_ = [("me_tile_rows", C.c_int), ("fsr_blocks", C.c_int)]
+    _fields_ = [("me_tile_rows", C.c_int), ("fsr_blocks", C.c_int), ("me_variant", C.c_int)]
 
 
 class rfsr_tuning(C.Structure):
     _fields_ = [("tuned", C.c_int), ("steps", C.c_int), ("shape", rfsr_batch_shape),
-                ("me_ns", C.c_float * 2), ("fsr_ns", C.c_float * 3)]
+                ("me_ns", C.c_float * 3), ("fsr_ns", C.c_float * 3)]
 
 
 class rfsr_state_header(C.Structure):
@@ -262,9 +262,9 @@ class Engine:
     def step(self) -> int:
         return _check(load().rfsr_engine_step(self.handle))
 
-    def set_shape(self, me_tile_rows: int = 64, fsr_blocks: int = 4):
+    def set_shape(self, me_tile_rows: int = 64, fsr_blocks: int = 4, me_variant: int = 0):
         """rfsr_engine_set_shape: fix the batched tile shape (ends autotuning)."""
-        sh = rfsr_batch_shape(me_tile_rows, fsr_blocks)
+        sh = rfsr_batch_shape(me_tile_rows, fsr_blocks, me_variant)
         _check(load().rfsr_engine_set_shape(self.handle, C.byref(sh)))
 
     def tuning(self) -> dict:
@@ -272,8 +272,11 @@ class Engine:
         t = rfsr_tuning()
         _check(load().rfsr_engine_get_tuning(self.handle, C.byref(t)))
         return {"tuned": bool(t.tuned), "steps": t.steps,
-                "shape": {"me_tile_rows": t.shape.me_tile_rows, "fsr_blocks": t.shape.fsr_blocks},
-                "me_ns_per_pixel_ref": {"64": round(t.me_ns[0], 5), "32": round(t.me_ns[1], 5)},
+                "shape": {"me_tile_rows": t.shape.me_tile_rows, "fsr_blocks": t.shape.fsr_blocks,
+                          "me_variant": t.shape.me_variant},
+                "me_ns_per_pixel_ref": {"strips64": round(t.me_ns[0], 5),
+                                        "strips32": round(t.me_ns[1], 5),
+                                        "box": round(t.me_ns[2], 5)},
                 "fsr_ns_per_block": {"4": round(t.fsr_ns[0], 3), "2": round(t.fsr_ns[1], 3),
                                      "8": round(t.fsr_ns[2], 3)}}
 

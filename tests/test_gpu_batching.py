@@ -89,15 +89,17 @@ def test_batched_steps_equal_streams_alone(built):
                     np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PCNT), pcnt)
 
 
-@pytest.mark.parametrize("rows,blocks", [(64, 4), (32, 4), (64, 2), (32, 2), (64, 8), (32, 8)])
-def test_every_batch_shape_equals_streams_alone(built, rows, blocks):
+@pytest.mark.parametrize("rows,blocks,variant", [(64, 4, 0), (32, 4, 0), (64, 2, 0), (32, 2, 0),
+                                                 (64, 8, 0), (32, 8, 0), (64, 4, 1)])
+def test_every_batch_shape_equals_streams_alone(built, rows, blocks, variant):
     """Each tile shape the autotuner can choose gives the same bits as the streams run alone."""
     F = 4
     seqs = sequences(F)
     alone = run_alone(seqs, F, planes=False)
     with rfsr.Engine(device=0, batched=True, autotune=False) as eng:
-        eng.set_shape(me_tile_rows=rows, fsr_blocks=blocks)
-        assert eng.tuning()["shape"] == {"me_tile_rows": rows, "fsr_blocks": blocks}
+        eng.set_shape(me_tile_rows=rows, fsr_blocks=blocks, me_variant=variant)
+        assert eng.tuning()["shape"] == {"me_tile_rows": rows, "fsr_blocks": blocks,
+                                         "me_variant": variant}
         sts = [eng.create_stream(height=H, width=W, cc_mode=mode, keep_f32=True)
                for H, W, _, mode, _ in SPECS]
         for t in range(F):
