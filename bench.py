@@ -724,8 +724,8 @@ def summarize_launches(path):
 def run_ncu_case(args):
     """A short, untimed kernel sequence for an ncu capture: 'frame_step' runs `frames` frames of
     the 1080p workload on one unbatched stream (device-resident inputs, check mode --cc-mode);
-    'batched' runs `frames`
-    batched steps of the 64-stream mix (default tile shape, no autotuning)."""
+    'batched' runs `frames` batched steps of --streams streams of the uneven-size mix (default
+    tile shape, no autotuning)."""
     import torch
     from paper_2203_09200_gb300 import build as pbuild
     from paper_2203_09200_gb300 import rfsr
@@ -742,7 +742,7 @@ def run_ncu_case(args):
                 st.push_frame_device(d_smp[f], d_msk[f])
                 st.get_frame_device(timeout_ms=120000)
     else:
-        specs = synth.config4_streams(n_streams=64, frames=nf)
+        specs = synth.config4_streams(n_streams=args.streams, frames=nf)
         streams = crop_streams(synth.config2(seed=44, H=1080, W=1920, F=nf), specs, nf)
         d_in = [[(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in zip(sm, mk)]
                 for _, sm, mk in streams]
@@ -771,6 +771,7 @@ def main():
     ap.add_argument("--ncu-case", choices=["frame_step", "batched"],
                     help="run only a short untimed kernel sequence (for ncu captures)")
     ap.add_argument("--frames", type=int, default=6, help="frames of --ncu-case")
+    ap.add_argument("--streams", type=int, default=64, help="streams of --ncu-case batched")
     ap.add_argument("--cc-mode", default="nnc_frmc", choices=list(MODES),
                     help="consistency-check mode of --ncu-case frame_step")
     ap.add_argument("--quality", action="store_true",
