@@ -28,7 +28,10 @@
 // median field once, decides every pixel, and compacts the pixels that need a reverse check into
 // a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
 // registers, lane 0 scores d = 0 and the other lanes split the remaining offsets, each costing T
-// rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.
+// rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.  The
+// current frame's copies use a 26-word row stride and a copy stride of 3 mod 32, and the offsets
+// are dealt to lanes (per column phase, nearest first) so that the 32 lanes of a round read 32
+// distinct banks for every template word.
 #include "rfsr_internal.h"
 
 namespace rfsr {

@@ -6,8 +6,13 @@
 // with b_t = 0 outside the frame and past-frame coordinates clamped to the border.  Equal costs
 // are resolved by the tie order |v|_1, then v_y, then v_x (the paper gives none).
 //
-// GB300 design: integer-only, no tensor cores.  One CTA owns a TH x TW tile of outputs for one
-// past frame; the current tile (plus the template halo) and the past-frame window (plus the
+// GB300 design: integer-only, no tensor cores.  Three exact kernels live here: me9_kernel (T = 9,
+// warp strips with byte SIMD and packed 16-bit sums, below), the general sliding-window box-sum
+// kernel (any T, this paragraph), and rme9_kernel, the RME reverse field for T = 9 (end of the
+// file).  Batched engines choose the ME kernel for T = 9 by measurement (both give the same
+// vectors).
+//
+// Box-sum kernel: one CTA owns a TH x TW tile of outputs for one past frame; the current tile (plus the template halo) and the past-frame window (plus the
 // search margin) are staged once in shared memory.  Candidates are visited in tie order and, for
 // each, the cost of every output in the tile comes from a separable sliding-window box sum over
 // the masked absolute-difference plane D_v(x) = b_t(x) |f_sub_t(x) - rec(clamp(x+v))|:
