@@ -251,6 +251,60 @@ def test_full_frame_1080p_every_pixel(engine):
     compare(got, ref, msk, smp)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_constant_video(engine, mode):
+    """Degenerate content: every frame constant.  Every candidate ties (the tie order decides),
+    every check passes, and FSR must return the constant."""
+    H, W = 48, 80
+    rng = np.random.default_rng(5)
+    perm = synth.dynamic_permutations(H, W, rng)
+    frame = np.full((H, W), 137, np.uint8)
+    masks = [synth.positions_to_mask(synth.dynamic_positions(perm, t)) for t in range(4)]
+    hist = [(frame, (frame * masks[3 - k]).astype(np.uint8), masks[3 - k]) for k in (1, 2, 3)]
+    smp, msk = (frame * masks[3]).astype(np.uint8), masks[3]
+    got = gpu_step(engine, smp, msk, hist, cc_mode=mode)
+    ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NAMES[mode], T=9, R=8)
+    compare(got, ref, msk, smp)
+    np.testing.assert_array_equal(got["rec"], frame)
+
+
+def test_maximum_frame_size(engine):
+    """The largest frame the ABI accepts (8192 x 8192, one past frame, NNC+FRMC): frame 0 (FSR
+    only) on sampled blocks, frame 1 against a generator-made past frame on sampled pixels."""
+    H = W = 8192
+    rng = np.random.default_rng(77)
+    f0 = rng.integers(0, 256, size=(H, W), dtype=np.int64).astype(np.uint8)
+    f1 = np.roll(f0, (2, 3), axis=(0, 1))
+    m0 = synth.positions_to_mask(synth.fixed_positions(H, W, rng))
+    m1 = synth.positions_to_mask(synth.fixed_positions(H, W, rng))
+    s0, s1 = (f0 * m0).astype(np.uint8), (f1 * m1).astype(np.uint8)
+    st = engine.create_stream(height=H, width=W, num_refs=1, cc_mode="nnc_frmc", keep_f32=True)
+    try:
+        st.push_frame(s0, m0)
+        rec0, g0 = st.get_frame(timeout_ms=120000, f32=True)
+        st.set_history([(f0, s0, m0)])
+        st.push_frame(s1, m1)
+        st.get_frame(timeout_ms=120000)
+        mv, fmv, dec = (st.debug_get(w, 1) for w in (rfsr.DBG_MV, rfsr.DBG_FMV, rfsr.DBG_DECISION))
+        psum, pcnt = st.debug_get(rfsr.DBG_PSUM), st.debug_get(rfsr.DBG_PCNT)
+    finally:
+        st.destroy()
+    np.testing.assert_array_equal(rec0[m0 == 1], s0[m0 == 1])
+    P = oracle.FsrParams()
+    nb = H // 4
+    blocks = [(0, 0), (0, nb - 1), (nb - 1, 0), (nb - 1, nb - 1)]
+    blocks += [(int(rng.integers(0, nb)), int(rng.integers(0, nb))) for _ in range(20)]
+    for by, bx in blocks:
+        got = np.ascontiguousarray(g0[4 * by:4 * by + 4, 4 * bx:4 * bx + 4])
+        ok, e0, it = oracle.fsr_block_valid(P, s0, m0, None, None, by, bx, got)
+        assert ok, (by, bx, e0)
+    for (y, x) in sample_pixels(H, W, 40, seed=8):
+        d, v, fv, pv = oracle.cc_pixel(oracle.CC_NNC_FRMC, 9, 8, 8, s1, m1, f0, s0, m0, y, x)
+        assert tuple(mv[y, x]) == v and tuple(fmv[y, x]) == fv and dec[y, x] == d, (y, x)
+        assert psum[y, x] == (pv if d == oracle.DEC_ACCEPT else 0), (y, x)
+        assert pcnt[y, x] == (1 if d == oracle.DEC_ACCEPT else 0), (y, x)
+
+
 def test_fsr_device_full_hd_sampled(engine):
     """Stand-alone FSR over a full 1920x1080 frame with generator-made projections."""
     seq = synth.config3(F=1)
