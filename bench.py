@@ -347,6 +347,32 @@ def run_check_modes(rfsr, torch, steps=8):
     return out
 
 
+def run_unloaded_latency(rfsr, torch, frames=12):
+    """Per-frame latency of the serving engine with one stream alone and one frame in flight
+    (host buffers, push -> collected), per size of the arrival mix: the service time that the
+    loaded runs add queueing to."""
+    import time as _t
+    base = synth.config3(seed=56, H=2160, W=3840, F=4)
+    out = {}
+    for (H, W) in SIZES5:
+        rng = np.random.default_rng(H + W)
+        perm = synth.dynamic_permutations(H, W, rng)
+        ms = [synth.positions_to_mask(synth.dynamic_positions(perm, t)) for t in range(4)]
+        sm = [np.ascontiguousarray(base.frames[t, :H, :W] * ms[t]) for t in range(4)]
+        with rfsr.Engine(device=torch.cuda.current_device(), serve=True, max_inflight=2) as eng:
+            st = eng.create_stream(height=H, width=W)
+            lat = []
+            for t in range(frames):
+                t0 = _t.perf_counter()
+                st.push_frame(sm[t % 4], ms[t % 4])
+                st.get_frame(timeout_ms=120000)
+                if t >= 3:
+                    lat.append(1e3 * (_t.perf_counter() - t0))
+        out[f"{W}x{H}"] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 3)}
+    return out
+
+
 def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=5, memory_budget=0):
     """Poisson arrivals on a serving engine, closed loop with <= 2 frames in flight per stream:
     per-frame latency (push returned -> result collected) and aggregate throughput."""
@@ -626,6 +652,7 @@ def run_ours(args, rank, world, local_rank):
             rfsr, torch, small_streams(), what="256 streams of 320x240, half fixed / half dynamic masks")
         serving = run_serving(rfsr, torch)
         serving["budget_2gb"] = run_serving(rfsr, torch, memory_budget=2 << 30)
+        serving["unloaded"] = run_unloaded_latency(rfsr, torch)
         check_modes = run_check_modes(rfsr, torch)
 
     if rank != 0:
