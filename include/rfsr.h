@@ -147,7 +147,7 @@ void rfsr_stream_config_default(rfsr_stream_config *cfg);
 /* Create an engine on cfg->device.  *out is owned by the library until rfsr_engine_destroy.
  * Errors: EINVAL (NULL / bad field), EDEVICE (no such device, stream creation failed). */
 int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out);
-/* Waits for all work, destroys all streams of the engine and frees everything. */
+/* Waits for all work, destroys all streams of the engine and frees everything (EINVAL: NULL). */
 int rfsr_engine_destroy(rfsr_engine *eng);
 /* Batched engines: one frame step (Fig. 1) over every live stream that has a staged frame.
  * Each phase (ingest, ME, RME field, checks + projection, FSR) is one persistent launch over the
@@ -160,7 +160,8 @@ int rfsr_engine_step(rfsr_engine *eng);
 /* Device time of the most recently launched batched step (waits for it) and its frame count.
  * Needs a batched engine created with profile = 1 (else ESTATE). */
 int rfsr_engine_last_step_ms(rfsr_engine *eng, float *ms, int *frames);
-/* Wait (bounded) until all launched work of the engine is done.  ETIMEDOUT on timeout. */
+/* Wait (bounded) until all launched work of the engine is done.  Errors: ETIMEDOUT, ESTATE
+ * (a batched engine without a serving thread still has staged frames: call rfsr_engine_step). */
 int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
 /* Batched engines: use this tile shape from the next step on (waits for the engine's launched
  * work, drops its captured graphs and ends autotuning).  Errors: EINVAL (shape not one of the
@@ -168,8 +169,9 @@ int rfsr_engine_sync(rfsr_engine *eng, int timeout_ms);
 int rfsr_engine_set_shape(rfsr_engine *eng, const rfsr_batch_shape *shape);
 /* Batched engines: the autotuner's state and measurements (ESTATE: engine not batched).  The
  * autotuner runs tuning step i with ME candidate i mod 3 (strips of 64 / 32 rows, box sums) and
- * FSR candidate i mod 3 (4 / 2 / 8 blocks), timing those two phases with CUDA events per unit of work, and keeps per
- * phase the fastest once each candidate has two measurements (at most 32 tuning steps). */
+ * FSR candidate i mod 3 (4 / 2 / 8 blocks), timing those two phases with CUDA events per unit of
+ * work, and keeps per phase the fastest once each candidate has two measurements (at most 32
+ * tuning steps). */
 int rfsr_engine_get_tuning(rfsr_engine *eng, rfsr_tuning *out);
 
 /* ---- streams (the four calls of the serving interface) ---------------------------------- */
@@ -212,7 +214,8 @@ int rfsr_get_frame(rfsr_stream *s, uint8_t *out_u8, float *out_f32, int timeout_
 /* As rfsr_get_frame, into DEVICE buffers (either may be NULL). */
 int rfsr_get_frame_device(rfsr_stream *s, uint8_t *d_out_u8, float *d_out_f32, int timeout_ms);
 
-/* Destroy a stream.  Waits for its frames in flight, then frees its device and host state. */
+/* Destroy a stream.  Waits for its frames in flight, then frees its device and host state.
+ * A queued stream leaves the admission queue.  Errors: EINVAL (NULL). */
 int rfsr_destroy(rfsr_stream *s);
 
 /* ---- state, history injection and debug planes (parity tests, checkpointing) ------------ */
@@ -223,7 +226,7 @@ typedef struct {
     int history_frames;    /* past frames available to the next frame (0..K)                      */
     size_t device_bytes;   /* device memory held by this stream                                   */
 } rfsr_stream_info;
-int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info);
+int rfsr_stream_get_info(rfsr_stream *s, rfsr_stream_info *info);   /* EINVAL: NULL argument */
 /* Admission state of s: 1 live, 0 queued for memory (rfsr_create_stream returned EAGAIN),
  * negative on error (EINVAL: NULL stream). */
 int rfsr_stream_state(rfsr_stream *s);
@@ -250,8 +253,9 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst);
 /* Reconstruct every 4x4 block of an H x W frame from its 32x32 support.  d_smp: sample plane
  * (H*W uint8), d_msk: 0/1 mask (H*W uint8), d_psum / d_pcnt: projection sums and counts (H*W
  * uint16 / uint8, both NULL for single-frame FSR; d_psum 2-byte aligned).  Outputs: d_out_f32
- * (H*W float, [0,1] scale, 4-byte aligned, may be NULL) and d_out_u8 (H*W uint8, may be NULL).  cfg supplies the fsr_* fields and
- * height / width.  Runs on cuda_stream (cudaStream_t, NULL = legacy default stream) and returns
+ * (H*W float, [0,1] scale, 4-byte aligned, may be NULL) and d_out_u8 (H*W uint8, may be NULL).
+ * cfg supplies the fsr_* fields and height / width.  Runs on cuda_stream (cudaStream_t,
+ * NULL = legacy default stream) and returns
  * without waiting.  Errors: EINVAL, EDEVICE. */
 int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
                     const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
@@ -296,7 +300,7 @@ typedef struct {
     int streams_live;
     int streams_queued;
 } rfsr_engine_info;
-int rfsr_engine_get_info(rfsr_engine *eng, rfsr_engine_info *info);
+int rfsr_engine_get_info(rfsr_engine *eng, rfsr_engine_info *info);   /* EINVAL: NULL argument */
 
 /* Device time of the phases of the most recently pushed frame of s (waits for it), measured with
  * CUDA events on the engine's stream around each kernel: ms[0] ingest, ms[1] motion estimation,

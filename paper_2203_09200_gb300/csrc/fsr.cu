@@ -27,7 +27,8 @@
 //   * Selection: one pass per lane keeps its maximum and its bin, the warp maximum comes from
 //     __reduce_max_sync on the (non-negative) float bits and the lowest canonical index among the
 //     lanes that reach it from __reduce_min_sync.  The winning bin is the same in every lane, so
-//     the owner lane reads R there through one uniform switch and a shuffle pair sends it out.  The rank-2 residual update works on (Re, Im) as packed FP32 pairs
+//     the owner lane reads R there through one uniform switch and a shuffle pair sends it out.
+//     The rank-2 residual update works on (Re, Im) as packed FP32 pairs
 //     (R -= dr (a + c) + di (c.y - a.y, a.x - c.x)): one pair add, two scalar subtractions and two
 //     pair FMAs per bin.
 //   * The per-warp shared memory is one 12.5 KB union (support, row spectra, W).

@@ -12,9 +12,10 @@
 // file).  Batched engines choose the ME kernel for T = 9 by measurement (both give the same
 // vectors).
 //
-// Box-sum kernel: one CTA owns a TH x TW tile of outputs for one past frame; the current tile (plus the template halo) and the past-frame window (plus the
-// search margin) are staged once in shared memory.  Candidates are visited in tie order and, for
-// each, the cost of every output in the tile comes from a separable sliding-window box sum over
+// Box-sum kernel: one CTA owns a TH x TW tile of outputs for one past frame; the current tile
+// (plus the template halo) and the past-frame window (plus the search margin) are staged once in
+// shared memory.  Candidates are visited in tie order and, for each, the cost of every output in
+// the tile comes from a separable sliding-window box sum over
 // the masked absolute-difference plane D_v(x) = b_t(x) |f_sub_t(x) - rec(clamp(x+v))|:
 //   1. D_v over the (TH+2h) x (TW+2h) region,
 //   2. vertical running sums over T rows (column sums),

@@ -608,7 +608,8 @@ int step_batch_locked(rfsr_engine *e)
             cudaGraphExec_t ex = nullptr;
             cudaError_t er = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
             if (er == cudaSuccess) {
-                cudaError_t er2 = cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream);
+                cudaError_t er2 = cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc),
+                                                  cudaMemcpyHostToDevice, e->stream);
                 if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, sh, e->stream);
                 er = cudaStreamEndCapture(e->stream, &g);
                 if (er == cudaSuccess) er = er2;
@@ -1118,7 +1119,8 @@ static int collect(rfsr_stream *s, int timeout_ms, Slot **out)
         }
         if (timeout_ms >= 0 &&
             std::chrono::duration_cast<std::chrono::milliseconds>(Clock::now() - t0).count() >= timeout_ms)
-            return fail(RFSR_ETIMEDOUT, "frame not launched within timeout (batched engine: call rfsr_engine_step)");
+            return fail(RFSR_ETIMEDOUT,
+                        "frame not launched within timeout (batched engine: call rfsr_engine_step)");
         if (spins < 2000) std::this_thread::yield();
         else std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
