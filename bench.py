@@ -85,10 +85,16 @@ KERNEL_PROFILES = {"fsr_kernel": ("fsr_kernel_1080p.md", ["fsr.cu", "rfsr_intern
 
 
 def kernel_source_sha(kernel):
+    """Hash of the kernel's source code without comments and whitespace (an edit to a comment
+    does not change the kernel the counters were taken on)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_PROFILES[kernel][1]:
-        h.update(open(os.path.join(CSRC, f), "rb").read())
+        src = open(os.path.join(CSRC, f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(re.sub(r"\s+", "", src).encode())
     return h.hexdigest()[:16]
 
 
