@@ -112,6 +112,10 @@ def _load():
         lib.orc_fsr_block_alt.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I,
                                           I, dp, dp, dp, dp, dp, dp, ip, dp, dp, I]
         lib.orc_fsr_frame.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, dp, dp]
+        lib.orc_fsr_frame_concealed.argtypes = [C.POINTER(_FsrParams), C.c_double, u8p, u8p, u16p,
+                                                u8p, I, I, dp, dp]
+        lib.orc_fsr_support.argtypes = [C.POINTER(_FsrParams), C.c_double, dp, u8p, u8p, u16p, u8p,
+                                        I, I, I, I, dp, dp]
         lib.orc_quantize.argtypes = [dp, u8p, u8p, I, I, u8p]
         lib.orc_set_threads.argtypes = [I]
         if omp:
@@ -323,6 +327,41 @@ def fsr_frame(params: FsrParams, smp, msk, psum=None, pcnt=None):
     lib.orc_fsr_frame(C.byref(cp), _p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(psum, C.c_uint16),
                       _p(pcnt, C.c_uint8), H, W, _p(out, C.c_double), _p(gap, C.c_double))
     return out, gap
+
+
+def fsr_frame_concealed(params: FsrParams, delta: float, smp, msk, psum=None, pcnt=None):
+    """FSR of every block in raster order with concealed weighting delta (the original FSR: the
+    pixels of earlier blocks that are neither measured nor projected join the support with weight
+    delta rho^d); delta = 0 equals fsr_frame.  Returns (H x W output, per-block min gap)."""
+    lib = _load()
+    smp, msk = _u8(smp), _u8(msk)
+    H, W = smp.shape
+    psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
+    pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
+    out = np.zeros((H, W))
+    gap = np.zeros((-(-H // params.B), -(-W // params.B)))
+    cp = params._c()
+    lib.orc_fsr_frame_concealed(C.byref(cp), float(delta), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
+                                _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W,
+                                _p(out, C.c_double), _p(gap, C.c_double))
+    return out, gap
+
+
+def fsr_support(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by, bx):
+    """(weights, values) of the N x N support of block (by, bx)."""
+    lib = _load()
+    smp, msk = _u8(smp), _u8(msk)
+    H, W = smp.shape
+    conc = None if conc is None else np.ascontiguousarray(conc, np.float64)
+    psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
+    pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
+    w = np.zeros((params.N, params.N))
+    f = np.zeros((params.N, params.N))
+    cp = params._c()
+    lib.orc_fsr_support(C.byref(cp), float(delta), _p(conc, C.c_double), _p(smp, C.c_uint8),
+                        _p(msk, C.c_uint8), _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, by, bx,
+                        _p(w, C.c_double), _p(f, C.c_double))
+    return w, f
 
 
 def quantize(x, smp, msk) -> np.ndarray:

@@ -477,17 +477,53 @@ static void dft2_real(const double *a, int N, const double *tc, const double *ts
         }
 }
 
+/* The N x N support of block (by, bx) (Sec. 2.1): known pixels are the measured ones (value
+ * s/255, weight rho^d, d = distance to the support centre) and the projected ones (value
+ * psum / (255 pcnt), weight proj_weight rho^d); with concealed weighting delta > 0 (the original
+ * FSR, which the paper sets to zero in Sec. 4 so that blocks are independent), the pixels of
+ * blocks already reconstructed in raster order that are neither measured nor projected are known
+ * too, with value conc (their reconstruction) and weight delta rho^d.  Everything else, and
+ * everything outside the frame, has weight 0. */
+static void fsr_support(const orc_fsr_params *P, double delta, const double *conc,
+                        const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
+                        const uint8_t *pcnt, int H, int W, int by, int bx, double *w, double *f)
+{
+    const int N = P->N, B = P->B, o = (P->N - P->B) / 2;
+    const double c = (N - 1) / 2.0;
+    for (int m = 0; m < N; ++m)
+        for (int n = 0; n < N; ++n) {
+            int y = B * by - o + m, x = B * bx - o + n;
+            double d = sqrt((m - c) * (m - c) + (n - c) * (n - c));
+            double wt = 0.0, val = 0.0;
+            if (inside(y, x, H, W)) {
+                size_t i = (size_t)y * W + x;
+                int earlier = y / B < by || (y / B == by && x / B < bx);
+                if (msk[i]) { wt = pow(P->rho, d); val = smp[i] / 255.0; }
+                else if (pcnt && pcnt[i] > 0) {
+                    wt = P->proj_weight * pow(P->rho, d);
+                    val = (double)psum[i] / (255.0 * pcnt[i]);
+                } else if (conc && delta > 0.0 && earlier) {
+                    wt = delta * pow(P->rho, d);
+                    val = conc[i];
+                }
+            }
+            w[m * N + n] = wt;
+            f[m * N + n] = val;
+        }
+}
+
 /* Extended form for tests: besides the B*B block output it can return the support weights and
  * values, the model g over the whole support, the final residual spectrum, the selected bins, the
  * relative gap between the best and second best selection criterion at every iteration and their
  * minimum.  A near tie (tiny gap) means that another rounding of the same arithmetic may select
  * the other bin; both continuations are results of the method.  second_at >= 0 takes the second
  * best bin at that one iteration (the other resolution of a near tie); -1 = plain argmax. */
-void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
-                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
-                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
-                       double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
-                       int second_at)
+static void fsr_block_core(const orc_fsr_params *P, double delta, const double *conc,
+                           const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
+                           const uint8_t *pcnt, int H, int W, int by, int bx, double *out,
+                           double *w_out, double *f_out, double *g_out, double *rre_out,
+                           double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
+                           int second_at)
 {
     const int N = P->N, B = P->B, o = (P->N - P->B) / 2;
     static _Thread_local double w[ORC_NMAX * ORC_NMAX], f[ORC_NMAX * ORC_NMAX];
@@ -496,28 +532,13 @@ void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_
     static _Thread_local double Rre[ORC_NMAX * ORC_NMAX], Rim[ORC_NMAX * ORC_NMAX];
     static _Thread_local double g[ORC_NMAX * ORC_NMAX], fw[ORC_NMAX * ORC_NMAX];
     static _Thread_local double tc[ORC_NMAX], ts[ORC_NMAX];
-    const double c = (N - 1) / 2.0;
     twiddles(N, tc, ts);
-
-    for (int m = 0; m < N; ++m)
-        for (int n = 0; n < N; ++n) {
-            int y = B * by - o + m, x = B * bx - o + n;
-            double d = sqrt((m - c) * (m - c) + (n - c) * (n - c));
-            double wt = 0.0, val = 0.0;
-            if (inside(y, x, H, W)) {
-                size_t i = (size_t)y * W + x;
-                if (msk[i]) { wt = pow(P->rho, d); val = smp[i] / 255.0; }
-                else if (pcnt && pcnt[i] > 0) {
-                    wt = P->proj_weight * pow(P->rho, d);
-                    val = (double)psum[i] / (255.0 * pcnt[i]);
-                }
-            }
-            w[m * N + n] = wt;
-            f[m * N + n] = val;
-            fw[m * N + n] = wt * val;
-            g[m * N + n] = 0.0;
-            wf[m * N + n] = freq_weight(m, n, N);
-        }
+    fsr_support(P, delta, conc, smp, msk, psum, pcnt, H, W, by, bx, w, f);
+    for (int i = 0; i < N * N; ++i) {
+        fw[i] = w[i] * f[i];
+        g[i] = 0.0;
+        wf[i] = freq_weight(i / N, i % N, N);
+    }
     dft2_real(w, N, tc, ts, Wre, Wim);
     dft2_real(fw, N, tc, ts, Rre, Rim);
 
@@ -585,6 +606,16 @@ void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_
     if (min_gap_out) *min_gap_out = min_gap;
 }
 
+void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
+                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
+                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
+                       double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
+                       int second_at)
+{
+    fsr_block_core(P, 0.0, NULL, smp, msk, psum, pcnt, H, W, by, bx, out, w_out, f_out, g_out,
+                   rre_out, rim_out, sel_out, min_gap_out, gaps_out, second_at);
+}
+
 void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
@@ -621,6 +652,41 @@ void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *m
                     if (inside(y, x, H, W)) out[(size_t)y * W + x] = blk[m * B + n];
                 }
         }
+}
+
+/* FSR of every block with concealed weighting delta (the original FSR; the paper uses delta = 0,
+ * Sec. 4): blocks are reconstructed one after the other in raster order, and each sees the pixels
+ * of the blocks before it that are neither measured nor projected as known pixels with their
+ * reconstruction as value and weight delta rho^d.  out (H x W) also serves as that input; the
+ * result for delta = 0 equals orc_fsr_frame. */
+void orc_fsr_frame_concealed(const orc_fsr_params *P, double delta, const uint8_t *smp,
+                             const uint8_t *msk, const uint16_t *psum, const uint8_t *pcnt, int H,
+                             int W, double *out, double *min_gap)
+{
+    int B = P->B, nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
+    memset(out, 0, sizeof(double) * (size_t)H * W);
+    for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx) {
+            double blk[ORC_NMAX * ORC_NMAX];
+            double gap;
+            fsr_block_core(P, delta, out, smp, msk, psum, pcnt, H, W, by, bx, blk, 0, 0, 0, 0, 0, 0,
+                           &gap, 0, -1);
+            if (min_gap) min_gap[by * nbx + bx] = gap;
+            for (int m = 0; m < B; ++m)
+                for (int n = 0; n < B; ++n) {
+                    int y = B * by + m, x = B * bx + n;
+                    if (inside(y, x, H, W)) out[(size_t)y * W + x] = blk[m * B + n];
+                }
+        }
+}
+
+/* The support (weights and values) of block (by, bx) with concealed weighting delta and
+ * concealed values conc (H x W), for the tests. */
+void orc_fsr_support(const orc_fsr_params *P, double delta, const double *conc, const uint8_t *smp,
+                     const uint8_t *msk, const uint16_t *psum, const uint8_t *pcnt, int H, int W,
+                     int by, int bx, double *w_out, double *f_out)
+{
+    fsr_support(P, delta, conc, smp, msk, psum, pcnt, H, W, by, bx, w_out, f_out);
 }
 
 /* 8-bit reconstruction: measured pixels keep their sample, all others are 255*x rounded half to

@@ -567,3 +567,63 @@ def test_openmp_build_gives_identical_results():
         np.testing.assert_array_equal(a.pcnt, b.pcnt)
         np.testing.assert_array_equal(a.fsr, b.fsr)
         np.testing.assert_array_equal(a.rec, b.rec)
+
+
+# --------------------------------------------------------------------------------------------
+# concealed weighting delta > 0 (the original FSR; the paper uses 0, Sec. 4)
+# --------------------------------------------------------------------------------------------
+def _conc_inputs(H=40, W=44, seed=12):
+    seq = synth.config2(seed=seed, H=H, W=W, F=1)
+    smp, msk = seq.samples[0], seq.masks[0]
+    rng = np.random.default_rng(seed)
+    pcnt = np.where((msk == 0) & (rng.random((H, W)) < 0.3), 1, 0).astype(np.uint8)
+    psum = (pcnt.astype(np.uint16) * seq.frames[0]).astype(np.uint16)
+    return seq, smp, msk, psum, pcnt
+
+
+def test_concealed_support_follows_its_definition():
+    """Weights: rho^d measured, mu rho^d projected, delta rho^d for the pixels of earlier blocks
+    (raster order) that are neither, 0 otherwise -- built here independently in numpy."""
+    seq, smp, msk, psum, pcnt = _conc_inputs()
+    H, W = smp.shape
+    P = oracle.FsrParams(proj_weight=0.8)
+    delta = 0.37
+    conc = np.random.default_rng(1).random((H, W))
+    for by, bx in [(0, 0), (3, 5), (9, 10), (4, 0)]:
+        w, f = oracle.fsr_support(P, delta, conc, smp, msk, psum, pcnt, by, bx)
+        N, B, o = P.N, P.B, (P.N - P.B) // 2
+        cc = (N - 1) / 2.0
+        for m in range(N):
+            for n in range(N):
+                y, x = B * by - o + m, B * bx - o + n
+                d = np.hypot(m - cc, n - cc)
+                ew, ef = 0.0, 0.0
+                if 0 <= y < H and 0 <= x < W:
+                    earlier = y // B < by or (y // B == by and x // B < bx)
+                    if msk[y, x]:
+                        ew, ef = P.rho ** d, smp[y, x] / 255.0
+                    elif pcnt[y, x]:
+                        ew, ef = P.proj_weight * P.rho ** d, psum[y, x] / (255.0 * pcnt[y, x])
+                    elif earlier:
+                        ew, ef = delta * P.rho ** d, conc[y, x]
+                assert abs(w[m, n] - ew) < 1e-12 and abs(f[m, n] - ef) < 1e-12, (by, bx, m, n)
+
+
+def test_concealed_zero_delta_equals_parallel_fsr():
+    seq, smp, msk, psum, pcnt = _conc_inputs()
+    P = oracle.FsrParams(iterations=30)
+    a, _ = oracle.fsr_frame(P, smp, msk, psum, pcnt)
+    b, _ = oracle.fsr_frame_concealed(P, 0.0, smp, msk, psum, pcnt)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_concealed_first_block_and_constant_frame():
+    seq, smp, msk, psum, pcnt = _conc_inputs()
+    P = oracle.FsrParams(iterations=30)
+    a, _ = oracle.fsr_frame(P, smp, msk, psum, pcnt)
+    b, _ = oracle.fsr_frame_concealed(P, 0.5, smp, msk, psum, pcnt)
+    np.testing.assert_array_equal(a[:4, :4], b[:4, :4])      # block (0, 0) has nothing earlier
+    assert np.abs(a - b).max() > 1e-6                         # later blocks see concealed pixels
+    flat = np.full(smp.shape, 90, np.uint8)
+    c, _ = oracle.fsr_frame_concealed(P, 0.5, (flat * msk).astype(np.uint8), msk)
+    np.testing.assert_allclose(c, 90 / 255.0, atol=1e-12)
