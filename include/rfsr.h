@@ -137,6 +137,13 @@ typedef struct {
     float fsr_proj_weight; /* weight factor of projected pixels (default 1: same as measured)     */
     int fsr_overwrite_projected; /* 0: D-FSR (Sec. 3.2, default); 1: R-FSR overwrite          */
     int keep_f32;          /* 1: keep the FP32 FSR output of every frame for rfsr_get_frame      */
+    float fsr_concealed_weight; /* delta >= 0 (default 0, Sec. 4: every block independent).  delta
+                              > 0 is the original FSR: the pixels of blocks already reconstructed
+                              in raster order that are neither measured nor projected join the
+                              support with weight delta rho^d and their reconstruction as value;
+                              blocks then run as wavefronts (block (i, j) after (i-1, j+4) and
+                              (i, j-1)), one launch per wave, far slower.  Unbatched engines only
+                              (EINVAL on batched ones); rfsr_fsr_device then needs d_out_f32.    */
 } rfsr_stream_config;
 
 /* Fill a config with the defaults above (1280x720, NNC_FRMC, K=3, T=9, R=8). */
@@ -279,7 +286,7 @@ typedef struct {
     int64_t frames;              /* frames the exported stream had processed                       */
 } rfsr_state_header;
 #define RFSR_STATE_MAGIC 0x54534652u   /* "RFST" */
-#define RFSR_STATE_VERSION 1u
+#define RFSR_STATE_VERSION 2u
 
 /* Export s into buf (cap bytes); *bytes receives the size needed (buf == NULL: size query).
  * Taken between frames: every pushed frame must have been collected.

@@ -111,6 +111,8 @@ def _load():
                                          dp, dp, dp, dp, dp, dp, ip, dp]
         lib.orc_fsr_block_alt.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I,
                                           I, dp, dp, dp, dp, dp, dp, ip, dp, dp, I]
+        lib.orc_fsr_block_conc.argtypes = [C.POINTER(_FsrParams), C.c_double, dp, u8p, u8p,
+                                           u16p, u8p, I, I, I, I, dp, dp, dp, I]
         lib.orc_fsr_frame.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, dp, dp]
         lib.orc_fsr_frame_concealed.argtypes = [C.POINTER(_FsrParams), C.c_double, u8p, u8p, u16p,
                                                 u8p, I, I, dp, dp]
@@ -309,6 +311,42 @@ def fsr_block_valid(params: FsrParams, smp, msk, psum, pcnt, by, bx, got, tol: f
     for i in order:
         alt = fsr_block(params, smp, msk, psum, pcnt, by, bx, second_at=i)
         if float(np.abs(np.asarray(got, np.float64) - alt.out).max()) <= tol:
+            return True, e0, i
+    return False, e0, -1
+
+
+def fsr_block_concealed(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by, bx,
+                        second_at: int = -1):
+    """FSR of block (by, bx) with concealed weighting delta, the pixels of the blocks before it in
+    raster order taking their values from conc (H x W).  Returns (B x B output, min gap, gaps per
+    iteration); second_at as in fsr_block."""
+    lib = _load()
+    smp, msk = _u8(smp), _u8(msk)
+    H, W = smp.shape
+    conc = np.ascontiguousarray(conc, np.float64)
+    psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
+    pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
+    out = np.zeros((params.B, params.B))
+    gaps = np.zeros(max(1, params.iterations))
+    gap = C.c_double()
+    lib.orc_fsr_block_conc(C.byref(params._c()), float(delta), _p(conc, C.c_double),
+                           _p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(psum, C.c_uint16),
+                           _p(pcnt, C.c_uint8), H, W, by, bx, _p(out, C.c_double), C.byref(gap),
+                           _p(gaps, C.c_double), int(second_at))
+    return out, gap.value, gaps[:params.iterations]
+
+
+def fsr_block_concealed_valid(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by,
+                              bx, got, tol: float = 1e-4, near: float = 1e-3, tries: int = 12):
+    """fsr_block_valid for concealed weighting delta with concealed values conc."""
+    out, _, gaps = fsr_block_concealed(params, delta, conc, smp, msk, psum, pcnt, by, bx)
+    e0 = float(np.abs(np.asarray(got, np.float64) - out).max())
+    if e0 <= tol:
+        return True, e0, -1
+    for i in [int(i) for i in np.argsort(gaps) if gaps[i] < near][:tries]:
+        alt, _, _ = fsr_block_concealed(params, delta, conc, smp, msk, psum, pcnt, by, bx,
+                                        second_at=i)
+        if float(np.abs(np.asarray(got, np.float64) - alt).max()) <= tol:
             return True, e0, i
     return False, e0, -1
 

@@ -616,6 +616,17 @@ void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_
                    rre_out, rim_out, sel_out, min_gap_out, gaps_out, second_at);
 }
 
+/* orc_fsr_block_alt with concealed weighting delta and concealed values conc (H x W; the
+ * reconstruction of the blocks before (by, bx) in raster order), for the tests. */
+void orc_fsr_block_conc(const orc_fsr_params *P, double delta, const double *conc,
+                        const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
+                        const uint8_t *pcnt, int H, int W, int by, int bx, double *out,
+                        double *min_gap_out, double *gaps_out, int second_at)
+{
+    fsr_block_core(P, delta, conc, smp, msk, psum, pcnt, H, W, by, bx, out, 0, 0, 0, 0, 0, 0,
+                   min_gap_out, gaps_out, second_at);
+}
+
 void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,

@@ -73,8 +73,9 @@ struct FsrArgs {
     const FsrTables *tab;
     const int *status;
     int *status_out;
+    const float *conc;                     // concealed weighting: this frame's output so far
     int H, W, iters, overwrite;
-    float gamma, mu;
+    float gamma, mu, delta;
 };
 
 __device__ __forceinline__ void fsr_args(FsrArgs &a, const FrameTask &t)
@@ -95,6 +96,8 @@ __device__ __forceinline__ void fsr_args(FsrArgs &a, const FrameTask &t)
     a.overwrite = t.fsr_overwrite_projected;
     a.gamma = t.fsr_gamma;
     a.mu = t.fsr_proj_weight;
+    a.conc = t.fsr_out;
+    a.delta = t.fsr_concealed;
 }
 
 struct Twiddles {
@@ -231,9 +234,10 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     {
         const uint8_t *msk = a.msk, *smp = a.smp, *pcnt = a.pcnt;
         const uint16_t *psum = a.psum;
-        const float mu = a.mu;
+        const float mu = a.mu, delta = a.delta;
         const int x = xs + lane;
         const bool xin = (unsigned)x < (unsigned)W;
+        const bool xearlier = x / kFsrB < bj;   // column of a block left of this one
 #pragma unroll 4
         for (int m = 0; m < N; ++m) {
             const int y = ys + m;
@@ -250,6 +254,9 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
                 } else if (c) {
                     wt = mu * wd;
                     val = (float)ps / (255.0f * (float)c);
+                } else if (delta > 0.f && (y / kFsrB < bi || (y / kFsrB == bi && xearlier))) {
+                    wt = delta * wd;                     // reconstructed earlier (raster order)
+                    val = a.conc[i];
                 }
             }
             ws.sup.w[m * SS + lane] = wt;
@@ -428,6 +435,24 @@ __global__ void __launch_bounds__(WPB1 * 32, 4) fsr_kernel(FrameTask t)
     fsr_block(sm.tw, sm.w[warp], a, blockIdx.x * WPB1 + warp);
 }
 
+// Concealed weighting > 0: block (i, j) reads the blocks before it in raster order that overlap
+// its support (rows i-4 .. i-1 at columns j-4 .. j+4, and row i left of j), so blocks run as
+// wavefronts w = 5 i + j -- every such block has a smaller w.  One launch per wave; warp b of the
+// launch takes the b-th block (i = i_lo + b, j = w - 5 i) of that wave.
+__global__ void __launch_bounds__(WPB1 * 32, 4) fsr_wave_kernel(FrameTask t, int wave, int i_lo,
+                                                                 int count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<WPB1> &sm = *reinterpret_cast<Smem<WPB1> *>(smem_raw);
+    load_twiddles(sm.tw);
+    const int warp = threadIdx.x >> 5, b = blockIdx.x * WPB1 + warp;
+    if (b >= count) return;
+    const int i = i_lo + b, j = wave - 5 * i;
+    FsrArgs a;
+    fsr_args(a, t);
+    fsr_block(sm.tw, sm.w[warp], a, i * ((t.W + kFsrB - 1) / kFsrB) + j);
+}
+
 // batched form: CTAs claim tiles (WPB consecutive blocks of one task) in increasing order from
 // the batch's tile queue, so each tile runs as in the single-stream launch (its warps start
 // together on adjacent blocks and share their support rows in L1).  The next claim is issued
@@ -489,6 +514,7 @@ cudaError_t init_fsr(int dev)
     cudaError_t e = cudaMemcpyToSymbol(c_cs, cs, sizeof(cs));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sn, sn, sizeof(sn));
     if (e == cudaSuccess) e = smem_attr(fsr_kernel, sizeof(Smem<WPB1>));
+    if (e == cudaSuccess) e = smem_attr(fsr_wave_kernel, sizeof(Smem<WPB1>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2>, sizeof(Smem<2>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4>, sizeof(Smem<4>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8>, sizeof(Smem<8>));
@@ -534,6 +560,19 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
     if (e != cudaSuccess) return e;
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
+    if (t.fsr_concealed > 0.f) {                       // wavefronts, one launch per wave
+        const int nby = (t.H + kFsrB - 1) / kFsrB, nbx = (t.W + kFsrB - 1) / kFsrB;
+        for (int w = 0; w <= 5 * (nby - 1) + nbx - 1; ++w) {
+            const int i_lo = w - (nbx - 1) > 0 ? (w - (nbx - 1) + 4) / 5 : 0;
+            const int i_hi = w / 5 < nby - 1 ? w / 5 : nby - 1;
+            const int count = i_hi - i_lo + 1;
+            if (count <= 0) continue;
+            fsr_wave_kernel<<<(count + WPB1 - 1) / WPB1, WPB1 * 32, sizeof(Smem<WPB1>), st>>>(
+                t, w, i_lo, count);
+            count_launch();
+        }
+        return cudaGetLastError();
+    }
     fsr_kernel<<<tiles_fsr(t, WPB1), WPB1 * 32, sizeof(Smem<WPB1>), st>>>(t);
     count_launch();
     return cudaGetLastError();

@@ -391,6 +391,7 @@ void prepare_frame(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const ui
     t.cc_mode = s->cfg.cc_mode;
     t.fsr_iters = s->cfg.fsr_iterations;
     t.fsr_gamma = s->cfg.fsr_gamma;
+    t.fsr_concealed = s->cfg.fsr_concealed_weight;
     t.fsr_proj_weight = s->cfg.fsr_proj_weight;
     t.fsr_overwrite_projected = s->cfg.fsr_overwrite_projected;
     t.fsr_tables = s->tables;
@@ -949,6 +950,8 @@ static int check_stream_config(const rfsr_stream_config *c)
     if (!(c->fsr_rho > 0.f && c->fsr_rho <= 1.f)) return fail(RFSR_EINVAL, "stream config: fsr_rho");
     if (!(c->fsr_gamma > 0.f && c->fsr_gamma <= 2.f)) return fail(RFSR_EINVAL, "stream config: fsr_gamma");
     if (!(c->fsr_proj_weight >= 0.f)) return fail(RFSR_EINVAL, "stream config: fsr_proj_weight");
+    if (!(c->fsr_concealed_weight >= 0.f && c->fsr_concealed_weight <= 1e6f))
+        return fail(RFSR_EINVAL, "stream config: fsr_concealed_weight must be >= 0");
     return RFSR_OK;
 }
 
@@ -985,6 +988,8 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
     }
     int rc = check_stream_config(cfg);
     if (rc) return rc;
+    if (cfg->fsr_concealed_weight > 0.f && batched(e))
+        return fail(RFSR_EINVAL, "create_stream: concealed weighting > 0 needs an unbatched engine");
     CK(cudaSetDevice(e->cfg.device));
     auto *s = new rfsr_stream();
     s->eng = e;
@@ -1448,6 +1453,8 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
         return fail(RFSR_EINVAL, "fsr_device: psum must be 2-byte and out_f32 4-byte aligned");
     int rc = check_stream_config(cfg);
     if (rc) return rc;
+    if (cfg->fsr_concealed_weight > 0.f && !d_out_f32)
+        return fail(RFSR_EINVAL, "fsr_device: concealed weighting > 0 reads d_out_f32, which is NULL");
     // tables and a zero status word, cached per (device, rho)
     static std::mutex mu;
     static std::map<std::pair<int, float>, std::pair<float *, int *>> cache;
@@ -1478,6 +1485,7 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
     t.W = cfg->width;
     t.fsr_iters = cfg->fsr_iterations;
     t.fsr_gamma = cfg->fsr_gamma;
+    t.fsr_concealed = cfg->fsr_concealed_weight;
     t.fsr_proj_weight = cfg->fsr_proj_weight;
     t.fsr_overwrite_projected = cfg->fsr_overwrite_projected;
     t.fsr_tables = tables;

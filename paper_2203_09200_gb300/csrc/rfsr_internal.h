@@ -31,6 +31,7 @@ struct FrameTask {
     // FSR
     int fsr_iters;
     float fsr_gamma;
+    float fsr_concealed;       // concealed weighting delta (0: blocks independent)
     float fsr_proj_weight;
     int fsr_overwrite_projected;
     const float *fsr_tables;   // FsrTables in device memory

@@ -50,7 +50,7 @@ class rfsr_stream_config(C.Structure):
                 ("search_radius", C.c_int), ("check_radius", C.c_int),
                 ("fsr_iterations", C.c_int), ("fsr_rho", C.c_float), ("fsr_gamma", C.c_float),
                 ("fsr_proj_weight", C.c_float), ("fsr_overwrite_projected", C.c_int),
-                ("keep_f32", C.c_int)]
+                ("keep_f32", C.c_int), ("fsr_concealed_weight", C.c_float)]
 
 
 class rfsr_batch_shape(C.Structure):
@@ -180,8 +180,8 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
                   num_refs: int = 3, template_size: int = 9, search_radius: int = 8,
                   check_radius: Optional[int] = None, fsr_iterations: int = 100,
                   fsr_rho: float = 0.7, fsr_gamma: float = 0.5, fsr_proj_weight: float = 1.0,
-                  fsr_overwrite_projected: bool = False, keep_f32: bool = False
-                  ) -> rfsr_stream_config:
+                  fsr_overwrite_projected: bool = False, keep_f32: bool = False,
+                  fsr_concealed_weight: float = 0.0) -> rfsr_stream_config:
     c = rfsr_stream_config()
     load().rfsr_stream_config_default(C.byref(c))
     c.height, c.width = height, width
@@ -195,6 +195,7 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
     c.fsr_rho, c.fsr_gamma, c.fsr_proj_weight = fsr_rho, fsr_gamma, fsr_proj_weight
     c.fsr_overwrite_projected = int(bool(fsr_overwrite_projected))
     c.keep_f32 = int(bool(keep_f32))
+    c.fsr_concealed_weight = fsr_concealed_weight
     return c
 
 

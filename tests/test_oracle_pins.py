@@ -627,3 +627,31 @@ def test_concealed_first_block_and_constant_frame():
     flat = np.full(smp.shape, 90, np.uint8)
     c, _ = oracle.fsr_frame_concealed(P, 0.5, (flat * msk).astype(np.uint8), msk)
     np.testing.assert_allclose(c, 90 / 255.0, atol=1e-12)
+
+
+def test_concealed_block_reads_only_earlier_blocks():
+    """A block of the raster-order frame equals the block computed alone from the frame's final
+    output, and values of the block itself or of later blocks in conc change nothing."""
+    seq, smp, msk, psum, pcnt = _conc_inputs()
+    P = oracle.FsrParams(iterations=30)
+    delta = 0.5
+    out, gap = oracle.fsr_frame_concealed(P, delta, smp, msk, psum, pcnt)
+    rng = np.random.default_rng(4)
+    for by, bx in [(0, 0), (0, 7), (3, 0), (5, 6), (9, 10)]:
+        blk, g, _ = oracle.fsr_block_concealed(P, delta, out, smp, msk, psum, pcnt, by, bx)
+        np.testing.assert_array_equal(blk, out[4 * by:4 * by + 4, 4 * bx:4 * bx + 4])
+        assert g == gap[by, bx]
+        later = out.copy()
+        ys, xs = np.mgrid[0:out.shape[0], 0:out.shape[1]]
+        tail = (ys // 4 > by) | ((ys // 4 == by) & (xs // 4 >= bx))
+        later[tail] = rng.random(int(tail.sum()))
+        blk2, _, _ = oracle.fsr_block_concealed(P, delta, later, smp, msk, psum, pcnt, by, bx)
+        np.testing.assert_array_equal(blk, blk2)
+    # a value in an earlier block that is neither measured nor projected does change the result
+    y, x = next((y, x) for y in range(4, 8) for x in range(4, 8)
+                if msk[y, x] == 0 and pcnt[y, x] == 0)
+    moved = out.copy()
+    moved[y, x] += 0.25
+    a, _, _ = oracle.fsr_block_concealed(P, delta, out, smp, msk, psum, pcnt, 2, 2)
+    b, _, _ = oracle.fsr_block_concealed(P, delta, moved, smp, msk, psum, pcnt, 2, 2)
+    assert np.abs(a - b).max() > 1e-6
