@@ -30,6 +30,15 @@ __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b, uint32_t c)
     else return a ^ b;
 }
 
+// kind 12: the chains alternate between a 3-input add and an integer multiply-add, the mix of an
+// integer kernel that spreads its additions over both pipes
+template <int OP>
+__device__ __forceinline__ uint32_t op_chain(int i, uint32_t a, uint32_t b, uint32_t c)
+{
+    if constexpr (OP == 12) return (i & 1) ? a * b + c : a + b + c;
+    else return op<OP>(a, b, c);
+}
+
 template <int OP>
 __global__ void __launch_bounds__(256) int_kernel(uint32_t *out, long long *cycles, int iters,
                                                  uint32_t seed)
@@ -43,7 +52,7 @@ __global__ void __launch_bounds__(256) int_kernel(uint32_t *out, long long *cycl
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u)
 #pragma unroll
-            for (int i = 0; i < CHAINS; ++i) v[i] = op<OP>(v[i], v[(i + 1) % CHAINS], c);
+            for (int i = 0; i < CHAINS; ++i) v[i] = op_chain<OP>(i, v[i], v[(i + 1) % CHAINS], c);
     }
     const long long t1 = clock64();
     uint32_t x = 0;
@@ -121,7 +130,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
                              double *ops_per_clk_sm)
 {
     using namespace rfsr;
-    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 11)
+    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 12)
         return RFSR_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return RFSR_EDEVICE;
     int sms = 0;
@@ -138,6 +147,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
     case 6: e = run(int_kernel<6>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 7: e = run(int_kernel<7>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 8: e = run(int_kernel<8>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 12: e = run(int_kernel<12>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 9: e = run(int_kernel<9>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 10: e = run(int_kernel<10>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     default: e = run(ffma_kernel, sms, iters, ops_per_sec, ops_per_clk_sm); break;

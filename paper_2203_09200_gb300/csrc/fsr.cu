@@ -19,15 +19,16 @@
 //     radix-2 FFT plus the real-input split), then one column of the half spectrum (32-point
 //     complex radix-2 FFT, in place in shared memory); twiddles come from a host-computed table
 //     in constant memory at compile-time indices.
-//   * R is Hermitian (the signal is real), so only l = 0..16 is kept: lane k holds R(k, 0..16)
-//     in registers, with its frequency weights (0 for the non-canonical member of a pair).  The
+//   * R is Hermitian (the signal is real), so 17 bins per lane suffice: rows 0..16 at columns
+//     0..16 and rows 1..15 at columns 16..32, in registers with their frequency weights.  The
 //     full weight spectrum W (read at shifts k -+ u) lives in shared memory as rows of 49 columns
 //     (0..31 and 0..16 again), so both shifted reads are immediate offsets from one pointer and
 //     the 32 lanes' row-shifted reads fall in distinct banks.
-//   * Selection: one pass per lane keeps its maximum and its bin, the warp maximum comes from
-//     __reduce_max_sync on the (non-negative) float bits and the lowest canonical index among the
-//     lanes that reach it from __reduce_min_sync.  The winning bin is the same in every lane, so
-//     the owner lane reads R there through one uniform switch and a shuffle pair sends it out.
+//   * Selection: per lane a max tree over integer keys (the float bits of e with the slot in the
+//     low 5 bits), the warp maximum from __reduce_max_sync and the lowest canonical index among
+//     the lanes that reach it from __reduce_min_sync.  The winning bin's slot is the same in
+//     every lane, so the owner lane reads R there through one uniform switch and a shuffle pair
+//     sends it out.
 //     The rank-2 residual update works on (Re, Im) as packed FP32 pairs
 //     (R -= dr (a + c) + di (c.y - a.y, a.x - c.x)): one pair add, two scalar subtractions and two
 //     pair FMAs per bin.
@@ -284,16 +285,24 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     if (lane < 2) column_dft(ws.dft.f, N - NH + lane);
     __syncwarp();
 
-    // 4. lane k takes R(k, 0..16) into registers; W goes to the full padded layout
+    // 4. 17 bins of the half spectrum per lane in registers.  Lane k <= 16 holds R(k, s), lane
+    //    k > 16 holds R(32 - k, 16 + s) = conj(R(k, 16 - s)), s = 0..16.  Slot s then has the
+    //    canonical linear index rowbase + s in every lane (the bins (32 - k, 16) and (32 - k, 0)
+    //    of slots 0 and 16 in lanes k > 16 repeat bins of lane 32 - k and get weight 0), so a tie
+    //    inside a lane always goes to the lowest slot.  W goes to the full padded layout.
     const int k = lane;
-    float2 Rr[NH];                                     // (Re, Im) of R(k, l)
+    const bool upper = k > N / 2;
+    const int kap = upper ? N - k : k;                 // row of the held bins
+    const int c0 = upper ? N / 2 : 0;                  // column of slot 0
+    const int rowbase = kap * N + c0;                  // canonical linear index of slot 0
+    float2 Rr[NH];                                     // (Re, Im) of R(kap, c0 + s)
     {
         float2 Wt[NH];
 #pragma unroll
-        for (int l = 0; l < NH; ++l) {
-            const float2 r = ws.dft.f[k * NH + l];
-            Rr[l] = r;
-            Wt[l] = ws.dft.w[k * NH + l];
+        for (int s = 0; s < NH; ++s) {
+            const float2 r = ws.dft.f[k * NH + (upper ? NH - 1 - s : s)];
+            Rr[s] = upper ? make_float2(r.x, -r.y) : r;
+            Wt[s] = ws.dft.w[k * NH + s];
         }
         __syncwarp();
 #pragma unroll
@@ -301,7 +310,7 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     }
     __syncwarp();
     // W(k, l) for l = 17..31 from Hermitian symmetry, W(k, l) = conj(W(-k, -l)); columns 32..48
-    // repeat 0..16 so that the shifted reads W(k -+ u, l -+ u_l) need no wrap-around
+    // repeat 0..16 so that the shifted reads W(kap -+ u, c0 + s -+ u_l) need no wrap-around
 #pragma unroll
     for (int l = NH; l < N; ++l) {
         const float2 a = ws.W[((N - k) & (N - 1)) * WS + (N - l)];
@@ -312,50 +321,44 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     __syncwarp();
     const float W0 = ws.W[0].x;
 
-    // frequency weights of this row, 0 for the non-canonical member of a pair
+    // frequency weights of the held bins (wf is even in both frequencies), 0 for the repeats
     float wfr[NH];
 #pragma unroll
-    for (int l = 0; l < NH; ++l) {
-        const bool canon = (l != 0 && l != NH - 1) || k <= N / 2;
-        wfr[l] = canon ? __ldg(&tab->wf[k * NH + l]) : 0.f;
+    for (int s = 0; s < NH; ++s) {
+        const bool held = !upper || (s != 0 && s != NH - 1);
+        wfr[s] = held ? __ldg(&tab->wf[k * NH + (upper ? NH - 1 - s : s)]) : 0.f;
     }
-    // Ties go to the pair with the lower canonical linear index min(32k+l, 32k'+l'), k' = -k,
-    // l' = -l (mod 32).  Within a stored row that index grows with l for k <= 16 and falls with l
-    // for k > 16 (whose l = 0, 16 bins are not canonical), so a scan in increasing l keeps the
-    // first maximum (strict >) in rows k <= 16 and the last one (>=) in rows k > 16.  Both are one
-    // integer compare on the float bits (e >= 0): e >= be <=> bits(e) + 1 > bits(be).
-    const uint32_t bias = k > N / 2 ? 1u : 0u;
 
     const int pm = (lane >> 2) & 3, pn = lane & 3;     // block pixel of lanes 0..15
     float g = 0.f;
     const float gscale = W0 > 0.f ? gamma / W0 : 0.f;
     for (int it = 0; it < iters && W0 > 0.f; ++it) {
-        float be = 0.f;
-        int bl = -1;
+        // Selection key of slot s: the bits of e = wf |R|^2 (e >= 0, so they order like e) with
+        // the low 5 bits replaced by 31 - s.  The integer maximum then picks the largest e and,
+        // among values equal to 2^-18 relative, the lowest slot; a max tree keeps the scan short.
+        uint32_t key[NH];
 #pragma unroll
-        for (int l = 0; l < NH; ++l) {
-            const float e = wfr[l] * fmaf(Rr[l].x, Rr[l].x, Rr[l].y * Rr[l].y);
-            const bool take = (int)(__float_as_uint(e) + bias) > (int)__float_as_uint(be);
-            be = take ? e : be;
-            bl = take ? l : bl;
+        for (int s = 0; s < NH; ++s) {
+            const float e = wfr[s] * fmaf(Rr[s].x, Rr[s].x, Rr[s].y * Rr[s].y);
+            key[s] = (__float_as_uint(e) & ~31u) | (uint32_t)(31 - s);
         }
-        const float m = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(be)));
-        if (!(m > 0.f)) break;                          // residual exhausted
-        int mykey = 0x7fffffff;
-        if (be == m) {
-            const int lin = k * N + bl, clin = ((N - k) & (N - 1)) * N + ((N - bl) & (N - 1));
-            mykey = min(lin, clin);
-        }
+#pragma unroll
+        for (int w = 1; w < NH; w *= 2)
+#pragma unroll
+            for (int s = 0; s + w < NH; s += 2 * w) key[s] = max(key[s], key[s + w]);
+        const uint32_t best = key[0];
+        const uint32_t m = __reduce_max_sync(0xffffffffu, best);
+        if ((m >> 5) == 0) break;                      // residual exhausted
+        // among the lanes whose value reaches the maximum, the lowest canonical index wins
+        const int mykey = ((best ^ m) >> 5) == 0 ? rowbase + 31 - (int)(best & 31) : 0x7fffffff;
         const int win = __reduce_min_sync(0xffffffffu, mykey);
-        // the stored representative of the winning pair and its owner lane
-        int uk = win >> 5, ul = win & (N - 1);
-        if (ul > N / 2) {
-            uk = (N - uk) & (N - 1);
-            ul = N - ul;
-        }
-        // R(uk, ul) from its owner lane: ul is the same in every lane, so one switch branch
+        const int uk = win >> 5, ul = win & (N - 1);   // the canonical bin u
+        // R(u) from its owner: lane uk, slot ul (ul <= 16) or lane 32 - uk, slot ul - 16; the
+        // slot is the same in every lane, so one switch branch reads it
+        const int owner = ul <= N / 2 ? uk : N - uk;
+        const int slot = ul <= N / 2 ? ul : ul - N / 2;
         float2 rv = Rr[0];
-        switch (ul) {
+        switch (slot) {
 #define RFSR_CASE(c) case c: rv = Rr[c]; break;
             RFSR_CASE(1) RFSR_CASE(2) RFSR_CASE(3) RFSR_CASE(4) RFSR_CASE(5) RFSR_CASE(6)
             RFSR_CASE(7) RFSR_CASE(8) RFSR_CASE(9) RFSR_CASE(10) RFSR_CASE(11) RFSR_CASE(12)
@@ -363,14 +366,14 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
 #undef RFSR_CASE
             default: break;
         }
-        const float ure = __shfl_sync(0xffffffffu, rv.x, uk);
-        const float uim = __shfl_sync(0xffffffffu, rv.y, uk);
+        const float ure = __shfl_sync(0xffffffffu, rv.x, owner);
+        const float uim = __shfl_sync(0xffffffffu, rv.y, owner);
         const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
         const float dr = gscale * ure;
         const float di = self ? 0.f : gscale * uim;
-        // W(k-u) at column l - u_l + 32, W(k+u) at column l + u_l of the wrapped rows
-        const float2 *pa = ws.W + ((k - uk) & (N - 1)) * WS + (N - ul);
-        const float2 *pc = ws.W + ((k + uk) & (N - 1)) * WS + ul;
+        // W(kap - u) and W(kap + u) of the held bins start at columns (c0 -+ u_l) mod 32
+        const float2 *pa = ws.W + ((kap - uk) & (N - 1)) * WS + ((c0 - ul) & (N - 1));
+        const float2 *pc = ws.W + ((kap + uk) & (N - 1)) * WS + ((c0 + ul) & (N - 1));
         // packed FP32 pairs: R -= dr (a + c) + di (c.y - a.y, a.x - c.x), or R -= dr a (self)
         const float2 ndr = make_float2(-dr, -dr), ndi = make_float2(-di, -di);
         if (self) {

@@ -182,6 +182,16 @@ __device__ __forceinline__ uint32_t lane_mask(uint32_t t)
     return m;
 }
 
+// a * b + c on the integer multiply-add unit.  With b = 1 (or -1, both held in registers whose
+// value the compiler cannot see) it is an addition (subtraction) that runs on the FMA pipe, which
+// the byte-SIMD work of these kernels leaves idle, instead of taking another ALU slot.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 template <int WARPS>
 struct Smem9 {
     uint32_t rf[s_rrows<WARPS>() * S_RWORDS];
@@ -246,6 +256,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
     }
     const int nv = (2 * R + 1) * (2 * R + 1);
     const int oy = y0 + S_ROWS * warp;                     // first output row of the warp
+    const uint32_t one = (uint32_t)(W > 0), m1 = 0u - one;  // 1 and -1 (W > 0 always)
     for (int o = 0; o < nv; ++o) {
         const short2 v = sm.vord[o];
         const int vy = v.x, vx = v.y;
@@ -269,23 +280,23 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
             const uint32_t d4 = __vabsdiffu4(cs[i], r4) & cmk[i];
             dlo[i] = __byte_perm(d4, 0u, 0x4240);
             dhi[i] = __byte_perm(d4, 0u, 0x4341);
-            lo += dlo[i];
-            hi += dhi[i];
+            lo = imad(dlo[i], one, lo);
+            hi = imad(dhi[i], one, hi);
             if (i >= 9) {
-                lo -= dlo[i - 9];
-                hi -= dhi[i - 9];
+                lo = imad(dlo[i - 9], m1, lo);
+                hi = imad(dhi[i - 9], m1, hi);
             }
             if (i >= 8) {
                 const int j = i - 8;                       // output row of this window
-                const uint32_t Q = lo + hi;                // (c0+c1, c2+c3)
+                const uint32_t Q = imad(hi, one, lo);      // (c0+c1, c2+c3)
                 const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
                 const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
                 const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
                 const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
                 const uint32_t A = __byte_perm(Ql, Q, 0x5432);   // (left c-2+c-1, c0+c1)
                 const uint32_t B = __byte_perm(Q, Qr, 0x5432);   // (c2+c3, right c4+c5)
-                uint32_t h02 = Ql + A + Q + B + lor;             // (H0, H2)
-                uint32_t h13 = h02 + Qr - lol - lor;             // (H1, H3)
+                uint32_t h02 = imad(lor, one, imad(imad(B, one, Q), one, imad(A, one, Ql)));  // (H0, H2)
+                uint32_t h13 = imad(imad(lol, m1, Qr), one, imad(lor, m1, h02));         // (H1, H3)
                 uint32_t rinv = 0;
                 if (border) {
                     const int py = oy + j;
