@@ -21,17 +21,17 @@
 // NNC runs first and the reverse check only for NNC survivors (the combination of Sec. 3.1.2).
 //
 // GB300 design: one CTA per 32x32 pixel tile, all past frames in one launch.  The current frame
-// around the tile (template + check halo) is staged once in shared memory as masked samples and
-// byte masks, each in four byte-shifted copies so that a template row at any column is three
-// aligned 32-bit words; the template counts n are computed once per tile.  Per past frame the
+// around the tile (template + check halo) is staged once in shared memory as (masked samples,
+// byte mask) word pairs in four byte-shifted copies, so that a template row at any column is
+// three aligned 8-byte loads; the template counts n are computed once per tile.  Per past frame the
 // CTA stages the ME field with a 2-pixel halo and the past frame around the tile, computes the
 // median field once, decides every pixel, and compacts the pixels that need a reverse check into
 // a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
 // registers, lane 0 scores d = 0 and the other lanes split the remaining offsets, each costing T
 // rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.  The
-// current frame's copies use a 26-word row stride and a copy stride of 3 mod 32, and the offsets
-// are dealt to lanes (per column phase, nearest first) so that the 32 lanes of a round read 32
-// distinct banks for every template word.
+// current frame's copies use a row stride of 19 and a copy stride of 12 mod 16 units, and the
+// offsets are dealt to lanes (per column phase, nearest first) so that the 16 lanes of each
+// half-warp read 16 distinct bank pairs for every template word.
 #include "rfsr_internal.h"
 
 namespace rfsr {
@@ -47,11 +47,13 @@ constexpr int RS = TP + 2 * HC;               // staged region side (64)
 constexpr int NWD = RS / 4 + 1;               // data words per staged row (+1 feeds the shifted copies)
 constexpr int RWD = NWD;                      // past frame: row stride (words)
 constexpr int CPY = RS * RWD + 8;             // past frame: words per shifted copy
-// Current frame (the templates the reverse checks slide): row stride 26 and copy stride 3 (mod
-// 32) words.  With the FRMC lane order below, the 32 lanes of a warp, each scoring one offset d
-// of the same pixel, then read 32 distinct banks for every template word.
-constexpr int RWDC = 26;
-constexpr int CPYC = RS * RWDC + 3;
+// Current frame (the templates the reverse checks slide): (masked samples, byte mask) word pairs,
+// one 8-byte unit per region word, row stride 19 and copy stride 12 (mod 16) units.  A warp's
+// 8-byte loads are served per half-warp; with the lane order below the 16 lanes of a half-warp,
+// each scoring one offset d of the same pixel, read 16 distinct bank pairs for every template
+// word.
+constexpr int RWDC = 19;
+constexpr int CPYC = RS * RWDC + 12;
 constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +- 9)
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
@@ -91,17 +93,20 @@ __host__ __device__ constexpr int cand_dx(int c, bool frmc, int Rc)
     return frmc ? frmc_offset(c % 7) : c % (2 * Rc + 1) - Rc;
 }
 
+// bank pair (8-byte unit mod 16) of a candidate's first template word
 constexpr int cand_bank(int c, int ph, bool frmc, int Rc)
 {
     const int v = ph + cand_dx(c, frmc, Rc), dy = cand_dy(c, frmc, Rc);
-    return ((((v & 3) * CPYC + dy * RWDC + (v >> 2)) % 32) + 32) % 32;
+    return ((((v & 3) * CPYC + dy * RWDC + (v >> 2)) % 16) + 16) % 16;
 }
 
+// Half-round i of bank pair b holds the i-th candidate (in increasing |d|_1) that starts there;
+// round r is half-rounds 2r (lanes 0..15) and 2r + 1 (lanes 16..31).
 constexpr void build_order(CandOrder &o, bool frmc, int Rc)
 {
     const int side = frmc ? 7 : 2 * Rc + 1, n = side * side, lmax = frmc ? 14 : 2 * Rc;
     for (int ph = 0; ph < 4; ++ph) {
-        uint8_t taken[32] = {}, fill[MAXROUND] = {};
+        uint8_t taken[16] = {}, fill[2 * MAXROUND] = {};
         for (int r = 0; r < MAXROUND; ++r)
             for (int l = 0; l < 32; ++l) o.lane[ph][r][l] = NOCAND;
         uint32_t nr = 0;
@@ -109,31 +114,36 @@ constexpr void build_order(CandOrder &o, bool frmc, int Rc)
             for (int c = 0; c < n; ++c) {
                 const int dy = cand_dy(c, frmc, Rc), dx = cand_dx(c, frmc, Rc);
                 if ((dy < 0 ? -dy : dy) + (dx < 0 ? -dx : dx) != L) continue;
-                const int b = cand_bank(c, ph, frmc, Rc), r = taken[b]++;
-                o.lane[ph][r][fill[r]++] = (uint16_t)c;
-                nr = (uint32_t)r + 1 > nr ? (uint32_t)r + 1 : nr;
+                const int hr = taken[cand_bank(c, ph, frmc, Rc)]++;
+                if (hr >= 2 * MAXROUND) {                      // does not fit: order_ok fails
+                    o.nround[ph] = MAXROUND + 1;
+                    return;
+                }
+                o.lane[ph][hr / 2][16 * (hr & 1) + fill[hr]++] = (uint16_t)c;
+                nr = (uint32_t)hr / 2 + 1 > nr ? (uint32_t)hr / 2 + 1 : nr;
             }
         o.nround[ph] = nr;
     }
 }
 
-// every candidate placed once, the centre first, distinct banks in every round
+// every candidate placed once, the centre first, distinct bank pairs in every half-warp
 constexpr bool order_ok(const CandOrder &o, bool frmc, int Rc)
 {
     const int side = frmc ? 7 : 2 * Rc + 1, n = side * side;
     for (int ph = 0; ph < 4; ++ph) {
         if (o.nround[ph] > MAXROUND || o.lane[ph][0][0] != n / 2) return false;
         int placed = 0;
-        for (int r = 0; r < MAXROUND; ++r) {
-            bool seen[32] = {};
-            for (int l = 0; l < 32; ++l) {
-                const int c = o.lane[ph][r][l];
-                if (c == NOCAND) continue;
-                ++placed;
-                if (seen[cand_bank(c, ph, frmc, Rc)]) return false;
-                seen[cand_bank(c, ph, frmc, Rc)] = true;
+        for (int r = 0; r < MAXROUND; ++r)
+            for (int half = 0; half < 2; ++half) {
+                bool seen[16] = {};
+                for (int l = 16 * half; l < 16 * half + 16; ++l) {
+                    const int c = o.lane[ph][r][l];
+                    if (c == NOCAND) continue;
+                    ++placed;
+                    if (seen[cand_bank(c, ph, frmc, Rc)]) return false;
+                    seen[cand_bank(c, ph, frmc, Rc)] = true;
+                }
             }
-        }
         if (placed != n) return false;
     }
     return true;
@@ -146,13 +156,12 @@ constexpr bool frmc_order_ok()
     return order_ok(o, true, 0) && o.nround[0] == 2 && o.nround[1] == 2 && o.nround[2] == 2 &&
            o.nround[3] == 2;
 }
-static_assert(frmc_order_ok(), "FRMC lane order: a round has two candidates in one bank");
+static_assert(frmc_order_ok(), "FRMC lane order: two rounds without shared bank pairs");
 
 __device__ CandOrder g_order[NORDER];      // written once per device by init_cc
 
 struct Smem {
-    uint32_t cs[4 * CPYC];        // masked samples, byte-shifted copies
-    uint32_t cm[4 * CPYC];        // byte masks, byte-shifted copies
+    uint2 csm[4 * CPYC];          // (masked samples, byte mask) words, byte-shifted copies
     uint32_t rf[4 * CPY];         // past frame (clamped coordinates), byte-shifted copies
     uint8_t nsrc[NS][NS];         // measured pixels in the template around each source
     char2 mv[MT][MT];
@@ -189,39 +198,60 @@ __device__ __forceinline__ int median9(int p0, int p1, int p2, int p3, int p4, i
     return med3(lo, med3(p1, p4, p7), hi);
 }
 
-// Stage a frame region (rows y0-HC.., cols x0-HC..) into four byte-shifted copies: copy j, word w
-// of a row holds region bytes 4w+j .. 4w+j+3 (row stride RW, copy stride CP words).  MODE 0:
-// masked samples and 1: byte mask (both 0 outside the frame); MODE 2: past frame with clamped
-// coordinates.
-template <int MODE, int RW, int CP>
-__device__ void stage(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
+// Stage the past frame around the tile (rows y0-HC.., cols x0-HC.., clamped coordinates) into
+// four byte-shifted copies: copy j, word w of a row holds region bytes 4w+j .. 4w+j+3.
+__device__ void stage_past(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
 {
     for (int i = threadIdx.x; i < RS * NWD; i += NT) {
         const int r = i / NWD, w = i - r * NWD;
         const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
         uint32_t v = 0;
-        if (MODE == 2) {
-            const uint8_t *row = src + (size_t)min(max(gy, 0), H - 1) * W;
+        const uint8_t *row = src + (size_t)min(max(gy, 0), H - 1) * W;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
-        } else if (gy >= 0 && gy < H) {
-            // 16-bit loads: W is even and gx is even, so a pixel pair never straddles the border
-            const uint8_t *row = src + (size_t)gy * W;
-#pragma unroll
-            for (int b = 0; b < 4; b += 2) {
-                const int x = gx + b;
-                if (x >= 0 && x < W)
-                    v |= (uint32_t)(*reinterpret_cast<const uint16_t *>(row + x)) << (8 * b);
-            }
-        }
-        dst[r * RW + w] = v;
+        for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        dst[r * RWD + w] = v;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * RS * (NWD - 1); i += NT) {
         const int j = 1 + i / (RS * (NWD - 1));
         const int rem = i - (j - 1) * RS * (NWD - 1);
         const int r = rem / (NWD - 1), w = rem - r * (NWD - 1);
-        dst[j * CP + r * RW + w] = __funnelshift_r(dst[r * RW + w], dst[r * RW + w + 1], 8 * j);
+        dst[j * CPY + r * RWD + w] = __funnelshift_r(dst[r * RWD + w], dst[r * RWD + w + 1], 8 * j);
+    }
+}
+
+// Stage the current frame around the tile as (masked samples, byte mask) word pairs in four
+// byte-shifted copies (copy j, unit w of a row holds region bytes 4w+j .. 4w+j+3 of both planes;
+// 0 outside the frame).
+__device__ void stage_current(uint2 *dst, const uint8_t *__restrict__ smp,
+                              const uint8_t *__restrict__ msk, int H, int W, int y0, int x0)
+{
+    for (int i = threadIdx.x; i < RS * NWD; i += NT) {
+        const int r = i / NWD, w = i - r * NWD;
+        const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
+        uint32_t vs = 0, vm = 0;
+        if (gy >= 0 && gy < H) {
+            // 16-bit loads: W is even and gx is even, so a pixel pair never straddles the border
+            const size_t ro = (size_t)gy * W;
+#pragma unroll
+            for (int b = 0; b < 4; b += 2) {
+                const int x = gx + b;
+                if (x >= 0 && x < W) {
+                    vs |= (uint32_t)(*reinterpret_cast<const uint16_t *>(smp + ro + x)) << (8 * b);
+                    vm |= (uint32_t)(*reinterpret_cast<const uint16_t *>(msk + ro + x)) << (8 * b);
+                }
+            }
+        }
+        dst[r * RWDC + w] = make_uint2(vs, vm);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * RS * (NWD - 1); i += NT) {
+        const int j = 1 + i / (RS * (NWD - 1));
+        const int rem = i - (j - 1) * RS * (NWD - 1);
+        const int r = rem / (NWD - 1), w = rem - r * (NWD - 1);
+        const uint2 a = dst[r * RWDC + w], b = dst[r * RWDC + w + 1];
+        dst[j * CPYC + r * RWDC + w] = make_uint2(__funnelshift_r(a.x, b.x, 8 * j),
+                                                  __funnelshift_r(a.y, b.y, 8 * j));
     }
 }
 
@@ -237,11 +267,17 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     int acc = 0;
 #pragma unroll
     for (int r = 0; r < T; ++r) {
-        const uint32_t *cs = sm.cs + j * CPYC + (sy + r) * RWDC + w;
-        const uint32_t *cm = sm.cm + j * CPYC + (sy + r) * RWDC + w;
-        acc += __vsadu4(cs[0] & w0, P[r][0] & cm[0] & w0);
-        if (w1) acc += __vsadu4(cs[1] & w1, P[r][1] & cm[1] & w1);
-        if (w2) acc += __vsadu4(cs[2] & w2, P[r][2] & cm[2] & w2);
+        const uint2 *c = sm.csm + j * CPYC + (sy + r) * RWDC + w;
+        const uint2 c0 = c[0];
+        acc += __vsadu4(c0.x & w0, P[r][0] & c0.y & w0);
+        if (w1) {
+            const uint2 c1 = c[1];
+            acc += __vsadu4(c1.x & w1, P[r][1] & c1.y & w1);
+        }
+        if (w2) {
+            const uint2 c2 = c[2];
+            acc += __vsadu4(c2.x & w2, P[r][2] & c2.y & w2);
+        }
     }
     return acc;
 }
@@ -264,8 +300,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         uint4 *dst = reinterpret_cast<uint4 *>(&sm.ord);
         for (int i = tid; i < (int)(sizeof(CandOrder) / sizeof(uint4)); i += NT) dst[i] = src[i];
     }
-    stage<0, RWDC, CPYC>(sm.cs, t.cur_smp, H, W, y0, x0);
-    stage<1, RWDC, CPYC>(sm.cm, t.cur_msk, H, W, y0, x0);
+    stage_current(sm.csm, t.cur_smp, t.cur_msk, H, W, y0, x0);
     __syncthreads();
     // template counts n around every source position of the tile +- 9 (current mask, 0 outside)
     for (int i = tid; i < NS * NS; i += NT) {
@@ -273,10 +308,10 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         const int ry = sy + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
         int n = 0;
         for (int r = 0; r < T; ++r) {
-            const uint32_t *cm = sm.cm + (rx & 3) * CPYC + (ry + r) * RWDC + (rx >> 2);
+            const uint2 *cm = sm.csm + (rx & 3) * CPYC + (ry + r) * RWDC + (rx >> 2);
 #pragma unroll
             for (int b = 0; b < (T + 3) / 4; ++b) {
-                uint32_t m = cm[b];
+                uint32_t m = cm[b].y;
                 if (4 * b + 4 > T) m &= (1u << (8 * (T - 4 * b))) - 1u;
                 n += __popc(m);
             }
@@ -297,7 +332,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             sm.mv[r][c] = mvk[(size_t)gy * W + gx];
         }
         if (tid == 0) sm.nlist = 0;
-        if (frmc || rmc) stage<2, RWD, CPY>(sm.rf, t.ref_rec[k], H, W, y0, x0);
+        if (frmc || rmc) stage_past(sm.rf, t.ref_rec[k], H, W, y0, x0);
         __syncthreads();
         if (use_nnc) {
             for (int i = tid; i < MD * MD; i += NT) {
@@ -343,7 +378,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             const size_t gi = (size_t)y * W + x;
             reinterpret_cast<char2 *>(t.fmv[k])[gi] = make_char2((signed char)fy, (signed char)fx);
             const int qy = y + fy, qx = x + fx;
-            const uint32_t mword = sm.cm[(py + HC) * RWDC + ((px + HC) >> 2)];
+            const uint32_t mword = sm.csm[(py + HC) * RWDC + ((px + HC) >> 2)].y;
             const bool measured = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
             if (measured) {
                 dec[i] = 0;
