@@ -32,10 +32,19 @@ __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b, uint32_t c)
 
 // kind 12: the chains alternate between a 3-input add and an integer multiply-add, the mix of an
 // integer kernel that spreads its additions over both pipes
+// kind 13: byte SAD with its accumulate as one SIMD-video instruction
+__device__ __forceinline__ uint32_t sad4_acc(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 template <int OP>
 __device__ __forceinline__ uint32_t op_chain(int i, uint32_t a, uint32_t b, uint32_t c)
 {
     if constexpr (OP == 12) return (i & 1) ? a * b + c : a + b + c;
+    else if constexpr (OP == 13) return sad4_acc(a, b, c);
     else return op<OP>(a, b, c);
 }
 
@@ -130,7 +139,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
                              double *ops_per_clk_sm)
 {
     using namespace rfsr;
-    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 12)
+    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 13)
         return RFSR_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return RFSR_EDEVICE;
     int sms = 0;
@@ -148,6 +157,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
     case 7: e = run(int_kernel<7>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 8: e = run(int_kernel<8>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 12: e = run(int_kernel<12>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 13: e = run(int_kernel<13>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 9: e = run(int_kernel<9>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 10: e = run(int_kernel<10>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     default: e = run(ffma_kernel, sms, iters, ops_per_sec, ops_per_clk_sm); break;

@@ -58,6 +58,12 @@ constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
+// Box-sum reverse checks (T <= 9): vertical sums of BOX_ND candidates at a time over the tile's
+// rows and the columns -4 .. 35 around it
+constexpr int BOX_ND = 6;                     // candidates per pass
+constexpr int BOX_W = TP + 8;                 // columns -4 .. 35 of the tile
+constexpr int BOX_MIN = 128;                  // listed pixels of one vector that pay for a box pass
+constexpr int HS = 2 * kMaxRadius + 1;        // side of the vector histogram
 
 // FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
 __host__ __device__ constexpr int frmc_offset(int i)
@@ -169,8 +175,12 @@ struct Smem {
     uint16_t list[TP * TP];       // tile pixels that need a reverse check
     uint8_t rej[TP * TP];
     CandOrder ord;                // reverse-check lane order of this tile's mode
+    uint32_t vsum[BOX_ND][TP][BOX_W];   // box checks: vertical T-sums per candidate and column
+    int hist[HS * HS];            // listed pixels per filtered vector
+    int boxv;                     // vector (histogram bin) checked by box sums, -1: none
     int nlist;
 };
+static_assert(offsetof(Smem, vsum) % 16 == 0, "vertical sums are read in 16-byte words");
 
 static_assert(offsetof(Smem, ord) % 16 == 0, "the lane order is written in 16-byte words");
 
@@ -255,6 +265,14 @@ __device__ void stage_current(uint2 *dst, const uint8_t *__restrict__ smp,
     }
 }
 
+// acc + sum over the four bytes of |a - b|, one SIMD-video instruction with its accumulate
+__device__ __forceinline__ int sad4_acc(uint32_t a, uint32_t b, int acc)
+{
+    int d;
+    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(acc));
+    return d;
+}
+
 // SAD over the measured current pixels of the T x T template whose top-left corner is at region
 // (sy, sx), against the past-frame patch words P held in registers
 template <int T>
@@ -269,17 +287,125 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     for (int r = 0; r < T; ++r) {
         const uint2 *c = sm.csm + j * CPYC + (sy + r) * RWDC + w;
         const uint2 c0 = c[0];
-        acc += __vsadu4(c0.x & w0, P[r][0] & c0.y & w0);
+        acc = sad4_acc(c0.x & w0, P[r][0] & c0.y & w0, acc);
         if (w1) {
             const uint2 c1 = c[1];
-            acc += __vsadu4(c1.x & w1, P[r][1] & c1.y & w1);
+            acc = sad4_acc(c1.x & w1, P[r][1] & c1.y & w1, acc);
         }
         if (w2) {
             const uint2 c2 = c[2];
-            acc += __vsadu4(c2.x & w2, P[r][2] & c2.y & w2);
+            acc = sad4_acc(c2.x & w2, P[r][2] & c2.y & w2, acc);
         }
     }
     return acc;
+}
+
+// candidate i of the reverse-check window in box order: the centre d = 0 first, then the others
+__device__ __forceinline__ int box_cand(int i, bool frmc, int Rc)
+{
+    const int n = frmc ? 49 : (2 * Rc + 1) * (2 * Rc + 1), c = n / 2;
+    return i == 0 ? c : (i <= c ? i - 1 : i);
+}
+
+// Reverse checks by box sums for every tile pixel whose filtered vector is v (T <= 9).  The cost
+// of candidate d at pixel p is C(p + d, v - d) = sum over o of F_d(p + o) with
+//     F_d(y) = b_t(y + d) |s_t(y + d) - rec(y + v)|,
+// a T x T box sum of one plane per candidate: the same integers the per-pixel path adds up, so
+// the decisions are identical.  A pass computes the vertical sums of BOX_ND candidates (one
+// thread per candidate, 4-column word and 8-row chunk), then every thread takes the 4 pixels of
+// one tile word: horizontal sums, and the exact SAD/n compare against d = 0 (first candidate).
+// Thread t ends with the verdicts of pixels (t / 8, 4 (t % 8) + c), c = 0..3, in rej.
+template <int T>
+__device__ void box_checks(Smem &sm, const FrameTask &t, int x0, int y0, int vy, int vx,
+                           bool frmc, bool (&rej)[4])
+{
+    constexpr int h = T / 2;
+    static_assert(h <= 4, "box checks cover columns -4 .. 35 of the tile");
+    const int H = t.H, W = t.W, tid = threadIdx.x;
+    const int n = frmc ? 49 : (2 * t.Rc + 1) * (2 * t.Rc + 1);
+    const int pr = tid >> 3, pw = tid & 7;               // this thread's pixel word
+    int e0[4] = {0, 0, 0, 0}, n0[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) rej[c] = false;
+    const bool inner = y0 - kMaxRadius >= 0 && x0 - kMaxRadius >= 0 && y0 + TP + kMaxRadius <= H &&
+                       x0 + TP + kMaxRadius <= W;
+    // past-frame word of F for tile column 4 wi - 4 at region column 4 wi + HC - 4 + vx
+    const int jr = (HC - 4 + vx) & 3, wr = (HC - 4 + vx) >> 2;
+    for (int base = 0; base < n; base += BOX_ND) {
+        const int nd = min(BOX_ND, n - base);
+        // vertical sums: task = (candidate, word wi of columns 4 wi - 4 .., chunk of 8 rows)
+        for (int task = tid; task < nd * 40; task += NT) {
+            const int dd = task / 40, rem = task - dd * 40, ch = rem / 10, wi = rem - ch * 10;
+            const int ci = box_cand(base + dd, frmc, t.Rc);
+            const int dy = cand_dy(ci, frmc, t.Rc), dx = cand_dx(ci, frmc, t.Rc);
+            const int jc = (HC - 4 + dx) & 3, wc = wi + ((HC - 4 + dx) >> 2);
+            const uint2 *cur = sm.csm + jc * CPYC + (8 * ch - h + HC + dy) * RWDC + wc;
+            const uint32_t *ref = sm.rf + jr * CPY + (8 * ch - h + HC + vy) * RWD + wi + wr;
+            uint32_t dlo[8 + 2 * h], dhi[8 + 2 * h], lo = 0, hi = 0;
+#pragma unroll
+            for (int i = 0; i < 8 + 2 * h; ++i) {
+                const uint2 c = cur[i * RWDC];
+                const uint32_t d4 = __vabsdiffu4(c.x, ref[i * RWD]) & c.y;
+                dlo[i] = __byte_perm(d4, 0u, 0x4240);          // columns 0, 2 as 16-bit lanes
+                dhi[i] = __byte_perm(d4, 0u, 0x4341);          // columns 1, 3
+                lo += dlo[i];
+                hi += dhi[i];
+                if (i >= T) {
+                    lo -= dlo[i - T];
+                    hi -= dhi[i - T];
+                }
+                if (i >= T - 1) {
+                    const int row = 8 * ch + i - (T - 1);
+                    *reinterpret_cast<uint4 *>(&sm.vsum[dd][row][4 * wi]) =
+                        make_uint4(lo & 0xffffu, hi & 0xffffu, lo >> 16, hi >> 16);
+                }
+            }
+        }
+        __syncthreads();
+        // horizontal sums and compare: tile columns 4 pw - h .. 4 pw + 3 + h are vsum columns
+        // 4 pw + 4 - h .. 4 pw + 7 + h; the four window sums slide by one column each
+#pragma unroll
+        for (int dd = 0; dd < BOX_ND; ++dd) {
+            if (dd >= nd) break;
+            const uint4 *vp = reinterpret_cast<const uint4 *>(&sm.vsum[dd][pr][4 * pw]);
+            const uint4 a = vp[0], b = vp[1], c = vp[2];
+            const int v[12] = {(int)a.x, (int)a.y, (int)a.z, (int)a.w, (int)b.x, (int)b.y,
+                               (int)b.z, (int)b.w, (int)c.x, (int)c.y, (int)c.z, (int)c.w};
+            int e[4];
+            int sum = 0;
+#pragma unroll
+            for (int j = -h; j <= h; ++j) sum += v[4 + j];
+            e[0] = sum;
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                sum += v[4 + h + q] - v[3 - h + q];
+                e[q] = sum;
+            }
+            if (base + dd == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    e0[q] = e[q];
+                    n0[q] = sm.nsrc[pr + kMaxRadius][4 * pw + q + kMaxRadius];
+                }
+                continue;
+            }
+            const int ci = box_cand(base + dd, frmc, t.Rc);
+            const int dy = cand_dy(ci, frmc, t.Rc), dx = cand_dx(ci, frmc, t.Rc);
+            const uint8_t *nrow = &sm.nsrc[pr + dy + kMaxRadius][4 * pw + dx + kMaxRadius];
+            if (inner) {                       // every source p + d of the tile is in the frame
+#pragma unroll
+                for (int q = 0; q < 4; ++q) rej[q] = rej[q] || e[q] * n0[q] < e0[q] * (int)nrow[q];
+            } else {
+                const bool yin = (unsigned)(y0 + pr + dy) < (unsigned)H;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool valid = yin && (unsigned)(x0 + 4 * pw + q + dx) < (unsigned)W;
+                    if (valid && e[q] * n0[q] < e0[q] * (int)nrow[q]) rej[q] = true;
+                }
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int T>
@@ -402,12 +528,53 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             }
         }
         __syncthreads();
-        // reverse checks: one warp per listed pixel
         const int nl = sm.nlist;
+        // FRMC: box-sum checks for the vector that most listed pixels share, if at least BOX_MIN
+        // do.  The cost of a candidate over the whole tile is one box sum, so the 49 candidates
+        // cost about as much as 130 per-pixel checks.  Under quarter sampling at most a third of
+        // the unmeasured pixels of a tile are projectable per past frame (256), so one vector at
+        // most pays for it in practice.  RMC stays per pixel: its 289 candidates make the box
+        // pass dearer than per-pixel checks, which stop at the first better candidate.
+        int boxbin = -1;
+        if constexpr (T <= 9) {
+            if (frmc && nl >= BOX_MIN) {
+                for (int i = tid; i < HS * HS; i += NT) sm.hist[i] = 0;
+                __syncthreads();
+                for (int li = tid; li < nl; li += NT) {
+                    const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
+                    const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
+                    atomicAdd(&sm.hist[(c.x + kMaxRadius) * HS + c.y + kMaxRadius], 1);
+                }
+                __syncthreads();
+                if (warp == 0) {                                  // the most frequent bin
+                    uint32_t key = 0;                              // count << 10 | 1023 - bin
+                    for (int i = lane; i < HS * HS; i += 32)
+                        key = max(key, ((uint32_t)sm.hist[i] << 10) | (1023u - i));
+                    key = __reduce_max_sync(0xffffffffu, key);
+                    if (lane == 0) sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
+                }
+                __syncthreads();
+                boxbin = sm.boxv;
+                if (boxbin >= 0) {
+                    const int vy = boxbin / HS - kMaxRadius, vx = boxbin % HS - kMaxRadius;
+                    bool rj[4];
+                    box_checks<T>(sm, t, x0, y0, vy, vx, frmc, rj);
+                    const int pr = tid >> 3, pw = tid & 7;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int px = 4 * pw + q;
+                        const char2 c = use_nnc ? sm.md[pr + 1][px + 1] : sm.mv[pr + 2][px + 2];
+                        if (c.x == vy && c.y == vx) sm.rej[pr * TP + px] = rj[q] ? 1 : 0;
+                    }
+                }
+            }
+        }
+        // reverse checks of the other listed pixels: one warp per pixel
         for (int li = warp; li < nl; li += NW) {
             const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
             const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
             const int fy = c.x, fx = c.y;
+            if ((fy + kMaxRadius) * HS + fx + kMaxRadius == boxbin) continue;   // done above
             uint32_t P[T][3];                          // past-frame patch around q
             {
                 const int ry = py + HC + fy - h, rx = px + HC + fx - h;

@@ -182,6 +182,55 @@ def test_shapes_and_parameters(engine, H, W, T, R, K, mode):
     compare(got, ref, msk, smp)
 
 
+def aligned_translation(H, W, seed, v, smooth=0.0, noise=0):
+    """Frame t is a texture (white, or Gaussian low-pass with cutoff `smooth` cycles per pixel),
+    frame t-1 the same texture moved by -v (cyclically) plus uniform noise of +-`noise`, and the
+    masks are consecutive dynamic quarter-sampling masks moved the same way (v even keeps them
+    valid).  Then q = p + v is measured in frame t-1 for a third of the unmeasured pixels -- the
+    most quarter sampling allows -- and ME finds v: the 32x32 tiles have about 256 listed pixels
+    that share one vector.  Smooth content with noise makes reverse checks fail often."""
+    rng = np.random.default_rng(seed)
+    if smooth:
+        f = rng.standard_normal((H, W))
+        k2 = np.fft.fftfreq(H)[:, None] ** 2 + np.fft.fftfreq(W)[None, :] ** 2
+        f = np.real(np.fft.ifft2(np.fft.fft2(f) * np.exp(-k2 / (2 * smooth ** 2))))
+        cur = np.clip(np.rint(128 + 40 * f / f.std()), 0, 255).astype(np.uint8)
+    else:
+        cur = rng.integers(0, 256, size=(H, W), dtype=np.int64).astype(np.uint8)
+    perm = synth.dynamic_permutations(H, W, rng)
+    m0 = synth.positions_to_mask(synth.dynamic_positions(perm, 1))
+    m1 = np.roll(synth.positions_to_mask(synth.dynamic_positions(perm, 0)), v, axis=(0, 1))
+    ref = np.roll(cur, v, axis=(0, 1)).astype(np.int64)
+    if noise:
+        ref += rng.integers(-noise, noise + 1, size=ref.shape)
+    ref = np.clip(ref, 0, 255).astype(np.uint8)
+    return (cur * m0).astype(np.uint8), m0, [(ref, (ref * m1).astype(np.uint8), m1)]
+
+
+@pytest.mark.parametrize("mode,T,v,smooth", [
+    ("frmc", 9, (0, 0), 0.0), ("frmc", 9, (2, -2), 0.05), ("nnc_frmc", 9, (0, 0), 0.05),
+    ("nnc_frmc", 9, (2, 2), 0.0), ("frmc", 5, (0, 2), 0.0), ("frmc", 3, (2, 0), 0.0),
+    ("nnc_frmc", 1, (0, 0), 0.0), ("rmc", 9, (-2, 4), 0.05)])
+def test_shared_vector_box_checks(engine, mode, T, v, smooth):
+    """Tiles whose checked pixels share one vector: with FRMC their checks run as box sums over
+    the tile (the others, and every RMC check, per pixel); every decision must equal the
+    oracle's, rejections included."""
+    H, W = 96, 160
+    smp, msk, hist = aligned_translation(H, W, seed=T * 10 + len(mode), v=v, smooth=smooth,
+                                         noise=12 if smooth else 0)
+    got = gpu_step(engine, smp, msk, hist, cc_mode=mode, template_size=T, num_refs=1)
+    ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NAMES[mode], T=T, R=8)
+    compare(got, ref, msk, smp)
+    # the box path really runs: most tiles hold >= 128 checked pixels with vector v
+    dec = ref.dec[0]
+    share = ((dec == oracle.DEC_ACCEPT) | (dec == oracle.DEC_CHECK_REJECT)) & \
+        (ref.fmv[0][..., 0] == v[0]) & (ref.fmv[0][..., 1] == v[1])
+    per_tile = share.reshape(H // 32, 32, W // 32, 32).sum(axis=(1, 3))
+    assert (per_tile >= 128).mean() >= 0.5, per_tile
+    if smooth:
+        assert ((dec == oracle.DEC_CHECK_REJECT) & share).sum() >= 50
+
+
 def test_random_content_and_ties(engine):
     """Independent random frames (no motion structure) and a flat reference (all costs tie)."""
     H, W = 48, 80
