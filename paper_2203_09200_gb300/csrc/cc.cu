@@ -58,10 +58,7 @@ constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
-// Box-sum reverse checks (T <= 9): vertical sums of BOX_ND candidates at a time over the tile's
-// rows and the columns -4 .. 35 around it
-constexpr int BOX_ND = 6;                     // candidates per pass
-constexpr int BOX_W = TP + 8;                 // columns -4 .. 35 of the tile
+// Box-sum FRMC checks (T = 9)
 constexpr int BOX_MIN = 128;                  // listed pixels of one vector that pay for a box pass
 constexpr int HS = 2 * kMaxRadius + 1;        // side of the vector histogram
 
@@ -175,12 +172,13 @@ struct Smem {
     uint16_t list[TP * TP];       // tile pixels that need a reverse check
     uint8_t rej[TP * TP];
     CandOrder ord;                // reverse-check lane order of this tile's mode
-    uint32_t vsum[BOX_ND][TP][BOX_W];   // box checks: vertical T-sums per candidate and column
+    uint32_t e0n0[TP][TP];        // box checks: cost | count << 16 of d = 0 per tile pixel
+    uint32_t rejw[TP][TP / 4];    // box checks: rejected bits of each 4-pixel word
     int hist[HS * HS];            // listed pixels per filtered vector
     int boxv;                     // vector (histogram bin) checked by box sums, -1: none
     int nlist;
 };
-static_assert(offsetof(Smem, vsum) % 16 == 0, "vertical sums are read in 16-byte words");
+static_assert(offsetof(Smem, e0n0) % 16 == 0, "d = 0 costs are read in 16-byte words");
 
 static_assert(offsetof(Smem, ord) % 16 == 0, "the lane order is written in 16-byte words");
 
@@ -300,111 +298,116 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     return acc;
 }
 
-// candidate i of the reverse-check window in box order: the centre d = 0 first, then the others
-__device__ __forceinline__ int box_cand(int i, bool frmc, int Rc)
+// Box sums of F_d over the tile for one candidate d (T = 9).  F_d(y) = b_t(y + d) |s_t(y + d) -
+// rec(y + v)| for tile rows r0 - 4 .. r0 + rows + 3 and the 4 columns 4 wi - 4 .. 4 wi - 1 of
+// this lane (wi = 0 and 9 are the halo words), kept as vertical 9-sums in two packed 16-bit words
+// (columns 0, 2 and 1, 3); the horizontal 9-sums come from the neighbouring lanes (lane +- 1 holds
+// word wi -+ 1) as in the forward ME.  fn(j, h02, h13) receives the window sums (H0, H2) and
+// (H1, H3) of output row r0 + j.
+template <int ROWS, typename Fn>
+__device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy, int dx, int vy,
+                                         int vx, Fn &&fn)
 {
-    const int n = frmc ? 49 : (2 * Rc + 1) * (2 * Rc + 1), c = n / 2;
-    return i == 0 ? c : (i <= c ? i - 1 : i);
+    const int jc = (HC - 4 + dx) & 3, wc = wi + ((HC - 4 + dx) >> 2);
+    const int jr = (HC - 4 + vx) & 3, wr = wi + ((HC - 4 + vx) >> 2);
+    const uint2 *cur = sm.csm + jc * CPYC + (r0 - 4 + HC + dy) * RWDC + wc;
+    const uint32_t *ref = sm.rf + jr * CPY + (r0 - 4 + HC + vy) * RWD + wr;
+    uint32_t dlo[ROWS + 8], dhi[ROWS + 8], lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < ROWS + 8; ++i) {
+        const uint2 c = cur[i * RWDC];
+        const uint32_t d4 = __vabsdiffu4(c.x, ref[i * RWD]) & c.y;
+        dlo[i] = __byte_perm(d4, 0u, 0x4240);
+        dhi[i] = __byte_perm(d4, 0u, 0x4341);
+        lo += dlo[i];
+        hi += dhi[i];
+        if (i >= 9) {
+            lo -= dlo[i - 9];
+            hi -= dhi[i - 9];
+        }
+        if (i >= 8) {
+            const uint32_t Q = lo + hi;
+            const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
+            const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
+            const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
+            const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
+            const uint32_t A = __byte_perm(Ql, Q, 0x5432), B = __byte_perm(Q, Qr, 0x5432);
+            const uint32_t h02 = Ql + A + Q + B + lor;
+            fn(i - 8, h02, h02 + Qr - lol - lor);
+        }
+    }
 }
 
-// Reverse checks by box sums for every tile pixel whose filtered vector is v (T <= 9).  The cost
-// of candidate d at pixel p is C(p + d, v - d) = sum over o of F_d(p + o) with
-//     F_d(y) = b_t(y + d) |s_t(y + d) - rec(y + v)|,
-// a T x T box sum of one plane per candidate: the same integers the per-pixel path adds up, so
-// the decisions are identical.  A pass computes the vertical sums of BOX_ND candidates (one
-// thread per candidate, 4-column word and 8-row chunk), then every thread takes the 4 pixels of
-// one tile word: horizontal sums, and the exact SAD/n compare against d = 0 (first candidate).
-// Thread t ends with the verdicts of pixels (t / 8, 4 (t % 8) + c), c = 0..3, in rej.
-template <int T>
-__device__ void box_checks(Smem &sm, const FrameTask &t, int x0, int y0, int vy, int vx,
-                           bool frmc, bool (&rej)[4])
+// FRMC reverse checks by box sums for every tile pixel whose filtered vector is v (T = 9).  The
+// cost of candidate d at pixel p is C(p + d, v - d) = sum over o of F_d(p + o), a 9 x 9 box sum of
+// one plane per candidate: the same integers the per-pixel path adds up, so the decisions are
+// identical.  First each warp computes the d = 0 costs of 4 tile rows (lanes 0..9 hold the words)
+// and stores them with the template counts; then warp w takes candidates 1 + w, 9 + w, ... over
+// the whole tile (lane = 3 chunks of 11 rows x 10 words) and keeps the verdicts of its pixels as
+// bits; they are merged into rejw and written to sm.rej for the pixels with vector v.
+__device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy, int vx,
+                            bool use_nnc)
 {
-    constexpr int h = T / 2;
-    static_assert(h <= 4, "box checks cover columns -4 .. 35 of the tile");
-    const int H = t.H, W = t.W, tid = threadIdx.x;
-    const int n = frmc ? 49 : (2 * t.Rc + 1) * (2 * t.Rc + 1);
-    const int pr = tid >> 3, pw = tid & 7;               // this thread's pixel word
-    int e0[4] = {0, 0, 0, 0}, n0[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) rej[c] = false;
+    const int H = t.H, W = t.W, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool inner = y0 - kMaxRadius >= 0 && x0 - kMaxRadius >= 0 && y0 + TP + kMaxRadius <= H &&
                        x0 + TP + kMaxRadius <= W;
-    // past-frame word of F for tile column 4 wi - 4 at region column 4 wi + HC - 4 + vx
-    const int jr = (HC - 4 + vx) & 3, wr = (HC - 4 + vx) >> 2;
-    for (int base = 0; base < n; base += BOX_ND) {
-        const int nd = min(BOX_ND, n - base);
-        // vertical sums: task = (candidate, word wi of columns 4 wi - 4 .., chunk of 8 rows)
-        for (int task = tid; task < nd * 40; task += NT) {
-            const int dd = task / 40, rem = task - dd * 40, ch = rem / 10, wi = rem - ch * 10;
-            const int ci = box_cand(base + dd, frmc, t.Rc);
-            const int dy = cand_dy(ci, frmc, t.Rc), dx = cand_dx(ci, frmc, t.Rc);
-            const int jc = (HC - 4 + dx) & 3, wc = wi + ((HC - 4 + dx) >> 2);
-            const uint2 *cur = sm.csm + jc * CPYC + (8 * ch - h + HC + dy) * RWDC + wc;
-            const uint32_t *ref = sm.rf + jr * CPY + (8 * ch - h + HC + vy) * RWD + wi + wr;
-            uint32_t dlo[8 + 2 * h], dhi[8 + 2 * h], lo = 0, hi = 0;
-#pragma unroll
-            for (int i = 0; i < 8 + 2 * h; ++i) {
-                const uint2 c = cur[i * RWDC];
-                const uint32_t d4 = __vabsdiffu4(c.x, ref[i * RWD]) & c.y;
-                dlo[i] = __byte_perm(d4, 0u, 0x4240);          // columns 0, 2 as 16-bit lanes
-                dhi[i] = __byte_perm(d4, 0u, 0x4341);          // columns 1, 3
-                lo += dlo[i];
-                hi += dhi[i];
-                if (i >= T) {
-                    lo -= dlo[i - T];
-                    hi -= dhi[i - T];
-                }
-                if (i >= T - 1) {
-                    const int row = 8 * ch + i - (T - 1);
-                    *reinterpret_cast<uint4 *>(&sm.vsum[dd][row][4 * wi]) =
-                        make_uint4(lo & 0xffffu, hi & 0xffffu, lo >> 16, hi >> 16);
-                }
+    {   // d = 0: rows 4 warp .. 4 warp + 3
+        const int wi = min(lane, 9);
+        box_rows<4>(sm, 4 * warp, wi, 0, 0, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
+            if (lane >= 1 && lane <= 8) {
+                const int r = 4 * warp + j, x = 4 * (wi - 1);
+                const uint8_t *nr = &sm.nsrc[r + kMaxRadius][x + kMaxRadius];
+                *reinterpret_cast<uint4 *>(&sm.e0n0[r][x]) =
+                    make_uint4((h02 & 0xffffu) | (uint32_t)nr[0] << 16,
+                               (h13 & 0xffffu) | (uint32_t)nr[1] << 16,
+                               (h02 >> 16) | (uint32_t)nr[2] << 16, (h13 >> 16) | (uint32_t)nr[3] << 16);
             }
+        });
+        sm.rejw[tid >> 3][tid & 7] = 0;
+    }
+    __syncthreads();
+    const int ch = min(lane / 10, 2), wi = lane < 30 ? lane - 10 * ch : 9;
+    const bool out = lane < 30 && wi >= 1 && wi <= 8;
+    uint32_t rb0 = 0, rb1 = 0;                       // verdict bits: row j, pixel q at 4 j + q
+    for (int i = 1 + warp; i < 49; i += NW) {
+        const int ci = i <= 24 ? i - 1 : i;          // the 48 offsets d != 0
+        const int dy = frmc_offset(ci / 7), dx = frmc_offset(ci % 7);
+        box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
+            const int r = 11 * ch + j, x = 4 * (wi - 1);
+            if (!out || r >= TP) return;
+            const uint4 z = *reinterpret_cast<const uint4 *>(&sm.e0n0[r][x]);
+            const uint32_t zz[4] = {z.x, z.y, z.z, z.w};
+            const int e[4] = {(int)(h02 & 0xffffu), (int)(h13 & 0xffffu), (int)(h02 >> 16),
+                              (int)(h13 >> 16)};
+            const uint8_t *nr = &sm.nsrc[r + dy + kMaxRadius][x + dx + kMaxRadius];
+            const bool yin = inner || (unsigned)(y0 + r + dy) < (unsigned)H;
+            uint32_t bits = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool valid = yin && (inner || (unsigned)(x0 + x + q + dx) < (unsigned)W);
+                const int c0 = (int)(zz[q] & 0xffffu), n0 = (int)(zz[q] >> 16);
+                if (valid && e[q] * n0 < c0 * (int)nr[q]) bits |= 1u << q;
+            }
+            if (j < 8) rb0 |= bits << (4 * j);
+            else rb1 |= bits << (4 * (j - 8));
+        });
+    }
+    if (out) {
+#pragma unroll
+        for (int j = 0; j < 11; ++j) {
+            const int r = 11 * ch + j;
+            const uint32_t bits = (j < 8 ? rb0 >> (4 * j) : rb1 >> (4 * (j - 8))) & 15u;
+            if (r < TP && bits) atomicOr(&sm.rejw[r][wi - 1], bits);
         }
-        __syncthreads();
-        // horizontal sums and compare: tile columns 4 pw - h .. 4 pw + 3 + h are vsum columns
-        // 4 pw + 4 - h .. 4 pw + 7 + h; the four window sums slide by one column each
+    }
+    __syncthreads();
+    const int pr = tid >> 3, pw = tid & 7;
+    const uint32_t bits = sm.rejw[pr][pw];
 #pragma unroll
-        for (int dd = 0; dd < BOX_ND; ++dd) {
-            if (dd >= nd) break;
-            const uint4 *vp = reinterpret_cast<const uint4 *>(&sm.vsum[dd][pr][4 * pw]);
-            const uint4 a = vp[0], b = vp[1], c = vp[2];
-            const int v[12] = {(int)a.x, (int)a.y, (int)a.z, (int)a.w, (int)b.x, (int)b.y,
-                               (int)b.z, (int)b.w, (int)c.x, (int)c.y, (int)c.z, (int)c.w};
-            int e[4];
-            int sum = 0;
-#pragma unroll
-            for (int j = -h; j <= h; ++j) sum += v[4 + j];
-            e[0] = sum;
-#pragma unroll
-            for (int q = 1; q < 4; ++q) {
-                sum += v[4 + h + q] - v[3 - h + q];
-                e[q] = sum;
-            }
-            if (base + dd == 0) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    e0[q] = e[q];
-                    n0[q] = sm.nsrc[pr + kMaxRadius][4 * pw + q + kMaxRadius];
-                }
-                continue;
-            }
-            const int ci = box_cand(base + dd, frmc, t.Rc);
-            const int dy = cand_dy(ci, frmc, t.Rc), dx = cand_dx(ci, frmc, t.Rc);
-            const uint8_t *nrow = &sm.nsrc[pr + dy + kMaxRadius][4 * pw + dx + kMaxRadius];
-            if (inner) {                       // every source p + d of the tile is in the frame
-#pragma unroll
-                for (int q = 0; q < 4; ++q) rej[q] = rej[q] || e[q] * n0[q] < e0[q] * (int)nrow[q];
-            } else {
-                const bool yin = (unsigned)(y0 + pr + dy) < (unsigned)H;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool valid = yin && (unsigned)(x0 + 4 * pw + q + dx) < (unsigned)W;
-                    if (valid && e[q] * n0[q] < e0[q] * (int)nrow[q]) rej[q] = true;
-                }
-            }
-        }
-        __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int px = 4 * pw + q;
+        const char2 c = use_nnc ? sm.md[pr + 1][px + 1] : sm.mv[pr + 2][px + 2];
+        if (c.x == vy && c.y == vx) sm.rej[pr * TP + px] = (bits >> q) & 1u;
     }
 }
 
@@ -529,14 +532,14 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         }
         __syncthreads();
         const int nl = sm.nlist;
-        // FRMC: box-sum checks for the vector that most listed pixels share, if at least BOX_MIN
-        // do.  The cost of a candidate over the whole tile is one box sum, so the 49 candidates
+        // FRMC, T = 9: box-sum checks for the vector that most listed pixels share, if at least
+        // BOX_MIN do.  The cost of a candidate over the whole tile is one box sum, so the 49 candidates
         // cost about as much as 130 per-pixel checks.  Under quarter sampling at most a third of
         // the unmeasured pixels of a tile are projectable per past frame (256), so one vector at
         // most pays for it in practice.  RMC stays per pixel: its 289 candidates make the box
         // pass dearer than per-pixel checks, which stop at the first better candidate.
         int boxbin = -1;
-        if constexpr (T <= 9) {
+        if constexpr (T == 9) {
             if (frmc && nl >= BOX_MIN) {
                 for (int i = tid; i < HS * HS; i += NT) sm.hist[i] = 0;
                 __syncthreads();
@@ -555,18 +558,9 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                 }
                 __syncthreads();
                 boxbin = sm.boxv;
-                if (boxbin >= 0) {
-                    const int vy = boxbin / HS - kMaxRadius, vx = boxbin % HS - kMaxRadius;
-                    bool rj[4];
-                    box_checks<T>(sm, t, x0, y0, vy, vx, frmc, rj);
-                    const int pr = tid >> 3, pw = tid & 7;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int px = 4 * pw + q;
-                        const char2 c = use_nnc ? sm.md[pr + 1][px + 1] : sm.mv[pr + 2][px + 2];
-                        if (c.x == vy && c.y == vx) sm.rej[pr * TP + px] = rj[q] ? 1 : 0;
-                    }
-                }
+                if (boxbin >= 0)
+                    box_checks9(sm, t, x0, y0, boxbin / HS - kMaxRadius, boxbin % HS - kMaxRadius,
+                                use_nnc);
             }
         }
         // reverse checks of the other listed pixels: one warp per pixel
