@@ -61,7 +61,9 @@ union WarpSmem {
         float2 w[N * NH];                  // row spectra of the weights, then column pass in place
         float2 f[N * NH];                  // row spectra of the weighted values
     } dft;
-    float2 W[N * WS];                      // full weight spectrum, columns 0..48 (wrapped)
+    float2 W[N * WS + NH];                 // full weight spectrum, columns 0..48 (wrapped),
+                                           // then a zero row (the second term of a self-
+                                           // conjugate update)
 };
 
 // the fields of a FrameTask that the FSR of one block reads
@@ -318,6 +320,7 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     }
 #pragma unroll
     for (int l = 0; l < NH; ++l) ws.W[k * WS + N + l] = ws.W[k * WS + l];
+    if (lane < NH) ws.W[N * WS + lane] = make_float2(0.f, 0.f);
     __syncwarp();
     const float W0 = ws.W[0].x;
 
@@ -330,8 +333,13 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     }
 
     const int pm = (lane >> 2) & 3, pn = lane & 3;     // block pixel of lanes 0..15
+    const int jm = o + pm, jn = o + pn;
     float g = 0.f;
     const float gscale = W0 > 0.f ? gamma / W0 : 0.f;
+    // the model term of the previous iteration, added while this iteration's reductions run:
+    // g += gf (dr cos - di sin) at phase jp (gf = 1 for a self-conjugate bin, else 2)
+    float gdr = 0.f, gdi = 0.f, gf = 0.f;
+    int jp = 0;
     for (int it = 0; it < iters && W0 > 0.f; ++it) {
         // Selection key of slot s: the bits of e = wf |R|^2 (e >= 0, so they order like e) with
         // the low 5 bits replaced by 31 - s.  The integer maximum then picks the largest e and,
@@ -347,7 +355,9 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
 #pragma unroll
             for (int s = 0; s + w < NH; s += 2 * w) key[s] = max(key[s], key[s + w]);
         const uint32_t best = key[0];
+        g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
         const uint32_t m = __reduce_max_sync(0xffffffffu, best);
+        gf = 0.f;
         if ((m >> 5) == 0) break;                      // residual exhausted
         // among the lanes whose value reaches the maximum, the lowest canonical index wins
         const int mykey = ((best ^ m) >> 5) == 0 ? rowbase + 31 - (int)(best & 31) : 0x7fffffff;
@@ -371,28 +381,27 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
         const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
         const float dr = gscale * ure;
         const float di = self ? 0.f : gscale * uim;
-        // W(kap - u) and W(kap + u) of the held bins start at columns (c0 -+ u_l) mod 32
+        // W(kap - u) and W(kap + u) of the held bins start at columns (c0 -+ u_l) mod 32; a
+        // self-conjugate u has no second term, so its second read is the zero row
         const float2 *pa = ws.W + ((kap - uk) & (N - 1)) * WS + ((c0 - ul) & (N - 1));
-        const float2 *pc = ws.W + ((kap + uk) & (N - 1)) * WS + ((c0 + ul) & (N - 1));
-        // packed FP32 pairs: R -= dr (a + c) + di (c.y - a.y, a.x - c.x), or R -= dr a (self)
+        const float2 *pc = self ? ws.W + N * WS
+                                : ws.W + ((kap + uk) & (N - 1)) * WS + ((c0 + ul) & (N - 1));
+        // packed FP32 pairs: R -= dr (a + c) + di (c.y - a.y, a.x - c.x)
         const float2 ndr = make_float2(-dr, -dr), ndi = make_float2(-di, -di);
-        if (self) {
 #pragma unroll
-            for (int l = 0; l < NH; ++l) Rr[l] = __ffma2_rn(ndr, pa[l], Rr[l]);
-        } else {
-#pragma unroll
-            for (int l = 0; l < NH; ++l) {
-                const float2 a = pa[l], c = pc[l];
-                const float2 s = __fadd2_rn(a, c);
-                const float2 q = make_float2(c.y - a.y, a.x - c.x);
-                Rr[l] = __ffma2_rn(ndi, q, __ffma2_rn(ndr, s, Rr[l]));
-            }
+        for (int l = 0; l < NH; ++l) {
+            const float2 a = pa[l], c = pc[l];
+            const float2 s = __fadd2_rn(a, c);
+            const float2 q = make_float2(c.y - a.y, a.x - c.x);
+            Rr[l] = __ffma2_rn(ndi, q, __ffma2_rn(ndr, s, Rr[l]));
         }
-        // model at the block pixel of this lane: g += (1 or 2) Re(dc phi_u)
-        const int j = (uk * (o + pm) + ul * (o + pn)) & (N - 1);
-        const float re_part = dr * tw.cs[j] - di * tw.sn[j];
-        g += self ? re_part : 2.f * re_part;
+        // model at the block pixel of this lane, added in the next iteration (or after the loop)
+        jp = (uk * jm + ul * jn) & (N - 1);
+        gdr = dr;
+        gdi = di;
+        gf = self ? 1.f : 2.f;
     }
+    g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
 
     // 5. output: D-FSR overwrite and the 8-bit reconstruction
     if (lane < kFsrB * kFsrB) {
