@@ -355,12 +355,13 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
 #pragma unroll
             for (int s = 0; s + w < NH; s += 2 * w) key[s] = max(key[s], key[s + w]);
         const uint32_t best = key[0];
+        const int cand = rowbase + 31 - (int)(best & 31);   // canonical index of the lane's best
         g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
         const uint32_t m = __reduce_max_sync(0xffffffffu, best);
         gf = 0.f;
         if ((m >> 5) == 0) break;                      // residual exhausted
         // among the lanes whose value reaches the maximum, the lowest canonical index wins
-        const int mykey = ((best ^ m) >> 5) == 0 ? rowbase + 31 - (int)(best & 31) : 0x7fffffff;
+        const int mykey = ((best ^ m) >> 5) == 0 ? cand : 0x7fffffff;
         const int win = __reduce_min_sync(0xffffffffu, mykey);
         const int uk = win >> 5, ul = win & (N - 1);   // the canonical bin u
         // R(u) from its owner: lane uk, slot ul (ul <= 16) or lane 32 - uk, slot ul - 16; the

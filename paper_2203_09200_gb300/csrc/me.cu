@@ -192,9 +192,11 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
+// The staged past-frame window in four byte-shifted copies: copy j, word w of a row holds row
+// bytes 4 w + j .. 4 w + j + 3, so the word a lane compares at any column is one aligned load.
 template <int WARPS>
 struct Smem9 {
-    uint32_t rf[s_rrows<WARPS>() * S_RWORDS];
+    uint32_t rf[4][s_rrows<WARPS>() * S_RWORDS];
     short2 vord[NVMAX];
 };
 
@@ -218,7 +220,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
         uint32_t v = 0;
 #pragma unroll
         for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
-        sm.rf[i] = v;
+        sm.rf[0][i] = v;
     }
     build_tie_order(sm.vord, R);
 
@@ -245,6 +247,14 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
         cmk[i] = m;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nrows * (S_RWORDS - 1); i += S_NT) {
+        const int j = 1 + i / (nrows * (S_RWORDS - 1));
+        const int rem = i - (j - 1) * nrows * (S_RWORDS - 1);
+        const int r = rem / (S_RWORDS - 1), w = rem - r * (S_RWORDS - 1);
+        sm.rf[j][r * S_RWORDS + w] =
+            __funnelshift_r(sm.rf[0][r * S_RWORDS + w], sm.rf[0][r * S_RWORDS + w + 1], 8 * j);
+    }
+    __syncthreads();
 
     // border handling: candidates with p + v outside the frame are not allowed
     const bool border = (x0 - 4 - R < 0) || (x0 + 124 + R > W) || (y0 - R < 0) || (y0 + S_OUTH + R > H);
@@ -261,8 +271,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
         const short2 v = sm.vord[o];
         const int vy = v.x, vx = v.y;
         const int sh = (vx + R) & 3, q = (vx + R) >> 2;
-        const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)sh;
-        const uint32_t *rrow = sm.rf + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
+        const uint32_t *rrow = sm.rf[sh] + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
         uint32_t inv02 = 0, inv13 = 0;                     // lanes of invalid columns -> 0x7fff
         if (border) {
             const int c0 = cx + vx;
@@ -276,8 +285,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
         const uint32_t o2 = (uint32_t)o * 0x00010001u;
 #pragma unroll
         for (int i = 0; i < S_DROWS; ++i) {
-            const uint32_t r4 = __byte_perm(rrow[i * S_RWORDS], rrow[i * S_RWORDS + 1], sel);
-            const uint32_t d4 = __vabsdiffu4(cs[i], r4) & cmk[i];
+            const uint32_t d4 = __vabsdiffu4(cs[i], rrow[i * S_RWORDS]) & cmk[i];
             dlo[i] = __byte_perm(d4, 0u, 0x4240);
             dhi[i] = __byte_perm(d4, 0u, 0x4341);
             lo = imad(dlo[i], one, lo);
@@ -339,8 +347,8 @@ __global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
 
 __global__ void __launch_bounds__(s_nt<8>(), 2) me9_kernel(FrameTask t)
 {
-    __shared__ Smem9<8> sm;
-    me9_tile<8>(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    me9_tile<8>(*reinterpret_cast<Smem9<8> *>(smem_raw), t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // batched forms on the tile queue: tiles of a task flattened as (k, by, bx), bx fastest
@@ -358,7 +366,8 @@ __global__ void __launch_bounds__(NT) me_batched_kernel(BatchDesc *bd)
 template <int WARPS>
 __global__ void __launch_bounds__(s_nt<WARPS>(), 16 / WARPS) me9_batched_kernel(BatchDesc *bd)
 {
-    __shared__ Smem9<WARPS> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem9<WARPS> &sm = *reinterpret_cast<Smem9<WARPS> *>(smem_raw);
     __shared__ FrameTask task;
     __shared__ int claim[2];
     claim_tiles(bd, kPhMe, task, claim, [&](const FrameTask &t, int l) {
@@ -558,6 +567,23 @@ __global__ void __launch_bounds__(R9_NT, 2) rme9_batched_kernel(BatchDesc *bd)
 
 }  // namespace
 
+cudaError_t init_me(int dev)
+{
+    static int ready[64] = {};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (ready[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(me9_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem9<8>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(me9_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Smem9<8>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(me9_batched_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(Smem9<4>));
+    if (e == cudaSuccess) ready[dev] = 1;
+    return e;
+}
+
 int tiles_me(const FrameTask &t, int me_warps, int me_box)
 {
     if (t.K <= 0) return 0;
@@ -570,8 +596,12 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
 {
     if (t.K <= 0) return cudaSuccess;
     if (t.T == 9) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = init_me(dev);
+        if (e != cudaSuccess) return e;
         dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + s_outh<8>() - 1) / s_outh<8>(), t.K);
-        me9_kernel<<<grid, s_nt<8>(), 0, st>>>(t);
+        me9_kernel<<<grid, s_nt<8>(), sizeof(Smem9<8>), st>>>(t);
     } else {
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);
@@ -606,12 +636,18 @@ cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st)
 cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, int me_box, cudaStream_t st)
 {
     if (T == 9 && me_box) T = 0;                 // the box-sum kernel below handles any T
+    if (T == 9) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = init_me(dev);
+        if (e != cudaSuccess) return e;
+    }
     if (T == 9 && me_warps == 4) {
-        static const int grid = persistent_grid(me9_batched_kernel<4>, s_nt<4>(), 0);
-        me9_batched_kernel<4><<<grid, s_nt<4>(), 0, st>>>(bd);
+        static const int grid = persistent_grid(me9_batched_kernel<4>, s_nt<4>(), sizeof(Smem9<4>));
+        me9_batched_kernel<4><<<grid, s_nt<4>(), sizeof(Smem9<4>), st>>>(bd);
     } else if (T == 9) {
-        static const int grid = persistent_grid(me9_batched_kernel<8>, s_nt<8>(), 0);
-        me9_batched_kernel<8><<<grid, s_nt<8>(), 0, st>>>(bd);
+        static const int grid = persistent_grid(me9_batched_kernel<8>, s_nt<8>(), sizeof(Smem9<8>));
+        me9_batched_kernel<8><<<grid, s_nt<8>(), sizeof(Smem9<8>), st>>>(bd);
     } else {
         static const int grid = persistent_grid(me_batched_kernel, NT, 0);
         me_batched_kernel<<<grid, NT, 0, st>>>(bd);

@@ -752,6 +752,8 @@ int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
     if (ie != cudaSuccess) return bail(ie, "FSR set-up");
     ie = init_cc(cfg->device);
     if (ie != cudaSuccess) return bail(ie, "check set-up");
+    ie = init_me(cfg->device);
+    if (ie != cudaSuccess) return bail(ie, "ME set-up");
     if (batched(e)) {
         for (auto &set : e->sets) {
             cudaError_t er = cudaHostAlloc((void **)&set.h, sizeof(BatchDesc), cudaHostAllocPortable);

@@ -189,6 +189,8 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st);
 cudaError_t init_fsr(int device);
 // one-time per-device set-up of the check kernel (reverse-check lane orders)
 cudaError_t init_cc(int device);
+// one-time per-device set-up of the T = 9 ME kernels (shared-memory limit)
+cudaError_t init_me(int device);
 
 // set the calling thread's rfsr_last_error() message; returns code
 int set_error(int code, const std::string &msg);
