@@ -108,7 +108,8 @@ void fill_fsr_tables(FsrTables &tb, double rho)
 
 using Clock = std::chrono::steady_clock;
 
-// bounded wait on an event: polls (never blocks the driver) and gives up after timeout_ms
+// bounded wait on an event: polls (never blocks inside the CUDA runtime) and gives up after
+// timeout_ms
 int wait_event(cudaEvent_t ev, int timeout_ms, Clock::time_point t0 = Clock::now())
 {
     int spins = 0;
