@@ -214,6 +214,55 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
+// Support row m (frame row y) at support column `lane` (frame column x) of block (bi, bj): the
+// weight rho^d (x mu for projected pixels, x delta for concealed ones) and the weighted value.
+__device__ __forceinline__ void support_row(WarpSmem &ws, const FsrArgs &a, int m, int x, int y,
+                                            int bi, int bj, int lane)
+{
+    float wt = 0.f, val = 0.f;
+    if ((unsigned)x < (unsigned)a.W && (unsigned)y < (unsigned)a.H) {
+        const size_t i = (size_t)y * a.W + x;
+        const float wd = __ldg(&a.tab->wsp[m * N + lane]);
+        const unsigned mk = __ldg(a.msk + i), sv = __ldg(a.smp + i);
+        const unsigned c = a.pcnt != nullptr ? __ldg(a.pcnt + i) : 0u;
+        const unsigned ps = a.pcnt != nullptr ? __ldg(a.psum + i) : 0u;
+        if (mk) {
+            wt = wd;
+            val = (float)sv * (1.0f / 255.0f);
+        } else if (c) {
+            wt = a.mu * wd;
+            val = (float)ps / (255.0f * (float)c);
+        } else if (a.delta > 0.f && (y / kFsrB < bi || (y / kFsrB == bi && x / kFsrB < bj))) {
+            wt = a.delta * wd;                   // reconstructed earlier (raster order)
+            val = a.conc[i];
+        }
+    }
+    ws.sup.w[m * SS + lane] = wt;
+    ws.sup.f[m * SS + lane] = wt * val;
+}
+
+// output of one block pixel: D-FSR overwrite (R-FSR also overwrites projected pixels) and the
+// 8-bit reconstruction
+__device__ __forceinline__ void store_pixel(const FsrArgs &a, int y, int x, float g)
+{
+    if (y >= a.H || x >= a.W) return;
+    const size_t i = (size_t)y * a.W + x;
+    float v = g;
+    uint8_t q;
+    if (a.msk[i]) {
+        v = (float)a.smp[i] * (1.0f / 255.0f);
+        q = a.smp[i];
+    } else {
+        if (a.overwrite && a.pcnt != nullptr && a.pcnt[i])
+            v = (float)a.psum[i] / (255.0f * (float)a.pcnt[i]);
+        const float r = rintf(255.0f * v);
+        q = (uint8_t)fminf(fmaxf(r, 0.0f), 255.0f);
+    }
+    if (a.fsr_out) a.fsr_out[i] = v;
+    if (a.rec) a.rec[i] = q;
+    if (a.out_u8) a.out_u8[i] = q;
+}
+
 // block b of a frame, computed by one warp with its shared-memory area ws; tw holds the
 // twiddles.  Block 0 also publishes the frame's final status word.
 __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, const FsrArgs &a, int b)
@@ -235,36 +284,9 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
 
     // 1. support: lane = column, coalesced row loads; rows unrolled so that their loads overlap
     {
-        const uint8_t *msk = a.msk, *smp = a.smp, *pcnt = a.pcnt;
-        const uint16_t *psum = a.psum;
-        const float mu = a.mu, delta = a.delta;
         const int x = xs + lane;
-        const bool xin = (unsigned)x < (unsigned)W;
-        const bool xearlier = x / kFsrB < bj;   // column of a block left of this one
 #pragma unroll 4
-        for (int m = 0; m < N; ++m) {
-            const int y = ys + m;
-            float wt = 0.f, val = 0.f;
-            if (xin && (unsigned)y < (unsigned)H) {
-                const size_t i = (size_t)y * W + x;
-                const float wd = __ldg(&tab->wsp[m * N + lane]);
-                const unsigned mk = __ldg(msk + i), sv = __ldg(smp + i);
-                const unsigned c = pcnt != nullptr ? __ldg(pcnt + i) : 0u;
-                const unsigned ps = pcnt != nullptr ? __ldg(psum + i) : 0u;
-                if (mk) {
-                    wt = wd;
-                    val = (float)sv * (1.0f / 255.0f);
-                } else if (c) {
-                    wt = mu * wd;
-                    val = (float)ps / (255.0f * (float)c);
-                } else if (delta > 0.f && (y / kFsrB < bi || (y / kFsrB == bi && xearlier))) {
-                    wt = delta * wd;                     // reconstructed earlier (raster order)
-                    val = a.conc[i];
-                }
-            }
-            ws.sup.w[m * SS + lane] = wt;
-            ws.sup.f[m * SS + lane] = wt * val;
-        }
+        for (int m = 0; m < N; ++m) support_row(ws, a, m, x, ys + m, bi, bj, lane);
     }
     __syncwarp();
 
@@ -405,26 +427,175 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
 
     // 5. output: D-FSR overwrite and the 8-bit reconstruction
-    if (lane < kFsrB * kFsrB) {
-        const int y = kFsrB * bi + pm, x = kFsrB * bj + pn;
-        if (y < H && x < W) {
-            const size_t i = (size_t)y * W + x;
-            float v = g;
-            uint8_t q;
-            if (a.msk[i]) {
-                v = (float)a.smp[i] * (1.0f / 255.0f);
-                q = a.smp[i];
-            } else {
-                if (a.overwrite && a.pcnt != nullptr && a.pcnt[i])
-                    v = (float)a.psum[i] / (255.0f * (float)a.pcnt[i]);
-                const float r = rintf(255.0f * v);
-                q = (uint8_t)fminf(fmaxf(r, 0.0f), 255.0f);
-            }
-            if (a.fsr_out) a.fsr_out[i] = v;
-            if (a.rec) a.rec[i] = q;
-            if (a.out_u8) a.out_u8[i] = q;
+    if (lane < kFsrB * kFsrB) store_pixel(a, kFsrB * bi + pm, kFsrB * bj + pn, g);
+}
+
+// The same block computed by MW warps together (concealed weighting > 0, where blocks run as
+// wavefronts and the time is one block's latency, not the throughput of many).  Warp w holds the
+// slots s = w + MW j of every lane (slot 16 in warp 0), so a warp scans and updates a quarter of
+// the bins.  One barrier per iteration publishes every warp's best key and its lowest canonical
+// index among the lanes that reach it (the global winner is the lowest index among the warps
+// whose maximum is the global one); a second one publishes R(u) from its owner.  Every bin sees
+// the same operations in the same order as in fsr_block, so the results are identical.  (One
+// barrier with every warp's candidate R published beside its key measured slower.)
+constexpr int MW = 4;                      // warps per block
+constexpr int MWS = (NH + MW - 1) / MW;    // slots per lane and warp (the last only in warp 0)
+
+struct MwSmem {
+    Twiddles tw;
+    WarpSmem ws;
+    uint32_t redm[MW];                     // per warp: maximum key
+    int redc[MW];                          // per warp: lowest canonical index at its maximum
+    float2 ru;                             // R(u) of the winning bin
+};
+
+__device__ void fsr_block_mw(MwSmem &sm, const FsrArgs &a, int b)
+{
+    WarpSmem &ws = sm.ws;
+    const Twiddles &tw = sm.tw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int status = *a.status;
+    if (b == 0 && tid == 0 && a.status_out != nullptr) *a.status_out = status;
+    if (status) return;
+    const int H = a.H, W = a.W;
+    const int nbx = (W + kFsrB - 1) / kFsrB, nby = (H + kFsrB - 1) / kFsrB;
+    if (b >= nbx * nby) return;
+    const int bi = b / nbx, bj = b - bi * nbx;
+    const int o = (N - kFsrB) / 2;
+    const int ys = kFsrB * bi - o, xs = kFsrB * bj - o;
+    const FsrTables *tab = a.tab;
+
+    // 1. support: warp w loads rows w, w + MW, ...
+    for (int m = warp; m < N; m += MW) support_row(ws, a, m, xs + lane, ys + m, bi, bj, lane);
+    __syncthreads();
+    // 2. row DFTs: thread t < 2N transforms row t % N of the weights (t < N) or of the values
+    {
+        float x[N];
+        const int row = tid & (N - 1);
+        const float *src = tid < N ? ws.sup.w : ws.sup.f;
+        if (tid < 2 * N) {
+#pragma unroll
+            for (int n = 0; n < N; ++n) x[n] = src[row * SS + n];
         }
+        __syncthreads();                                   // the union is rewritten below
+        if (tid < 2 * N) real_row_dft(x, &(tid < N ? ws.dft.w : ws.dft.f)[row * NH]);
     }
+    __syncthreads();
+    // 3. column DFTs in place: 17 columns of W, then 17 of R
+    if (tid < 2 * NH) column_dft(tid < NH ? ws.dft.w : ws.dft.f, tid < NH ? tid : tid - NH);
+    __syncthreads();
+
+    // 4. this warp's slots of the half spectrum (layout as in fsr_block); warp 0 builds W
+    const int k = lane;
+    const bool upper = k > N / 2;
+    const int kap = upper ? N - k : k;
+    const int c0 = upper ? N / 2 : 0;
+    const int rowbase = kap * N + c0;
+    float2 Rr[MWS];
+    float wfr[MWS];
+#pragma unroll
+    for (int j = 0; j < MWS; ++j) {
+        const int sl = warp + MW * j;
+        const bool mine = sl < NH;
+        const int sc = mine ? sl : 0;
+        const float2 r = ws.dft.f[k * NH + (upper ? NH - 1 - sc : sc)];
+        Rr[j] = !mine ? make_float2(0.f, 0.f) : (upper ? make_float2(r.x, -r.y) : r);
+        const bool held = mine && (!upper || (sc != 0 && sc != NH - 1));
+        wfr[j] = held ? __ldg(&tab->wf[k * NH + (upper ? NH - 1 - sc : sc)]) : 0.f;
+    }
+    float2 Wt[NH];
+    if (warp == 0) {
+#pragma unroll
+        for (int l = 0; l < NH; ++l) Wt[l] = ws.dft.w[k * NH + l];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int l = 0; l < NH; ++l) ws.W[k * WS + l] = Wt[l];
+        __syncwarp();
+#pragma unroll
+        for (int l = NH; l < N; ++l) {
+            const float2 w2 = ws.W[((N - k) & (N - 1)) * WS + (N - l)];
+            ws.W[k * WS + l] = make_float2(w2.x, -w2.y);
+        }
+#pragma unroll
+        for (int l = 0; l < NH; ++l) ws.W[k * WS + N + l] = ws.W[k * WS + l];
+        if (lane < NH) ws.W[N * WS + lane] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float W0 = ws.W[0].x;
+
+    const int pm = (lane >> 2) & 3, pn = lane & 3;
+    const int jm = o + pm, jn = o + pn;
+    float g = 0.f;
+    const float gscale = W0 > 0.f ? a.gamma / W0 : 0.f;
+    float gdr = 0.f, gdi = 0.f, gf = 0.f;
+    int jp = 0;
+    for (int it = 0; it < a.iters && W0 > 0.f; ++it) {
+        uint32_t key[MWS];
+#pragma unroll
+        for (int j = 0; j < MWS; ++j) {
+            const float e = wfr[j] * fmaf(Rr[j].x, Rr[j].x, Rr[j].y * Rr[j].y);
+            key[j] = (__float_as_uint(e) & ~31u) | (uint32_t)(31 - min(warp + MW * j, NH - 1));
+        }
+#pragma unroll
+        for (int w = 1; w < MWS; w *= 2)
+#pragma unroll
+            for (int j = 0; j + w < MWS; j += 2 * w) key[j] = max(key[j], key[j + w]);
+        const uint32_t best = key[0];
+        const int cand = rowbase + 31 - (int)(best & 31);
+        g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
+        gf = 0.f;
+        const uint32_t mw = __reduce_max_sync(0xffffffffu, best);
+        const int cw = __reduce_min_sync(0xffffffffu, ((best ^ mw) >> 5) == 0 ? cand : 0x7fffffff);
+        if (lane == 0) {
+            sm.redm[warp] = mw;
+            sm.redc[warp] = cw;
+        }
+        __syncthreads();
+        uint32_t m = 0;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) m = max(m, sm.redm[w]);
+        int win = 0x7fffffff;
+#pragma unroll
+        for (int w = 0; w < MW; ++w)
+            if (((sm.redm[w] ^ m) >> 5) == 0) win = min(win, sm.redc[w]);
+        if ((m >> 5) == 0) break;                        // residual exhausted (the whole block)
+        const int uk = win >> 5, ul = win & (N - 1);
+        const int owner = ul <= N / 2 ? uk : N - uk;
+        const int slot = ul <= N / 2 ? ul : ul - N / 2;
+        if (warp == (slot & (MW - 1)) && lane == owner) {
+            const int j = slot / MW;                       // warp-uniform
+            float2 rv = Rr[0];
+#pragma unroll
+            for (int jj = 1; jj < MWS; ++jj) if (j == jj) rv = Rr[jj];
+            sm.ru = rv;
+        }
+        __syncthreads();
+        const float2 ru = sm.ru;
+        const bool self = ((uk & (N / 2 - 1)) == 0) && ((ul & (N / 2 - 1)) == 0);
+        const float dr = gscale * ru.x;
+        const float di = self ? 0.f : gscale * ru.y;
+        const float2 *pa = ws.W + ((kap - uk) & (N - 1)) * WS + ((c0 - ul) & (N - 1)) + warp;
+        const float2 *pc = (self ? ws.W + N * WS
+                                 : ws.W + ((kap + uk) & (N - 1)) * WS + ((c0 + ul) & (N - 1))) + warp;
+        const float2 ndr = make_float2(-dr, -dr), ndi = make_float2(-di, -di);
+#pragma unroll
+        for (int j = 0; j < MWS; ++j) {
+            if (warp + MW * j >= NH) break;                // slot 16: warp 0 only
+            const float2 av = pa[MW * j], cv = pc[MW * j];
+            const float2 sv = __fadd2_rn(av, cv);
+            const float2 q = make_float2(cv.y - av.y, av.x - cv.x);
+            Rr[j] = __ffma2_rn(ndi, q, __ffma2_rn(ndr, sv, Rr[j]));
+        }
+        jp = (uk * jm + ul * jn) & (N - 1);
+        gdr = dr;
+        gdi = di;
+        gf = self ? 1.f : 2.f;
+    }
+    g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
+    // 5. output: warp 0 holds the model at the 16 block pixels
+    if (warp == 0 && lane < kFsrB * kFsrB) store_pixel(a, kFsrB * bi + pm, kFsrB * bj + pn, g);
 }
 
 __device__ __forceinline__ void load_twiddles(Twiddles &tw)
@@ -450,20 +621,18 @@ __global__ void __launch_bounds__(WPB1 * 32, 4) fsr_kernel(FrameTask t)
 
 // Concealed weighting > 0: block (i, j) reads the blocks before it in raster order that overlap
 // its support (rows i-4 .. i-1 at columns j-4 .. j+4, and row i left of j), so blocks run as
-// wavefronts w = 5 i + j -- every such block has a smaller w.  One launch per wave; warp b of the
-// launch takes the b-th block (i = i_lo + b, j = w - 5 i) of that wave.
-__global__ void __launch_bounds__(WPB1 * 32, 4) fsr_wave_kernel(FrameTask t, int wave, int i_lo,
-                                                                 int count)
+// wavefronts w = 5 i + j -- every such block has a smaller w.  One launch per wave; CTA b of the
+// launch (MW warps) takes the b-th block (i = i_lo + b, j = w - 5 i) of that wave.
+__global__ void __launch_bounds__(MW * 32) fsr_wave_kernel(FrameTask t, int wave, int i_lo, int count)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<WPB1> &sm = *reinterpret_cast<Smem<WPB1> *>(smem_raw);
+    __shared__ __align__(16) MwSmem sm;
     load_twiddles(sm.tw);
-    const int warp = threadIdx.x >> 5, b = blockIdx.x * WPB1 + warp;
+    const int b = blockIdx.x;
     if (b >= count) return;
     const int i = i_lo + b, j = wave - 5 * i;
     FsrArgs a;
     fsr_args(a, t);
-    fsr_block(sm.tw, sm.w[warp], a, i * ((t.W + kFsrB - 1) / kFsrB) + j);
+    fsr_block_mw(sm, a, i * ((t.W + kFsrB - 1) / kFsrB) + j);
 }
 
 // batched form: CTAs claim tiles (WPB consecutive blocks of one task) in increasing order from
@@ -527,7 +696,6 @@ cudaError_t init_fsr(int dev)
     cudaError_t e = cudaMemcpyToSymbol(c_cs, cs, sizeof(cs));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sn, sn, sizeof(sn));
     if (e == cudaSuccess) e = smem_attr(fsr_kernel, sizeof(Smem<WPB1>));
-    if (e == cudaSuccess) e = smem_attr(fsr_wave_kernel, sizeof(Smem<WPB1>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2>, sizeof(Smem<2>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4>, sizeof(Smem<4>));
     if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8>, sizeof(Smem<8>));
@@ -580,8 +748,7 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
             const int i_hi = w / 5 < nby - 1 ? w / 5 : nby - 1;
             const int count = i_hi - i_lo + 1;
             if (count <= 0) continue;
-            fsr_wave_kernel<<<(count + WPB1 - 1) / WPB1, WPB1 * 32, sizeof(Smem<WPB1>), st>>>(
-                t, w, i_lo, count);
+            fsr_wave_kernel<<<count, MW * 32, 0, st>>>(t, w, i_lo, count);
             count_launch();
         }
         return cudaGetLastError();
