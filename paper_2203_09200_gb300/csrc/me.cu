@@ -484,6 +484,7 @@ __device__ __forceinline__ void rme9_tile(SmemR9 &sm, const FrameTask &t, int tb
 #pragma unroll
         for (int c = 0; c < 4; ++c) best[j][c] = 0x7fffu | (1u << 24);   // "infinite", n = 1
     const int nv = (2 * R + 1) * (2 * R + 1);
+    const uint32_t one = (uint32_t)(W > 0), m1 = 0u - one;  // 1 and -1 (W > 0 always)
     for (int o = 0; o < nv; ++o) {
         const short2 w = sm.vord[o];
         const int wy = w.x, wx = w.y;
@@ -501,23 +502,23 @@ __device__ __forceinline__ void rme9_tile(SmemR9 &sm, const FrameTask &t, int tb
             const uint32_t d4 = __vabsdiffu4(fr[i], c4) & m4;
             dlo[i] = __byte_perm(d4, 0u, 0x4240);
             dhi[i] = __byte_perm(d4, 0u, 0x4341);
-            lo += dlo[i];
-            hi += dhi[i];
+            lo = imad(dlo[i], one, lo);
+            hi = imad(dhi[i], one, hi);
             if (i >= 9) {
-                lo -= dlo[i - 9];
-                hi -= dhi[i - 9];
+                lo = imad(dlo[i - 9], m1, lo);
+                hi = imad(dhi[i - 9], m1, hi);
             }
             if (i >= 8) {
                 const int j = i - 8;                       // output row of this window
-                const uint32_t Q = lo + hi;
+                const uint32_t Q = imad(hi, one, lo);
                 const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
                 const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
                 const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
                 const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
                 const uint32_t A = __byte_perm(Ql, Q, 0x5432);
                 const uint32_t B = __byte_perm(Q, Qr, 0x5432);
-                const uint32_t h02 = Ql + A + Q + B + lor;   // SADs of columns 0, 2
-                const uint32_t h13 = h02 + Qr - lol - lor;   // SADs of columns 1, 3
+                const uint32_t h02 = imad(lor, one, imad(imad(B, one, Q), one, imad(A, one, Ql)));
+                const uint32_t h13 = imad(imad(lol, m1, Qr), one, imad(lor, m1, h02));
                 const uint32_t n4 = __byte_perm(nrow[j * S_RWORDS], nrow[j * S_RWORDS + 1], sel);
                 const uint32_t sad[4] = {h02 & 0xffffu, h13 & 0xffffu, h02 >> 16, h13 >> 16};
 #pragma unroll
