@@ -22,6 +22,8 @@
 //   3. horizontal running sums over T columns -> C(p, v),
 // so a cost costs O(1) operations instead of T^2.  The running minimum is an exact integer key
 // (cost << 9 | position of v in tie order), so the argmin and its tie rule are bit-exact.
+#include <type_traits>
+
 #include "rfsr_internal.h"
 
 namespace rfsr {
@@ -154,14 +156,16 @@ __device__ __forceinline__ void me_tile(Smem &sm, const FrameTask &t, int tbx, i
 // ---------------------------------------------------------------------------------------------
 // T = 9: warp-strip kernel with byte SIMD.  Lane l of a warp owns four adjacent columns (one
 // 32-bit word of bytes) of a 128-column strip, the warp owns 8 output rows, the CTA 8 warps.
-// For each candidate the lane walks the 16 rows of D_v its outputs need: one byte permute to
-// align the past-frame word, __vabsdiffu4, AND with the mask, and running vertical sums kept as
-// two packed 16-bit words (columns 0,2 and 1,3).  The 9-column horizontal sums take the left and
-// right lanes' vertical sums (four shuffles) and a few packed adds.  The running argmin is packed
-// too: two outputs per word, a guard-bit compare (cost + 0x7fff - new has its lane MSB set iff
-// new < cost), a sign-replicating prmt into a lane mask and two bit selects.  Candidates
-// run in tie order with strict improvement, so the first minimum in tie order wins.  Lanes 0 and
-// 31 only feed their neighbours: a strip yields 120 output columns.
+// For each candidate the lane walks the 16 rows of D_v its outputs need: one aligned load of the
+// past-frame word from the byte-shifted copy of its column phase, __vabsdiffu4, AND with the
+// mask, and running vertical sums kept as two packed 16-bit words (columns 0,2 and 1,3).  The
+// 9-column horizontal sums take the left and right lanes' vertical sums (four shuffles) and a few
+// packed adds.  The running argmin is packed too: two outputs per word, a guard-bit compare
+// (cost + 0x7fff - new has its lane MSB set iff new < cost), a sign-replicating prmt into a lane
+// mask and two bit selects.  Candidates run in tie order with strict improvement, so the first
+// minimum in tie order wins.  Lanes 0 and 31 only feed their neighbours: a strip yields 120
+// output columns.  CTAs whose candidates all stay inside the frame run a loop without the
+// border masks.
 // ---------------------------------------------------------------------------------------------
 // The template tile of a CTA is WARPS strips of 8 rows x 120 columns; its search window (the
 // staged past-frame rows) is the tile plus the template half and the radius on each side.
@@ -267,60 +271,65 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
     const int nv = (2 * R + 1) * (2 * R + 1);
     const int oy = y0 + S_ROWS * warp;                     // first output row of the warp
     const uint32_t one = (uint32_t)(W > 0), m1 = 0u - one;  // 1 and -1 (W > 0 always)
-    for (int o = 0; o < nv; ++o) {
-        const short2 v = sm.vord[o];
-        const int vy = v.x, vx = v.y;
-        const int sh = (vx + R) & 3, q = (vx + R) >> 2;
-        const uint32_t *rrow = sm.rf[sh] + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
-        uint32_t inv02 = 0, inv13 = 0;                     // lanes of invalid columns -> 0x7fff
-        if (border) {
-            const int c0 = cx + vx;
-            inv02 = ((unsigned)(c0) >= (unsigned)W ? 0x7fffu : 0u) |
-                    ((unsigned)(c0 + 2) >= (unsigned)W ? 0x7fff0000u : 0u);
-            inv13 = ((unsigned)(c0 + 1) >= (unsigned)W ? 0x7fffu : 0u) |
-                    ((unsigned)(c0 + 3) >= (unsigned)W ? 0x7fff0000u : 0u);
-        }
-        uint32_t lo = 0, hi = 0;                           // vertical sums, columns (0,2) (1,3)
-        uint32_t dlo[S_DROWS], dhi[S_DROWS];
-        const uint32_t o2 = (uint32_t)o * 0x00010001u;
-#pragma unroll
-        for (int i = 0; i < S_DROWS; ++i) {
-            const uint32_t d4 = __vabsdiffu4(cs[i], rrow[i * S_RWORDS]) & cmk[i];
-            dlo[i] = __byte_perm(d4, 0u, 0x4240);
-            dhi[i] = __byte_perm(d4, 0u, 0x4341);
-            lo = imad(dlo[i], one, lo);
-            hi = imad(dhi[i], one, hi);
-            if (i >= 9) {
-                lo = imad(dlo[i - 9], m1, lo);
-                hi = imad(dhi[i - 9], m1, hi);
+    // the candidate loop, instantiated for border CTAs (some p + v outside the frame) and for
+    // interior ones (no invalid-column or invalid-row masking at all)
+    auto candidates = [&](auto border_tag) {
+        constexpr bool BORDER = decltype(border_tag)::value;
+        for (int o = 0; o < nv; ++o) {
+            const short2 v = sm.vord[o];
+            const int vy = v.x, vx = v.y;
+            const int sh = (vx + R) & 3, q = (vx + R) >> 2;
+            const uint32_t *rrow = sm.rf[sh] + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
+            uint32_t inv02 = 0, inv13 = 0;                     // lanes of invalid columns -> 0x7fff
+            if constexpr (BORDER) {
+                const int c0 = cx + vx;
+                inv02 = ((unsigned)(c0) >= (unsigned)W ? 0x7fffu : 0u) |
+                        ((unsigned)(c0 + 2) >= (unsigned)W ? 0x7fff0000u : 0u);
+                inv13 = ((unsigned)(c0 + 1) >= (unsigned)W ? 0x7fffu : 0u) |
+                        ((unsigned)(c0 + 3) >= (unsigned)W ? 0x7fff0000u : 0u);
             }
-            if (i >= 8) {
-                const int j = i - 8;                       // output row of this window
-                const uint32_t Q = imad(hi, one, lo);      // (c0+c1, c2+c3)
-                const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
-                const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
-                const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
-                const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
-                const uint32_t A = __byte_perm(Ql, Q, 0x5432);   // (left c-2+c-1, c0+c1)
-                const uint32_t B = __byte_perm(Q, Qr, 0x5432);   // (c2+c3, right c4+c5)
-                uint32_t h02 = imad(lor, one, imad(imad(B, one, Q), one, imad(A, one, Ql)));  // (H0, H2)
-                uint32_t h13 = imad(imad(lol, m1, Qr), one, imad(lor, m1, h02));         // (H1, H3)
-                uint32_t rinv = 0;
-                if (border) {
-                    const int py = oy + j;
-                    rinv = (unsigned)(py + vy) >= (unsigned)H ? 0x7fff7fffu : 0u;
+            uint32_t lo = 0, hi = 0;                           // vertical sums, columns (0,2) (1,3)
+            uint32_t dlo[S_DROWS], dhi[S_DROWS];
+            const uint32_t o2 = (uint32_t)o * 0x00010001u;
+    #pragma unroll
+            for (int i = 0; i < S_DROWS; ++i) {
+                const uint32_t d4 = __vabsdiffu4(cs[i], rrow[i * S_RWORDS]) & cmk[i];
+                dlo[i] = __byte_perm(d4, 0u, 0x4240);
+                dhi[i] = __byte_perm(d4, 0u, 0x4341);
+                lo = imad(dlo[i], one, lo);
+                hi = imad(dhi[i], one, hi);
+                if (i >= 9) {
+                    lo = imad(dlo[i - 9], m1, lo);
+                    hi = imad(dhi[i - 9], m1, hi);
                 }
-                h02 |= inv02 | rinv;
-                h13 |= inv13 | rinv;
-                const uint32_t m02 = lane_mask(best02[j] + 0x7fff7fffu - h02);
-                const uint32_t m13 = lane_mask(best13[j] + 0x7fff7fffu - h13);
-                best02[j] = (best02[j] & ~m02) | (h02 & m02);
-                idx02[j] = (idx02[j] & ~m02) | (o2 & m02);
-                best13[j] = (best13[j] & ~m13) | (h13 & m13);
-                idx13[j] = (idx13[j] & ~m13) | (o2 & m13);
+                if (i >= 8) {
+                    const int j = i - 8;                       // output row of this window
+                    const uint32_t Q = imad(hi, one, lo);      // (c0+c1, c2+c3)
+                    const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
+                    const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
+                    const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
+                    const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
+                    const uint32_t A = __byte_perm(Ql, Q, 0x5432);   // (left c-2+c-1, c0+c1)
+                    const uint32_t B = __byte_perm(Q, Qr, 0x5432);   // (c2+c3, right c4+c5)
+                    uint32_t h02 = imad(lor, one, imad(imad(B, one, Q), one, imad(A, one, Ql)));  // (H0, H2)
+                    uint32_t h13 = imad(imad(lol, m1, Qr), one, imad(lor, m1, h02));         // (H1, H3)
+                    if constexpr (BORDER) {
+                        const uint32_t rinv = (unsigned)(oy + j + vy) >= (unsigned)H ? 0x7fff7fffu : 0u;
+                        h02 |= inv02 | rinv;
+                        h13 |= inv13 | rinv;
+                    }
+                    const uint32_t m02 = lane_mask(best02[j] + 0x7fff7fffu - h02);
+                    const uint32_t m13 = lane_mask(best13[j] + 0x7fff7fffu - h13);
+                    best02[j] = (best02[j] & ~m02) | (h02 & m02);
+                    idx02[j] = (idx02[j] & ~m02) | (o2 & m02);
+                    best13[j] = (best13[j] & ~m13) | (h13 & m13);
+                    idx13[j] = (idx13[j] & ~m13) | (o2 & m13);
+                }
             }
         }
-    }
+    };
+    if (border) candidates(std::true_type{});
+    else candidates(std::false_type{});
     if (lane == 0 || lane == 31) return;
     char2 *mv = reinterpret_cast<char2 *>(t.mv[k]);
 #pragma unroll
