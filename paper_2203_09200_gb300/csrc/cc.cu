@@ -32,6 +32,8 @@
 // current frame's copies use a row stride of 19 and a copy stride of 12 mod 16 units, and the
 // offsets are dealt to lanes (per column phase, nearest first) so that the 16 lanes of each
 // half-warp read 16 distinct bank pairs for every template word.
+#include <type_traits>
+
 #include "rfsr_internal.h"
 
 namespace rfsr {
@@ -369,29 +371,37 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
     const int ch = min(lane / 10, 2), wi = lane < 30 ? lane - 10 * ch : 9;
     const bool out = lane < 30 && wi >= 1 && wi <= 8;
     uint32_t rb0 = 0, rb1 = 0;                       // verdict bits: row j, pixel q at 4 j + q
-    for (int i = 1 + warp; i < 49; i += NW) {
-        const int ci = i <= 24 ? i - 1 : i;          // the 48 offsets d != 0
-        const int dy = frmc_offset(ci / 7), dx = frmc_offset(ci % 7);
-        box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
-            const int r = 11 * ch + j, x = 4 * (wi - 1);
-            if (!out || r >= TP) return;
-            const uint4 z = *reinterpret_cast<const uint4 *>(&sm.e0n0[r][x]);
-            const uint32_t zz[4] = {z.x, z.y, z.z, z.w};
-            const int e[4] = {(int)(h02 & 0xffffu), (int)(h13 & 0xffffu), (int)(h02 >> 16),
-                              (int)(h13 >> 16)};
-            const uint8_t *nr = &sm.nsrc[r + dy + kMaxRadius][x + dx + kMaxRadius];
-            const bool yin = inner || (unsigned)(y0 + r + dy) < (unsigned)H;
-            uint32_t bits = 0;
+    // instantiated for interior tiles (every source p + d in the frame) and for the others
+    auto candidates = [&](auto inner_tag) {
+        constexpr bool INNER = decltype(inner_tag)::value;
+        for (int i = 1 + warp; i < 49; i += NW) {
+            const int ci = i <= 24 ? i - 1 : i;      // the 48 offsets d != 0
+            const int dy = frmc_offset(ci / 7), dx = frmc_offset(ci % 7);
+            box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
+                const int r = 11 * ch + j, x = 4 * (wi - 1);
+                if (!out || r >= TP) return;
+                const uint4 z = *reinterpret_cast<const uint4 *>(&sm.e0n0[r][x]);
+                const uint32_t zz[4] = {z.x, z.y, z.z, z.w};
+                const int e[4] = {(int)(h02 & 0xffffu), (int)(h13 & 0xffffu), (int)(h02 >> 16),
+                                  (int)(h13 >> 16)};
+                const uint8_t *nr = &sm.nsrc[r + dy + kMaxRadius][x + dx + kMaxRadius];
+                uint32_t bits = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool valid = yin && (inner || (unsigned)(x0 + x + q + dx) < (unsigned)W);
-                const int c0 = (int)(zz[q] & 0xffffu), n0 = (int)(zz[q] >> 16);
-                if (valid && e[q] * n0 < c0 * (int)nr[q]) bits |= 1u << q;
-            }
-            if (j < 8) rb0 |= bits << (4 * j);
-            else rb1 |= bits << (4 * (j - 8));
-        });
-    }
+                for (int q = 0; q < 4; ++q) {
+                    bool valid = true;
+                    if constexpr (!INNER)
+                        valid = (unsigned)(y0 + r + dy) < (unsigned)H &&
+                                (unsigned)(x0 + x + q + dx) < (unsigned)W;
+                    const int c0 = (int)(zz[q] & 0xffffu), n0 = (int)(zz[q] >> 16);
+                    if (valid && e[q] * n0 < c0 * (int)nr[q]) bits |= 1u << q;
+                }
+                if (j < 8) rb0 |= bits << (4 * j);
+                else rb1 |= bits << (4 * (j - 8));
+            });
+        }
+    };
+    if (inner) candidates(std::true_type{});
+    else candidates(std::false_type{});
     if (out) {
 #pragma unroll
         for (int j = 0; j < 11; ++j) {
