@@ -78,7 +78,7 @@ __host__ __device__ constexpr int frmc_offset(int i)
 // candidate of bank b goes to round i.  A round then reads every template word in one
 // shared-memory wavefront; the centre d = 0 is lane 0 of round 0, and the nearest offsets -- the
 // likeliest to beat it when the vector is wrong -- fill round 0, so rejections end early.
-constexpr int MAXROUND = 16;                  // RMC with Rc = 9 needs 14
+constexpr int MAXROUND = 16;                  // RMC with Rc = 9 needs 12
 constexpr uint16_t NOCAND = 0xffff;
 constexpr int NORDER = 1 + kMaxRadius;        // FRMC, then RMC with Rc = 1..9
 
