@@ -303,8 +303,8 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
 // Box sums of F_d over the tile for one candidate d (T = 9).  F_d(y) = b_t(y + d) |s_t(y + d) -
 // rec(y + v)| for tile rows r0 - 4 .. r0 + rows + 3 and the 4 columns 4 wi - 4 .. 4 wi - 1 of
 // this lane (wi = 0 and 9 are the halo words), kept as vertical 9-sums in two packed 16-bit words
-// (columns 0, 2 and 1, 3); the horizontal 9-sums come from the neighbouring lanes (lane +- 1 holds
-// word wi -+ 1) as in the forward ME.  fn(j, h02, h13) receives the window sums (H0, H2) and
+// (columns 0, 2 and 1, 3); the horizontal 9-sums come from the neighbouring lanes (lanes lane - 1
+// and lane + 1 hold words wi - 1 and wi + 1) as in the forward ME.  fn(j, h02, h13) receives the window sums (H0, H2) and
 // (H1, H3) of output row r0 + j.
 template <int ROWS, typename Fn>
 __device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy, int dx, int vy,
