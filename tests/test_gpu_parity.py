@@ -207,19 +207,21 @@ def aligned_translation(H, W, seed, v, smooth=0.0, noise=0):
     return (cur * m0).astype(np.uint8), m0, [(ref, (ref * m1).astype(np.uint8), m1)]
 
 
-@pytest.mark.parametrize("mode,T,v,smooth", [
-    ("frmc", 9, (0, 0), 0.0), ("frmc", 9, (2, -2), 0.05), ("nnc_frmc", 9, (0, 0), 0.05),
-    ("nnc_frmc", 9, (2, 2), 0.0), ("frmc", 5, (0, 2), 0.0), ("frmc", 3, (2, 0), 0.0),
-    ("nnc_frmc", 1, (0, 0), 0.0), ("rmc", 9, (-2, 4), 0.05)])
-def test_shared_vector_box_checks(engine, mode, T, v, smooth):
+@pytest.mark.parametrize("mode,T,v,smooth,R", [
+    ("frmc", 9, (0, 0), 0.0, 8), ("frmc", 9, (2, -2), 0.05, 8), ("nnc_frmc", 9, (0, 0), 0.05, 8),
+    ("nnc_frmc", 9, (2, 2), 0.0, 8), ("frmc", 5, (0, 2), 0.0, 8), ("frmc", 3, (2, 0), 0.0, 8),
+    ("nnc_frmc", 1, (0, 0), 0.0, 8), ("rmc", 9, (-2, 4), 0.05, 8),
+    ("frmc", 9, (8, -8), 0.0, 9), ("nnc_frmc", 9, (-8, 6), 0.0, 8)])
+def test_shared_vector_box_checks(engine, mode, T, v, smooth, R):
     """Tiles whose checked pixels share one vector: with FRMC their checks run as box sums over
     the tile (the others, and every RMC check, per pixel); every decision must equal the
     oracle's, rejections included."""
     H, W = 96, 160
     smp, msk, hist = aligned_translation(H, W, seed=T * 10 + len(mode), v=v, smooth=smooth,
                                          noise=12 if smooth else 0)
-    got = gpu_step(engine, smp, msk, hist, cc_mode=mode, template_size=T, num_refs=1)
-    ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NAMES[mode], T=T, R=8)
+    got = gpu_step(engine, smp, msk, hist, cc_mode=mode, template_size=T, num_refs=1,
+                   search_radius=R)
+    ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NAMES[mode], T=T, R=R)
     compare(got, ref, msk, smp)
     # the box path really runs: most tiles hold >= 128 checked pixels with vector v
     dec = ref.dec[0]
@@ -496,3 +498,31 @@ def test_free_running_recursion_tracks_oracle(engine):
     for t in range(6):
         pg, pc = psnr(gpu[t], seq.frames[t]), psnr(cpu[t], seq.frames[t])
         assert abs(pg - pc) < 0.05, (t, pg, pc)
+
+
+def test_shared_vector_box_checks_batched_equal_alone(engine):
+    """The batched check kernel takes the same box-sum path: streams whose tiles share one vector,
+    stepped together on a batched engine, give the decisions, projections and reconstructions of
+    the same streams run alone."""
+    cases = [(96, 160, (2, -2), 0.0), (64, 128, (0, 0), 0.05), (128, 96, (-2, 4), 0.0)]
+    data = [aligned_translation(H, W, seed=50 + i, v=v, smooth=sm, noise=12 if sm else 0)
+            for i, (H, W, v, sm) in enumerate(cases)]
+    alone = []
+    for (H, W, _, _), (smp, msk, hist) in zip(cases, data):
+        got = gpu_step(engine, smp, msk, hist, cc_mode="nnc_frmc", num_refs=1)
+        alone.append(got)
+    with rfsr.Engine(device=0, batched=True) as beng:
+        sts = [beng.create_stream(height=H, width=W, cc_mode="nnc_frmc", num_refs=1, keep_f32=True)
+               for (H, W, _, _) in cases]
+        for st, (smp, msk, hist) in zip(sts, data):
+            st.set_history(hist)
+            st.push_frame(smp, msk)
+        beng.step()
+        for st, a, (smp, msk, hist) in zip(sts, alone, data):
+            rec, f32 = st.get_frame(timeout_ms=60000, f32=True)
+            np.testing.assert_array_equal(st.debug_get(rfsr.DBG_DECISION, 1), a["dec"][0])
+            np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PSUM), a["psum"])
+            np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PCNT), a["pcnt"])
+            np.testing.assert_array_equal(rec, a["rec"])
+            np.testing.assert_array_equal(f32, a["fsr"])
+            st.destroy()
