@@ -414,9 +414,12 @@ def run_unloaded_latency(rfsr, torch, frames=12):
     return out
 
 
-def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=5, memory_budget=0):
+def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=5, memory_budget=0,
+                pace_fps=0.0):
     """Poisson arrivals on a serving engine, closed loop with <= 2 frames in flight per stream:
-    per-frame latency (push returned -> result collected) and aggregate throughput."""
+    per-frame latency (push returned -> result collected) and aggregate throughput.  pace_fps > 0
+    paces every stream: frame n is pushed no earlier than n / pace_fps after the stream's
+    arrival (a camera), still with <= 2 frames in flight."""
     import time as _t
     arr = synth.config5_arrivals(seed=seed, n_streams=n_streams, rate_hz=rate_hz)
     nf = [max(2, int(round(a.spec.frames * frame_scale))) for a in arr]
@@ -453,7 +456,7 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             st = eng.create_stream(allow_queued=True, height=sp.H, width=sp.W,
                                    mask_type=sp.mask_type)
             if st.live:
-                active[nxt] = [st, 0, []]
+                active[nxt] = [st, 0, [], _t.perf_counter()]
             else:
                 queued.append((nxt, st))
                 n_queued += 1
@@ -461,11 +464,12 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             nxt += 1
         for q in list(queued):
             if q[1].live:
-                active[q[0]] = [q[1], 0, []]
+                active[q[0]] = [q[1], 0, [], _t.perf_counter()]
                 queued.remove(q)
         for i in list(active):
-            st, sent, inflight = active[i]
-            if sent < nf[i] and len(inflight) < 2:
+            st, sent, inflight, t0 = active[i]
+            due = pace_fps <= 0 or _t.perf_counter() - t0 >= sent / pace_fps
+            if sent < nf[i] and len(inflight) < 2 and due:
                 k = sent % 8
                 st.push_frame(samples[i][k], masks[i][k % len(masks[i])])
                 inflight.append(_t.perf_counter())
@@ -485,6 +489,8 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
     wall = _t.perf_counter() - t_start
     eng.destroy()
     lat_ms = np.array(lat) * 1e3
+    loop = (f"each stream paced at {pace_fps:g} fps" if pace_fps > 0 else "closed loop") + \
+        " with <= 2 frames in flight per stream"
     return {"p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
             "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
             "mpix_s": round(done_px / wall / 1e6, 3), "frames": int(len(lat)),
@@ -493,9 +499,8 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             "streams_queued": n_queued, "max_queue": max_queue,
             "workload": (f"{n_streams} streams arriving Poisson at {rate_hz:g}/s, sizes "
                          "320x240..3840x2160, fixed or dynamic mask 50/50, 1/f^2 texture + "
-                         f"moving objects, frames U{{30..300}} x {frame_scale:g}, closed loop "
-                         "with <= 2 frames in flight per stream, host buffers, serving engine "
-                         "(continuous batching, memory admission)")}
+                         f"moving objects, frames U{{30..300}} x {frame_scale:g}, {loop}, host "
+                         "buffers, serving engine (continuous batching, memory admission)")}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -693,6 +698,7 @@ def run_ours(args, rank, world, local_rank):
             rfsr, torch, small_streams(), what="256 streams of 320x240, half fixed / half dynamic masks")
         serving = run_serving(rfsr, torch)
         serving["budget_2gb"] = run_serving(rfsr, torch, memory_budget=2 << 30)
+        serving["paced_30fps"] = run_serving(rfsr, torch, n_streams=64, rate_hz=5.0, pace_fps=30.0)
         serving["unloaded"] = run_unloaded_latency(rfsr, torch)
         check_modes = run_check_modes(rfsr, torch)
         concealed = run_concealed(rfsr, torch)
