@@ -122,10 +122,19 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+
+    def wait_first(self, timeout_s: float = 5.0):
+        """Block until nvidia-smi has written its first sample (or timeout_s passed), so that
+        the samples cover the timed region from its start."""
+        t0 = time.perf_counter()
+        while self.p is not None and time.perf_counter() - t0 < timeout_s:
+            if os.path.getsize(self.f.name) > 0 or self.p.poll() is not None:
+                return
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:
@@ -635,6 +644,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(gpu_id_for(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.wait_first()
     launches0 = rfsr.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -654,7 +665,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = rfsr.kernel_launches() - launches0
-    clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_s = max_over_ranks(sum(step_ms) / 1e3, world)
     if world > 1:
@@ -688,6 +698,7 @@ def run_ours(args, rank, world, local_rank):
         st2.get_frame(timeout_ms=120000)
     torch.cuda.synchronize()
     e_s = max_over_ranks(time.perf_counter() - e0, world)
+    clocks = sampler.stop() if sampler else None    # sampled over both timed regions
     e2e = job_rate(args.steps, world, HW, e_s)
     eng.destroy()
     del d_smp, d_msk, flush
