@@ -846,7 +846,7 @@ def run_ncu_case(args):
     print(f"ncu case {args.ncu_case}: {nf} frames done", flush=True)
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -865,6 +865,11 @@ def main():
                     help="print the reconstruction-quality table (PSNR / SSIM per method) and exit")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print the per-kernel table of an ncu launch list and exit")
+    return ap
+
+
+def main():
+    ap = build_parser()
     args = ap.parse_args()
     if args.summarize_launches:
         print(summarize_launches(args.summarize_launches))
