@@ -144,6 +144,11 @@ typedef struct {
                               blocks then run as wavefronts (block (i, j) after (i-1, j+4) and
                               (i, j-1)), one launch per wave, far slower.  Unbatched engines only
                               (EINVAL on batched ones); rfsr_fsr_device then needs d_out_f32.    */
+    int fsr_trace;         /* 1: record, for every 4x4 block of every frame, the basis pair the FSR
+                              selected in each iteration (debug plane RFSR_DBG_FSR_SEL): the
+                              selection is an argmax, so this makes the FP32 result checkable
+                              against an FP64 replay of the same selections.  Costs
+                              2 * iterations bytes per block of device memory.  0 (default): off */
 } rfsr_stream_config;
 
 /* Fill a config with the defaults above (1280x720, NNC_FRMC, K=3, T=9, R=8). */
@@ -251,9 +256,17 @@ int rfsr_set_history(rfsr_stream *s, int nrefs, const uint8_t *const *rec,
  *   RFSR_DBG_PSUM      projection sums, H*W uint16;  RFSR_DBG_PCNT counts, H*W uint8
  *   RFSR_DBG_FSR       FSR output, H*W float;        RFSR_DBG_REC reconstruction, H*W uint8
  *   RFSR_DBG_RMV       k: reverse ME field at every past-frame pixel (RME mode only)
- * Errors: ESTATE (no frame done yet or k > K_eff of that frame), EINVAL. */
+ *   RFSR_DBG_FSR_SEL   FSR selections (streams with fsr_trace = 1): nblocks * fsr_iterations
+ *                      uint16, block-major over the row-major 4x4 blocks (ceil(H/4) x ceil(W/4));
+ *                      entry i of a block is the canonical linear index k*32 + l of the basis
+ *                      pair selected in iteration i (Sec. 2.1: one pair per iteration), or
+ *                      RFSR_FSR_SEL_NONE where the block ran no iteration i (W(0) = 0 or the
+ *                      residual was exhausted)
+ * Errors: ESTATE (no frame done yet, k > K_eff of that frame, plane not recorded), EINVAL. */
 enum { RFSR_DBG_MV = 0, RFSR_DBG_FMV = 1, RFSR_DBG_DECISION = 2, RFSR_DBG_PSUM = 3,
-       RFSR_DBG_PCNT = 4, RFSR_DBG_FSR = 5, RFSR_DBG_REC = 6, RFSR_DBG_RMV = 7 };
+       RFSR_DBG_PCNT = 4, RFSR_DBG_FSR = 5, RFSR_DBG_REC = 6, RFSR_DBG_RMV = 7,
+       RFSR_DBG_FSR_SEL = 8 };
+#define RFSR_FSR_SEL_NONE 0xffffu
 int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst);
 
 /* ---- stand-alone FSR (Sec. 2.1, 3.2) on device buffers ---------------------------------- */
@@ -267,6 +280,17 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst);
 int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
                     const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
                     uint8_t *d_out_u8, void *cuda_stream);
+
+/* As rfsr_fsr_device, and also records the selected basis pair of every iteration of every block
+ * in d_sel (device, nblocks * cfg->fsr_iterations uint16, 2-byte aligned; layout and
+ * RFSR_FSR_SEL_NONE as for RFSR_DBG_FSR_SEL).  The model update of Sec. 2.1 depends on the
+ * selections only, so an FP64 evaluation that follows the same selections reproduces the FP32
+ * output to rounding; this is how FP32 results at near-tied selections are checked.  Same errors
+ * as rfsr_fsr_device (EINVAL also for a NULL or misaligned d_sel). */
+int rfsr_fsr_device_trace(const rfsr_stream_config *cfg, const uint8_t *d_smp,
+                          const uint8_t *d_msk, const uint16_t *d_psum, const uint8_t *d_pcnt,
+                          float *d_out_f32, uint8_t *d_out_u8, uint16_t *d_sel,
+                          void *cuda_stream);
 
 /* ---- stream state: checkpoint / resume and migration between engines -------------------- */
 /* (No counterpart in the paper: serving infrastructure.)  The recursion state of a stream is
@@ -286,7 +310,7 @@ typedef struct {
     int64_t frames;              /* frames the exported stream had processed                       */
 } rfsr_state_header;
 #define RFSR_STATE_MAGIC 0x54534652u   /* "RFST" */
-#define RFSR_STATE_VERSION 2u
+#define RFSR_STATE_VERSION 3u
 
 /* Export s into buf (cap bytes); *bytes receives the size needed (buf == NULL: size query).
  * Taken between frames: every pushed frame must have been collected.

@@ -85,6 +85,12 @@ class FsrParams:
                           int(self.overwrite_projected))
 
 
+class _Replay(C.Structure):
+    _fields_ = [("iterations_run", C.c_int), ("divergences", C.c_int), ("first_div", C.c_int),
+                ("invalid", C.c_int), ("first_gap", C.c_double), ("max_gap", C.c_double),
+                ("max_scale", C.c_double), ("max_excess", C.c_double)]
+
+
 def _load():
     omp = _threads > 1
     lib = _libs.get(omp)
@@ -107,15 +113,16 @@ def _load():
         lib.orc_cc_pixel.argtypes = [I, I, I, I, u8p, u8p, u8p, u8p, u8p, I, I, I, I, i8p, i8p,
                                      ip]
         lib.orc_cc_pixel.restype = I
+        rp = C.POINTER(_Replay)
         lib.orc_fsr_block_ex.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I, I,
-                                         dp, dp, dp, dp, dp, dp, ip, dp]
-        lib.orc_fsr_block_alt.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, I,
-                                          I, dp, dp, dp, dp, dp, dp, ip, dp, dp, I]
-        lib.orc_fsr_block_conc.argtypes = [C.POINTER(_FsrParams), C.c_double, dp, u8p, u8p,
-                                           u16p, u8p, I, I, I, I, dp, dp, dp, I]
+                                         dp, dp, dp, dp, dp, dp, ip, dp, dp]
+        lib.orc_fsr_block_replay.argtypes = [C.POINTER(_FsrParams), C.c_double, dp, u8p, u8p,
+                                             u16p, u8p, I, I, I, I, u16p, dp, dp, ip, dp, dp, rp]
         lib.orc_fsr_frame.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I, dp, dp]
+        lib.orc_fsr_frame_replay.argtypes = [C.POINTER(_FsrParams), u8p, u8p, u16p, u8p, I, I,
+                                             u16p, dp, dp, dp, rp]
         lib.orc_fsr_frame_concealed.argtypes = [C.POINTER(_FsrParams), C.c_double, u8p, u8p, u16p,
-                                                u8p, I, I, dp, dp]
+                                                u8p, I, I, u16p, dp, dp, dp, rp]
         lib.orc_fsr_support.argtypes = [C.POINTER(_FsrParams), C.c_double, dp, u8p, u8p, u16p, u8p,
                                         I, I, I, I, dp, dp]
         lib.orc_quantize.argtypes = [dp, u8p, u8p, I, I, u8p]
@@ -271,9 +278,8 @@ class FsrTrace:
     gaps: np.ndarray         # (iterations,) relative best / second-best gap per iteration
 
 
-def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx, second_at: int = -1) -> FsrTrace:
-    """FSR of block (by, bx).  second_at >= 0 resolves the selection at that iteration the other
-    way (second best bin): the alternative continuation at a near tie."""
+def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx) -> FsrTrace:
+    """FSR of block (by, bx) along its own argmax, with every trace."""
     lib = _load()
     smp, msk = _u8(smp), _u8(msk)
     H, W = smp.shape
@@ -287,39 +293,78 @@ def fsr_block(params: FsrParams, smp, msk, psum, pcnt, by, bx, second_at: int = 
     gaps = np.zeros(max(1, params.iterations))
     gap = C.c_double()
     cp = params._c()
-    lib.orc_fsr_block_alt(C.byref(cp), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
-                          _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, by, bx,
-                          _p(out, C.c_double), _p(w, C.c_double), _p(f, C.c_double),
-                          _p(g, C.c_double), _p(rre, C.c_double), _p(rim, C.c_double),
-                          sel.ctypes.data_as(C.POINTER(C.c_int)), C.byref(gap),
-                          _p(gaps, C.c_double), int(second_at))
+    lib.orc_fsr_block_ex(C.byref(cp), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
+                         _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, by, bx,
+                         _p(out, C.c_double), _p(w, C.c_double), _p(f, C.c_double),
+                         _p(g, C.c_double), _p(rre, C.c_double), _p(rim, C.c_double),
+                         sel.ctypes.data_as(C.POINTER(C.c_int)), C.byref(gap),
+                         _p(gaps, C.c_double))
     return FsrTrace(out, w, f, g, rre + 1j * rim, sel[:params.iterations], gap.value,
                     gaps[:params.iterations])
 
 
-def fsr_block_valid(params: FsrParams, smp, msk, psum, pcnt, by, bx, got, tol: float = 1e-4,
-                    near: float = 1e-3, tries: int = 12):
-    """Is ``got`` (B x B) a result of the method for this block?  Either within ``tol`` of the
-    argmax continuation, or -- where the selection had a near tie (relative gap < ``near``) --
-    within ``tol`` of the continuation that resolves one of those near ties the other way.
-    Returns (ok, error of the plain continuation, iteration used or -1)."""
-    tr = fsr_block(params, smp, msk, psum, pcnt, by, bx)
-    e0 = float(np.abs(np.asarray(got, np.float64) - tr.out).max())
-    if e0 <= tol:
-        return True, e0, -1
-    order = [int(i) for i in np.argsort(tr.gaps) if tr.gaps[i] < near][:tries]
-    for i in order:
-        alt = fsr_block(params, smp, msk, psum, pcnt, by, bx, second_at=i)
-        if float(np.abs(np.asarray(got, np.float64) - alt.out).max()) <= tol:
-            return True, e0, i
-    return False, e0, -1
+@dataclasses.dataclass
+class Replay:
+    """Where a followed selection sequence left this evaluation's own argmax (Sec. 2.1 selects
+    one basis pair per iteration): counts, first iteration, and the criterion's relative shortfall
+    (best - followed) / best there and at worst; invalid: a followed index is no canonical bin;
+    max_scale: 2 S / |R(best)| at the worst divergence, S the magnitude the rounding of the
+    residual's arithmetic scales with (largest initial |R| plus the updates made so far);
+    max_excess: the largest gap / (bound_q + bound_u * 2 S / |R(best)|) over all divergences, for
+    the bound (bound_q, bound_u) given to the replay (0 without one)."""
+    iterations_run: int
+    divergences: int
+    first_div: int
+    invalid: bool
+    first_gap: float
+    max_gap: float
+    max_scale: float
+    max_excess: float
 
 
-def fsr_block_concealed(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by, bx,
-                        second_at: int = -1):
+def _replay(r: _Replay) -> Replay:
+    return Replay(r.iterations_run, r.divergences, r.first_div, bool(r.invalid), r.first_gap,
+                  r.max_gap, r.max_scale, r.max_excess)
+
+
+def _bound(bound):
+    return None if bound is None else np.ascontiguousarray(bound, np.float64).reshape(2)
+
+
+def _sel(sel, nblocks: int, iters: int) -> np.ndarray:
+    sel = np.ascontiguousarray(sel, np.uint16).reshape(-1)
+    assert sel.size == nblocks * max(1, iters), (sel.size, nblocks, iters)
+    return sel
+
+
+def fsr_block_replay(params: FsrParams, smp, msk, psum, pcnt, by, bx, sel, delta: float = 0.0,
+                     conc=None, bound=None):
+    """FSR of block (by, bx) following the selection sequence sel (``iterations`` uint16 entries,
+    0xFFFF = no further iteration) instead of its own argmax, with concealed weighting delta and
+    concealed values conc; bound = (bound_q, bound_u) for Replay.max_excess.  Returns (B x B
+    output, Replay)."""
+    lib = _load()
+    smp, msk = _u8(smp), _u8(msk)
+    H, W = smp.shape
+    psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
+    pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
+    conc = None if conc is None else np.ascontiguousarray(conc, np.float64)
+    sel = _sel(sel, 1, params.iterations)
+    bound = _bound(bound)
+    out = np.zeros((params.B, params.B))
+    r = _Replay()
+    lib.orc_fsr_block_replay(C.byref(params._c()), float(delta), _p(conc, C.c_double),
+                             _p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(psum, C.c_uint16),
+                             _p(pcnt, C.c_uint8), H, W, by, bx, _p(sel, C.c_uint16),
+                             _p(bound, C.c_double), _p(out, C.c_double), None, None, None,
+                             C.byref(r))
+    return out, _replay(r)
+
+
+def fsr_block_concealed(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by, bx):
     """FSR of block (by, bx) with concealed weighting delta, the pixels of the blocks before it in
     raster order taking their values from conc (H x W).  Returns (B x B output, min gap, gaps per
-    iteration); second_at as in fsr_block."""
+    iteration)."""
     lib = _load()
     smp, msk = _u8(smp), _u8(msk)
     H, W = smp.shape
@@ -329,26 +374,11 @@ def fsr_block_concealed(params: FsrParams, delta: float, conc, smp, msk, psum, p
     out = np.zeros((params.B, params.B))
     gaps = np.zeros(max(1, params.iterations))
     gap = C.c_double()
-    lib.orc_fsr_block_conc(C.byref(params._c()), float(delta), _p(conc, C.c_double),
-                           _p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(psum, C.c_uint16),
-                           _p(pcnt, C.c_uint8), H, W, by, bx, _p(out, C.c_double), C.byref(gap),
-                           _p(gaps, C.c_double), int(second_at))
+    lib.orc_fsr_block_replay(C.byref(params._c()), float(delta), _p(conc, C.c_double),
+                             _p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(psum, C.c_uint16),
+                             _p(pcnt, C.c_uint8), H, W, by, bx, None, None, _p(out, C.c_double),
+                             None, C.byref(gap), _p(gaps, C.c_double), None)
     return out, gap.value, gaps[:params.iterations]
-
-
-def fsr_block_concealed_valid(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by,
-                              bx, got, tol: float = 1e-4, near: float = 1e-3, tries: int = 12):
-    """fsr_block_valid for concealed weighting delta with concealed values conc."""
-    out, _, gaps = fsr_block_concealed(params, delta, conc, smp, msk, psum, pcnt, by, bx)
-    e0 = float(np.abs(np.asarray(got, np.float64) - out).max())
-    if e0 <= tol:
-        return True, e0, -1
-    for i in [int(i) for i in np.argsort(gaps) if gaps[i] < near][:tries]:
-        alt, _, _ = fsr_block_concealed(params, delta, conc, smp, msk, psum, pcnt, by, bx,
-                                        second_at=i)
-        if float(np.abs(np.asarray(got, np.float64) - alt).max()) <= tol:
-            return True, e0, i
-    return False, e0, -1
 
 
 def fsr_frame(params: FsrParams, smp, msk, psum=None, pcnt=None):
@@ -367,22 +397,65 @@ def fsr_frame(params: FsrParams, smp, msk, psum=None, pcnt=None):
     return out, gap
 
 
-def fsr_frame_concealed(params: FsrParams, delta: float, smp, msk, psum=None, pcnt=None):
+def _replay_arrays(reps) -> dict:
+    return {"iterations_run": np.array([r.iterations_run for r in reps], np.int32),
+            "divergences": np.array([r.divergences for r in reps], np.int32),
+            "first_div": np.array([r.first_div for r in reps], np.int32),
+            "invalid": np.array([r.invalid for r in reps], bool),
+            "first_gap": np.array([r.first_gap for r in reps]),
+            "max_gap": np.array([r.max_gap for r in reps]),
+            "max_scale": np.array([r.max_scale for r in reps]),
+            "max_excess": np.array([r.max_excess for r in reps])}
+
+
+def fsr_frame_replay(params: FsrParams, smp, msk, psum, pcnt, sel, bound=None):
+    """FSR of every block following the selection sequences sel (nblocks x iterations uint16,
+    block-major over the row-major blocks, 0xFFFF = no further iteration).  Returns (H x W
+    output, dict of per-block arrays: iterations_run, divergences, first_div, invalid, first_gap,
+    max_gap, max_scale, max_excess -- see Replay; bound as in fsr_block_replay)."""
+    lib = _load()
+    smp, msk = _u8(smp), _u8(msk)
+    H, W = smp.shape
+    psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
+    pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
+    nby, nbx = -(-H // params.B), -(-W // params.B)
+    sel = _sel(sel, nby * nbx, params.iterations)
+    bound = _bound(bound)
+    out = np.zeros((H, W))
+    reps = (_Replay * (nby * nbx))()
+    lib.orc_fsr_frame_replay(C.byref(params._c()), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
+                             _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W, _p(sel, C.c_uint16),
+                             _p(bound, C.c_double), _p(out, C.c_double), None, reps)
+    return out, _replay_arrays(reps)
+
+
+def fsr_frame_concealed(params: FsrParams, delta: float, smp, msk, psum=None, pcnt=None, sel=None,
+                        bound=None):
     """FSR of every block in raster order with concealed weighting delta (the original FSR: the
     pixels of earlier blocks that are neither measured nor projected join the support with weight
-    delta rho^d); delta = 0 equals fsr_frame.  Returns (H x W output, per-block min gap)."""
+    delta rho^d); delta = 0 equals fsr_frame.  Returns (H x W output, per-block min gap); with sel
+    (nblocks x iterations, as in fsr_frame_replay) every block follows its selection sequence and
+    a third element holds the per-block replay arrays."""
     lib = _load()
     smp, msk = _u8(smp), _u8(msk)
     H, W = smp.shape
     psum = None if psum is None else np.ascontiguousarray(psum, np.uint16)
     pcnt = None if pcnt is None else np.ascontiguousarray(pcnt, np.uint8)
     out = np.zeros((H, W))
-    gap = np.zeros((-(-H // params.B), -(-W // params.B)))
+    nby, nbx = -(-H // params.B), -(-W // params.B)
+    gap = np.zeros((nby, nbx))
     cp = params._c()
+    if sel is not None:
+        sel = _sel(sel, nby * nbx, params.iterations)
+    reps = (_Replay * (nby * nbx))() if sel is not None else None
+    bound = _bound(bound)
     lib.orc_fsr_frame_concealed(C.byref(cp), float(delta), _p(smp, C.c_uint8), _p(msk, C.c_uint8),
                                 _p(psum, C.c_uint16), _p(pcnt, C.c_uint8), H, W,
-                                _p(out, C.c_double), _p(gap, C.c_double))
-    return out, gap
+                                _p(sel, C.c_uint16), _p(bound, C.c_double), _p(out, C.c_double),
+                                _p(gap, C.c_double), reps)
+    if sel is None:
+        return out, gap
+    return out, gap, _replay_arrays(reps)
 
 
 def fsr_support(params: FsrParams, delta: float, conc, smp, msk, psum, pcnt, by, bx):

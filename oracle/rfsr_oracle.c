@@ -512,18 +512,38 @@ static void fsr_support(const orc_fsr_params *P, double delta, const double *con
         }
 }
 
+/* Outcome of a replay (fsr_block_core with a followed selection sequence). */
+typedef struct {
+    int iterations_run;   /* iterations taken; the followed sequence may end early (0xffff)      */
+    int divergences;      /* iterations whose followed pair is not this evaluation's argmax      */
+    int first_div;        /* the first such iteration, -1 if none                                 */
+    int invalid;          /* 1: a followed index is not the canonical member of a pair          */
+    double first_gap;     /* (best - followed) / best criterion at the first divergence          */
+    double max_gap;       /* the largest such relative gap over all divergences (0 if none)      */
+    double max_scale;     /* at that divergence: 2 S / |R(best)|, S = max_k |R_0(k)| plus
+                             2 gamma sum_j |R(u_j)| over the earlier iterations -- the magnitude
+                             that the rounding of the residual's arithmetic scales with          */
+    double max_excess;    /* max over divergences of gap / (bound_q + bound_u * 2 S / |R(best)|),
+                             for a caller-given bound of that form (0 if none is given)          */
+} orc_fsr_replay;
+
+#define ORC_SEL_NONE 0xffffu   /* a followed entry meaning "no further iteration" */
+
 /* Extended form for tests: besides the B*B block output it can return the support weights and
  * values, the model g over the whole support, the final residual spectrum, the selected bins, the
  * relative gap between the best and second best selection criterion at every iteration and their
- * minimum.  A near tie (tiny gap) means that another rounding of the same arithmetic may select
- * the other bin; both continuations are results of the method.  second_at >= 0 takes the second
- * best bin at that one iteration (the other resolution of a near tie); -1 = plain argmax. */
+ * minimum.
+ * Replay: with follow != NULL, iteration i updates the model with the pair follow[i] instead of
+ * its own argmax (and stops at the first ORC_SEL_NONE).  Sec. 2.1's update is a function of the
+ * selected pair, so following the selections another evaluation of the same method made (an FP32
+ * one, say) gives that evaluation's result up to its rounding; rep records where and by how much
+ * the followed pair's criterion fell short of this evaluation's maximum. */
 static void fsr_block_core(const orc_fsr_params *P, double delta, const double *conc,
                            const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
                            const uint8_t *pcnt, int H, int W, int by, int bx, double *out,
                            double *w_out, double *f_out, double *g_out, double *rre_out,
                            double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
-                           int second_at)
+                           const uint16_t *follow, const double *bound, orc_fsr_replay *rep)
 {
     const int N = P->N, B = P->B, o = (P->N - P->B) / 2;
     static _Thread_local double w[ORC_NMAX * ORC_NMAX], f[ORC_NMAX * ORC_NMAX];
@@ -544,6 +564,12 @@ static void fsr_block_core(const orc_fsr_params *P, double delta, const double *
 
     double min_gap = INFINITY;
     const double W0 = Wre[0];
+    orc_fsr_replay rp = {0, 0, -1, 0, 0.0, 0.0, 0.0, 0.0};
+    double scale = 0.0;                       /* S of orc_fsr_replay */
+    for (int i = 0; i < N * N; ++i) {
+        double a = sqrt(Rre[i] * Rre[i] + Rim[i] * Rim[i]);
+        if (a > scale) scale = a;
+    }
     for (int it = 0; it < P->iterations && W0 > 0.0; ++it) {
         int best = -1, best2 = -1;
         double bv = -1.0, second = -1.0;
@@ -558,7 +584,35 @@ static void fsr_block_core(const orc_fsr_params *P, double delta, const double *
         double gap = (bv > 0.0 && second >= 0.0) ? (bv - second) / bv : INFINITY;
         if (gap < min_gap) min_gap = gap;
         if (gaps_out) gaps_out[it] = gap;
-        if (it == second_at && best2 >= 0) best = best2;
+        (void)best2;
+        if (follow) {
+            unsigned fl = follow[it];
+            if (fl == ORC_SEL_NONE) break;
+            int fk = (int)fl / N, fc = (int)fl % N;
+            if ((int)fl >= N * N || (int)fl > ((N - fk) % N) * N + (N - fc) % N) {
+                rp.invalid = 1;
+                break;
+            }
+            if ((int)fl != best) {
+                double ef = wf[fl] * (Rre[fl] * Rre[fl] + Rim[fl] * Rim[fl]);
+                double g = bv > 0.0 ? (bv - ef) / bv : 0.0;
+                double rb = sqrt(Rre[best] * Rre[best] + Rim[best] * Rim[best]);
+                if (rp.divergences == 0) { rp.first_div = it; rp.first_gap = g; }
+                double sc = rb > 0.0 ? 2.0 * scale / rb : INFINITY;
+                if (g > rp.max_gap) {
+                    rp.max_gap = g;
+                    rp.max_scale = sc;
+                }
+                if (bound) {
+                    double x = g / (bound[0] + bound[1] * sc);
+                    if (x > rp.max_excess) rp.max_excess = x;
+                }
+                rp.divergences++;
+            }
+            best = (int)fl;
+        }
+        scale += 2.0 * P->gamma * sqrt(Rre[best] * Rre[best] + Rim[best] * Rim[best]);
+        rp.iterations_run = it + 1;
         int uk = best / N, ul = best % N;
         int self = (((N - uk) % N) == uk) && (((N - ul) % N) == ul);
         double dre = P->gamma * Rre[best] / W0, dim = P->gamma * Rim[best] / W0;
@@ -604,50 +658,50 @@ static void fsr_block_core(const orc_fsr_params *P, double delta, const double *
     if (rre_out) memcpy(rre_out, Rre, sizeof(double) * N * N);
     if (rim_out) memcpy(rim_out, Rim, sizeof(double) * N * N);
     if (min_gap_out) *min_gap_out = min_gap;
+    if (rep) *rep = rp;
 }
 
-void orc_fsr_block_alt(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
-                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
-                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
-                       double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out,
-                       int second_at)
-{
-    fsr_block_core(P, 0.0, NULL, smp, msk, psum, pcnt, H, W, by, bx, out, w_out, f_out, g_out,
-                   rre_out, rim_out, sel_out, min_gap_out, gaps_out, second_at);
-}
-
-/* orc_fsr_block_alt with concealed weighting delta and concealed values conc (H x W; the
- * reconstruction of the blocks before (by, bx) in raster order), for the tests. */
-void orc_fsr_block_conc(const orc_fsr_params *P, double delta, const double *conc,
-                        const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
-                        const uint8_t *pcnt, int H, int W, int by, int bx, double *out,
-                        double *min_gap_out, double *gaps_out, int second_at)
-{
-    fsr_block_core(P, delta, conc, smp, msk, psum, pcnt, H, W, by, bx, out, 0, 0, 0, 0, 0, 0,
-                   min_gap_out, gaps_out, second_at);
-}
-
+/* One block with every trace (support, model, final residual, selections, gaps), for the tests. */
 void orc_fsr_block_ex(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
                       const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
                       double *out, double *w_out, double *f_out, double *g_out, double *rre_out,
-                      double *rim_out, int *sel_out, double *min_gap_out)
+                      double *rim_out, int *sel_out, double *min_gap_out, double *gaps_out)
 {
-    orc_fsr_block_alt(P, smp, msk, psum, pcnt, H, W, by, bx, out, w_out, f_out, g_out, rre_out,
-                      rim_out, sel_out, min_gap_out, 0, -1);
+    fsr_block_core(P, 0.0, NULL, smp, msk, psum, pcnt, H, W, by, bx, out, w_out, f_out, g_out,
+                   rre_out, rim_out, sel_out, min_gap_out, gaps_out, NULL, NULL, NULL);
+}
+
+/* One block with concealed weighting delta and concealed values conc (H x W, may be NULL for
+ * delta = 0), along its own argmax (follow = NULL) or along the selection sequence
+ * follow[0 .. iterations) (replay, see fsr_block_core); sel_out, min_gap_out, gaps_out and rep
+ * may be NULL. */
+void orc_fsr_block_replay(const orc_fsr_params *P, double delta, const double *conc,
+                          const uint8_t *smp, const uint8_t *msk, const uint16_t *psum,
+                          const uint8_t *pcnt, int H, int W, int by, int bx,
+                          const uint16_t *follow, const double *bound, double *out, int *sel_out,
+                          double *min_gap_out, double *gaps_out, orc_fsr_replay *rep)
+{
+    fsr_block_core(P, delta, conc, smp, msk, psum, pcnt, H, W, by, bx, out, 0, 0, 0, 0, 0, sel_out,
+                   min_gap_out, gaps_out, follow, bound, rep);
 }
 
 void orc_fsr_block(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
                    const uint16_t *psum, const uint8_t *pcnt, int H, int W, int by, int bx,
                    double *out, double *min_gap_out)
 {
-    orc_fsr_block_ex(P, smp, msk, psum, pcnt, H, W, by, bx, out, 0, 0, 0, 0, 0, 0, min_gap_out);
+    fsr_block_core(P, 0.0, NULL, smp, msk, psum, pcnt, H, W, by, bx, out, 0, 0, 0, 0, 0, 0,
+                   min_gap_out, 0, NULL, NULL, NULL);
 }
 
 /* Every block of the frame; out is H x W (pixels of partial edge blocks outside the frame are
- * dropped), min_gap holds one value per block (row-major over blocks). */
-void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
-                   const uint16_t *psum, const uint8_t *pcnt, int H, int W, double *out,
-                   double *min_gap)
+ * dropped), min_gap holds one value per block (row-major over blocks).  follow (may be NULL):
+ * replay every block along its selection sequence, follow[b * iterations ..] for block b; rep
+ * (may be NULL) then receives one record per block, with max_excess measured against
+ * bound = {bound_q, bound_u} (may be NULL). */
+void orc_fsr_frame_replay(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
+                          const uint16_t *psum, const uint8_t *pcnt, int H, int W,
+                          const uint16_t *follow, const double *bound, double *out,
+                          double *min_gap, orc_fsr_replay *rep)
 {
     int B = P->B, nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -655,14 +709,24 @@ void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *m
         for (int bx = 0; bx < nbx; ++bx) {
             double blk[ORC_NMAX * ORC_NMAX];
             double gap;
-            orc_fsr_block(P, smp, msk, psum, pcnt, H, W, by, bx, blk, &gap);
-            if (min_gap) min_gap[by * nbx + bx] = gap;
+            const int b = by * nbx + bx;
+            fsr_block_core(P, 0.0, NULL, smp, msk, psum, pcnt, H, W, by, bx, blk, 0, 0, 0, 0, 0, 0,
+                           &gap, 0, follow ? follow + (size_t)b * P->iterations : NULL, bound,
+                           rep ? rep + b : NULL);
+            if (min_gap) min_gap[b] = gap;
             for (int m = 0; m < B; ++m)
                 for (int n = 0; n < B; ++n) {
                     int y = B * by + m, x = B * bx + n;
                     if (inside(y, x, H, W)) out[(size_t)y * W + x] = blk[m * B + n];
                 }
         }
+}
+
+void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *msk,
+                   const uint16_t *psum, const uint8_t *pcnt, int H, int W, double *out,
+                   double *min_gap)
+{
+    orc_fsr_frame_replay(P, smp, msk, psum, pcnt, H, W, NULL, NULL, out, min_gap, NULL);
 }
 
 /* FSR of every block with concealed weighting delta (the original FSR; the paper uses delta = 0,
@@ -672,7 +736,8 @@ void orc_fsr_frame(const orc_fsr_params *P, const uint8_t *smp, const uint8_t *m
  * result for delta = 0 equals orc_fsr_frame. */
 void orc_fsr_frame_concealed(const orc_fsr_params *P, double delta, const uint8_t *smp,
                              const uint8_t *msk, const uint16_t *psum, const uint8_t *pcnt, int H,
-                             int W, double *out, double *min_gap)
+                             int W, const uint16_t *follow, const double *bound, double *out,
+                             double *min_gap, orc_fsr_replay *rep)
 {
     int B = P->B, nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
     memset(out, 0, sizeof(double) * (size_t)H * W);
@@ -680,9 +745,11 @@ void orc_fsr_frame_concealed(const orc_fsr_params *P, double delta, const uint8_
         for (int bx = 0; bx < nbx; ++bx) {
             double blk[ORC_NMAX * ORC_NMAX];
             double gap;
+            const int b = by * nbx + bx;
             fsr_block_core(P, delta, out, smp, msk, psum, pcnt, H, W, by, bx, blk, 0, 0, 0, 0, 0, 0,
-                           &gap, 0, -1);
-            if (min_gap) min_gap[by * nbx + bx] = gap;
+                           &gap, 0, follow ? follow + (size_t)b * P->iterations : NULL, bound,
+                           rep ? rep + b : NULL);
+            if (min_gap) min_gap[b] = gap;
             for (int m = 0; m < B; ++m)
                 for (int n = 0; n < B; ++n) {
                     int y = B * by + m, x = B * bx + n;

@@ -32,6 +32,7 @@
 // current frame's copies use a row stride of 19 and a copy stride of 12 mod 16 units, and the
 // offsets are dealt to lanes (per column phase, nearest first) so that the 16 lanes of each
 // half-warp read 16 distinct bank pairs for every template word.
+#include <atomic>
 #include <type_traits>
 
 #include "rfsr_internal.h"
@@ -745,20 +746,25 @@ __global__ void __launch_bounds__(NT) rme_batched_kernel(BatchDesc *bd)
 
 int g_order_ready[64];
 
+// The dynamic shared-memory limit of a kernel is a per-device attribute: set it once on every
+// device the kernel is launched on (done[d] per device ordinal d).
 template <typename K>
-cudaError_t set_smem(K kernel, bool &done)
+cudaError_t set_smem(K kernel, std::atomic<bool> (&done)[64])
 {
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
-    if (e == cudaSuccess) done = true;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev].load()) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    if (e == cudaSuccess) done[dev].store(true);
     return e;
 }
 
 template <int T>
 cudaError_t launch_cc_t(const FrameTask &t, cudaStream_t st)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr[64];
     cudaError_t e = set_smem(cc_project_kernel<T>, attr);
     if (e != cudaSuccess) return e;
     dim3 grid((t.W + TP - 1) / TP, (t.H + TP - 1) / TP);
@@ -769,7 +775,7 @@ cudaError_t launch_cc_t(const FrameTask &t, cudaStream_t st)
 template <int T>
 cudaError_t launch_cc_batched_t(BatchDesc *bd, cudaStream_t st)
 {
-    static bool attr = false;
+    static std::atomic<bool> attr[64];
     cudaError_t e = set_smem(cc_batched_kernel<T>, attr);
     if (e != cudaSuccess) return e;
     static const int grid = persistent_grid(cc_batched_kernel<T>, NT, sizeof(Smem));

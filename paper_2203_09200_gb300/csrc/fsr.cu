@@ -77,6 +77,7 @@ struct FsrArgs {
     const int *status;
     int *status_out;
     const float *conc;                     // concealed weighting: this frame's output so far
+    uint16_t *sel;                         // optional trace: selected pair per block and iteration
     int H, W, iters, overwrite;
     float gamma, mu, delta;
 };
@@ -101,6 +102,7 @@ __device__ __forceinline__ void fsr_args(FsrArgs &a, const FrameTask &t)
     a.mu = t.fsr_proj_weight;
     a.conc = t.fsr_out;
     a.delta = t.fsr_concealed;
+    a.sel = t.fsr_sel;
 }
 
 struct Twiddles {
@@ -264,7 +266,9 @@ __device__ __forceinline__ void store_pixel(const FsrArgs &a, int y, int x, floa
 }
 
 // block b of a frame, computed by one warp with its shared-memory area ws; tw holds the
-// twiddles.  Block 0 also publishes the frame's final status word.
+// twiddles.  Block 0 also publishes the frame's final status word.  TRACE: the instantiation
+// that also records the selected pair of every iteration in a.sel (when it is set).
+template <bool TRACE>
 __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, const FsrArgs &a, int b)
 {
     const int lane = threadIdx.x & 31;
@@ -362,7 +366,8 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     // g += gf (dr cos - di sin) at phase jp (gf = 1 for a self-conjugate bin, else 2)
     float gdr = 0.f, gdi = 0.f, gf = 0.f;
     int jp = 0;
-    for (int it = 0; it < iters && W0 > 0.f; ++it) {
+    int it = 0;
+    for (; it < iters && W0 > 0.f; ++it) {
         // Selection key of slot s: the bits of e = wf |R|^2 (e >= 0, so they order like e) with
         // the low 5 bits replaced by 31 - s.  The integer maximum then picks the largest e and,
         // among values equal to 2^-18 relative, the lowest slot; a max tree keeps the scan short.
@@ -385,6 +390,9 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
         // among the lanes whose value reaches the maximum, the lowest canonical index wins
         const int mykey = ((best ^ m) >> 5) == 0 ? cand : 0x7fffffff;
         const int win = __reduce_min_sync(0xffffffffu, mykey);
+        if constexpr (TRACE) {
+            if (a.sel != nullptr && lane == 0) a.sel[(size_t)b * iters + it] = (uint16_t)win;
+        }
         const int uk = win >> 5, ul = win & (N - 1);   // the canonical bin u
         // R(u) from its owner: lane uk, slot ul (ul <= 16) or lane 32 - uk, slot ul - 16; the
         // slot is the same in every lane, so one switch branch reads it
@@ -425,6 +433,10 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
         gf = self ? 1.f : 2.f;
     }
     g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
+    if constexpr (TRACE) {                             // iterations not run: no selection
+        if (a.sel != nullptr)
+            for (int j = it + lane; j < iters; j += 32) a.sel[(size_t)b * iters + j] = 0xffffu;
+    }
 
     // 5. output: D-FSR overwrite and the 8-bit reconstruction
     if (lane < kFsrB * kFsrB) store_pixel(a, kFsrB * bi + pm, kFsrB * bj + pn, g);
@@ -531,7 +543,8 @@ __device__ void fsr_block_mw(MwSmem &sm, const FsrArgs &a, int b)
     const float gscale = W0 > 0.f ? a.gamma / W0 : 0.f;
     float gdr = 0.f, gdi = 0.f, gf = 0.f;
     int jp = 0;
-    for (int it = 0; it < a.iters && W0 > 0.f; ++it) {
+    int it = 0;
+    for (; it < a.iters && W0 > 0.f; ++it) {
         uint32_t key[MWS];
 #pragma unroll
         for (int j = 0; j < MWS; ++j) {
@@ -561,6 +574,7 @@ __device__ void fsr_block_mw(MwSmem &sm, const FsrArgs &a, int b)
         for (int w = 0; w < MW; ++w)
             if (((sm.redm[w] ^ m) >> 5) == 0) win = min(win, sm.redc[w]);
         if ((m >> 5) == 0) break;                        // residual exhausted (the whole block)
+        if (a.sel != nullptr && tid == 0) a.sel[(size_t)b * a.iters + it] = (uint16_t)win;
         const int uk = win >> 5, ul = win & (N - 1);
         const int owner = ul <= N / 2 ? uk : N - uk;
         const int slot = ul <= N / 2 ? ul : ul - N / 2;
@@ -594,6 +608,8 @@ __device__ void fsr_block_mw(MwSmem &sm, const FsrArgs &a, int b)
         gf = self ? 1.f : 2.f;
     }
     g = fmaf(gf, fmaf(gdr, tw.cs[jp], -gdi * tw.sn[jp]), g);
+    if (a.sel != nullptr && warp == 0)                   // iterations not run: no selection
+        for (int j = it + lane; j < a.iters; j += 32) a.sel[(size_t)b * a.iters + j] = 0xffffu;
     // 5. output: warp 0 holds the model at the 16 block pixels
     if (warp == 0 && lane < kFsrB * kFsrB) store_pixel(a, kFsrB * bi + pm, kFsrB * bj + pn, g);
 }
@@ -608,6 +624,7 @@ __device__ __forceinline__ void load_twiddles(Twiddles &tw)
 }
 
 // single-stream launch: one CTA = WPB1 consecutive blocks, one per warp
+template <bool TRACE>
 __global__ void __launch_bounds__(WPB1 * 32, 4) fsr_kernel(FrameTask t)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -616,7 +633,7 @@ __global__ void __launch_bounds__(WPB1 * 32, 4) fsr_kernel(FrameTask t)
     const int warp = threadIdx.x >> 5;
     FsrArgs a;
     fsr_args(a, t);
-    fsr_block(sm.tw, sm.w[warp], a, blockIdx.x * WPB1 + warp);
+    fsr_block<TRACE>(sm.tw, sm.w[warp], a, blockIdx.x * WPB1 + warp);
 }
 
 // Concealed weighting > 0: block (i, j) reads the blocks before it in raster order that overlap
@@ -640,7 +657,7 @@ __global__ void __launch_bounds__(MW * 32) fsr_wave_kernel(FrameTask t, int wave
 // together on adjacent blocks and share their support rows in L1).  The next claim is issued
 // before the current tile's work so that its latency is hidden.  Each warp keeps the arguments
 // of its task in shared memory (refreshed when the task changes).
-template <int WPB>
+template <int WPB, bool TRACE>
 __global__ void __launch_bounds__(WPB * 32, 16 / WPB) fsr_batched_kernel(BatchDesc *bd)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -664,7 +681,7 @@ __global__ void __launch_bounds__(WPB * 32, 16 / WPB) fsr_batched_kernel(BatchDe
             if (lane == 0) fsr_args(sm.args[warp], bd->task[ti]);
             __syncwarp();
         }
-        fsr_block(sm.tw, sm.w[warp], sm.args[warp], (c - lo) * WPB + warp);
+        fsr_block<TRACE>(sm.tw, sm.w[warp], sm.args[warp], (c - lo) * WPB + warp);
         // slot (it+1)&1 was last read before the previous barrier, so it may be rewritten now
         if (threadIdx.x == 0) sm.tile[(it + 1) & 1] = nxt;
         __syncthreads();
@@ -695,10 +712,14 @@ cudaError_t init_fsr(int dev)
     }
     cudaError_t e = cudaMemcpyToSymbol(c_cs, cs, sizeof(cs));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sn, sn, sizeof(sn));
-    if (e == cudaSuccess) e = smem_attr(fsr_kernel, sizeof(Smem<WPB1>));
-    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2>, sizeof(Smem<2>));
-    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4>, sizeof(Smem<4>));
-    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8>, sizeof(Smem<8>));
+    if (e == cudaSuccess) e = smem_attr(fsr_kernel<false>, sizeof(Smem<WPB1>));
+    if (e == cudaSuccess) e = smem_attr(fsr_kernel<true>, sizeof(Smem<WPB1>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2, false>, sizeof(Smem<2>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4, false>, sizeof(Smem<4>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8, false>, sizeof(Smem<8>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<2, true>, sizeof(Smem<2>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<4, true>, sizeof(Smem<4>));
+    if (e == cudaSuccess) e = smem_attr(fsr_batched_kernel<8, true>, sizeof(Smem<8>));
     if (e == cudaSuccess) g_ready[dev] = 1;
     return e;
 }
@@ -710,26 +731,33 @@ int tiles_fsr(const FrameTask &t, int fsr_blocks)
 }
 
 namespace {
-template <int WPB>
+template <int WPB, bool TRACE>
 void launch_fsr_batched_t(BatchDesc *bd, cudaStream_t st)
 {
-    static const int grid = persistent_grid(fsr_batched_kernel<WPB>, WPB * 32, sizeof(Smem<WPB>));
-    fsr_batched_kernel<WPB><<<grid, WPB * 32, sizeof(Smem<WPB>), st>>>(bd);
+    static const int grid = persistent_grid(fsr_batched_kernel<WPB, TRACE>, WPB * 32, sizeof(Smem<WPB>));
+    fsr_batched_kernel<WPB, TRACE><<<grid, WPB * 32, sizeof(Smem<WPB>), st>>>(bd);
+}
+
+template <bool TRACE>
+void launch_fsr_batched_b(BatchDesc *bd, int fsr_blocks, cudaStream_t st)
+{
+    switch (fsr_blocks) {
+    case 2: launch_fsr_batched_t<2, TRACE>(bd, st); break;
+    case 8: launch_fsr_batched_t<8, TRACE>(bd, st); break;
+    default: launch_fsr_batched_t<4, TRACE>(bd, st); break;
+    }
 }
 }  // namespace
 
-cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, cudaStream_t st)
+cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, bool trace, cudaStream_t st)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = init_fsr(dev);
     if (e != cudaSuccess) return e;
-    switch (fsr_blocks) {
-    case 2: launch_fsr_batched_t<2>(bd, st); break;
-    case 8: launch_fsr_batched_t<8>(bd, st); break;
-    default: launch_fsr_batched_t<4>(bd, st); break;
-    }
+    if (trace) launch_fsr_batched_b<true>(bd, fsr_blocks, st);
+    else launch_fsr_batched_b<false>(bd, fsr_blocks, st);
     count_launch();
     return cudaGetLastError();
 }
@@ -753,7 +781,8 @@ cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st)
         }
         return cudaGetLastError();
     }
-    fsr_kernel<<<tiles_fsr(t, WPB1), WPB1 * 32, sizeof(Smem<WPB1>), st>>>(t);
+    if (t.fsr_sel != nullptr) fsr_kernel<true><<<tiles_fsr(t, WPB1), WPB1 * 32, sizeof(Smem<WPB1>), st>>>(t);
+    else fsr_kernel<false><<<tiles_fsr(t, WPB1), WPB1 * 32, sizeof(Smem<WPB1>), st>>>(t);
     count_launch();
     return cudaGetLastError();
 }

@@ -131,7 +131,10 @@ extern "C" int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const u
         t.ref_msk[k] = d_ref_msk[k];
         t.mv[k] = reinterpret_cast<int8_t *>(take(2 * HW));
         t.fmv[k] = reinterpret_cast<int8_t *>(take(2 * HW));
+        // the check kernel writes the decisions straight into the caller's d_dec when given (it
+        // writes nothing when the mask is bad, so d_dec is then left as it was)
         t.dec[k] = take(HW);
+        if (d_dec) t.dec[k] = d_dec + (size_t)k * HW;
         if (cfg->cc_mode == RFSR_CC_RME) t.rmv[k] = reinterpret_cast<int8_t *>(take(2 * HW));
     }
     t.psum = d_psum;
@@ -150,11 +153,6 @@ extern "C" int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const u
     if (t.cc_mode == RFSR_CC_RME && (e = launch_rme_field(t, st)) != cudaSuccess)
         return dev_fail(e, "RME launch");
     if ((e = launch_cc_project(t, st)) != cudaSuccess) return dev_fail(e, "check launch");
-    if (d_dec)
-        for (int k = 0; k < nrefs; ++k)
-            if ((e = cudaMemcpyAsync(d_dec + (size_t)k * HW, t.dec[k], HW, cudaMemcpyDeviceToDevice,
-                                     st)) != cudaSuccess)
-                return dev_fail(e, "cudaMemcpyAsync");
     if (d_status &&
         (e = cudaMemcpyAsync(d_status, t.status, sizeof(int), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return dev_fail(e, "cudaMemcpyAsync");

@@ -224,6 +224,7 @@ struct rfsr_stream {
     uint16_t *psum = nullptr;
     uint8_t *pcnt = nullptr;
     float *fsr = nullptr;
+    uint16_t *fsr_sel = nullptr;   // selection trace (fsr_trace streams)
     float *tables = nullptr;
     int *d_zero = nullptr;
     std::vector<Slot> slots;
@@ -279,6 +280,14 @@ namespace {
 
 bool batched(const rfsr_engine *e) { return e->cfg.batched || e->cfg.serve; }
 
+// bytes of the FSR selection trace of one frame (0 unless the stream records it)
+size_t trace_bytes(const rfsr_stream_config *c)
+{
+    if (!c->fsr_trace) return 0;
+    const size_t nb = (size_t)((c->height + kFsrB - 1) / kFsrB) * ((c->width + kFsrB - 1) / kFsrB);
+    return std::max<size_t>(2, 2 * nb * (size_t)c->fsr_iterations);
+}
+
 // device bytes a stream will hold (admission against the engine budget)
 size_t stream_need(const rfsr_stream_config *c, int M)
 {
@@ -286,7 +295,8 @@ size_t stream_need(const rfsr_stream_config *c, int M)
     const int K = c->num_refs;
     const bool rme = c->cc_mode == RFSR_CC_RME;
     return (size_t)(K + 1) * 3 * HW + (size_t)K * (2 * HW * (rme ? 3 : 2) + HW) + 3 * HW + 4 * HW +
-           sizeof(FsrTables) + 64 + (size_t)M * (3 * HW + (c->keep_f32 ? 4 * HW : 0) + 4);
+           sizeof(FsrTables) + 64 + (size_t)M * (3 * HW + (c->keep_f32 ? 4 * HW : 0) + 4) +
+           trace_bytes(c);
 }
 
 // allocate a stream's device and pinned state (engine lock held)
@@ -319,6 +329,7 @@ int admit(rfsr_stream *s)
     AL(s->psum, 2 * HW);
     AL(s->pcnt, HW);
     AL(s->fsr, 4 * HW);
+    if (s->cfg.fsr_trace) AL(s->fsr_sel, trace_bytes(&s->cfg));
     AL(s->tables, sizeof(FsrTables));
     AL(s->d_zero, 64);
     cudaError_t er = cudaMemset(s->d_zero, 0, 64);
@@ -418,6 +429,7 @@ void prepare_frame(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const ui
     t.status = sl.d_status;
     t.prev_status = s->last_slot >= 0 ? s->slots[s->last_slot].d_status : s->d_zero;
     t.status_out = nullptr;
+    t.fsr_sel = s->fsr_sel;
     s->last_K = t.K;
     s->last_ring = s->ring_head;
     s->last_slot = slot_idx;
@@ -467,8 +479,8 @@ void engine_free(rfsr_engine *e, void *p)
 
 // launch the phases of one batch (captured into a graph, or directly); ph (tuning only): events
 // recorded before / after ME and before / after FSR
-cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape &sh, cudaStream_t st,
-                                cudaEvent_t *ph = nullptr)
+cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, bool trace, const BatchShape &sh,
+                                cudaStream_t st, cudaEvent_t *ph = nullptr)
 {
     cudaError_t e = launch_batch_prologue(d, st);
     if (e == cudaSuccess) e = launch_ingest_batched(d, st);
@@ -478,7 +490,7 @@ cudaError_t launch_batch_phases(BatchDesc *d, int T, bool rme, const BatchShape 
     if (e == cudaSuccess && rme) e = launch_rme_batched(d, T, st);
     if (e == cudaSuccess) e = launch_cc_batched(d, T, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[2], st);
-    if (e == cudaSuccess) e = launch_fsr_batched(d, sh.fsr_blocks, st);
+    if (e == cudaSuccess) e = launch_fsr_batched(d, sh.fsr_blocks, trace, st);
     if (e == cudaSuccess && ph) e = cudaEventRecord(ph[3], st);
     return e;
 }
@@ -541,7 +553,7 @@ int step_batch_locked(rfsr_engine *e)
     }
     BatchDesc *bd = set.h;
     int T = -1, n = 0;
-    bool rme = false;
+    bool rme = false, trace = false;
     std::vector<std::pair<rfsr_stream *, int>> taken;
     for (rfsr_stream *s : e->streams) {
         if (!s->live || s->launched >= s->pushed || n >= kMaxBatch) continue;
@@ -554,6 +566,7 @@ int step_batch_locked(rfsr_engine *e)
         t.status_out = sl.h_status_dev;
         if (sl.host_push) t.out_u8 = sl.h_out_dev;
         rme = rme || t.cc_mode == RFSR_CC_RME;
+        trace = trace || t.fsr_sel != nullptr;
         taken.emplace_back(s, si);
         ++n;
     }
@@ -600,7 +613,7 @@ int step_batch_locked(rfsr_engine *e)
     }
     const bool prof = e->cfg.profile != 0;
     if (prof) CK(cudaEventRecord(set.t0, e->stream));
-    const int key = 2 * T + (rme ? 1 : 0);
+    const int key = 4 * T + (trace ? 2 : 0) + (rme ? 1 : 0);
     bool launched = false;
     if (e->graphs_ok && !tuning) {
         auto it = set.graphs.find(key);
@@ -612,7 +625,7 @@ int step_batch_locked(rfsr_engine *e)
             if (er == cudaSuccess) {
                 cudaError_t er2 = cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc),
                                                   cudaMemcpyHostToDevice, e->stream);
-                if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, sh, e->stream);
+                if (er2 == cudaSuccess) er2 = launch_batch_phases(set.d, T, rme, trace, sh, e->stream);
                 er = cudaStreamEndCapture(e->stream, &g);
                 if (er == cudaSuccess) er = er2;
             }
@@ -636,7 +649,7 @@ int step_batch_locked(rfsr_engine *e)
     }
     if (!launched) {
         CK(cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream));
-        CK(launch_batch_phases(set.d, T, rme, sh, e->stream, tuning ? set.ph : nullptr));
+        CK(launch_batch_phases(set.d, T, rme, trace, sh, e->stream, tuning ? set.ph : nullptr));
     }
     if (tuning) {
         set.tune_pending = true;
@@ -955,6 +968,7 @@ static int check_stream_config(const rfsr_stream_config *c)
     if (!(c->fsr_proj_weight >= 0.f)) return fail(RFSR_EINVAL, "stream config: fsr_proj_weight");
     if (!(c->fsr_concealed_weight >= 0.f && c->fsr_concealed_weight <= 1e6f))
         return fail(RFSR_EINVAL, "stream config: fsr_concealed_weight must be >= 0");
+    if (c->fsr_trace != 0 && c->fsr_trace != 1) return fail(RFSR_EINVAL, "stream config: fsr_trace must be 0 or 1");
     return RFSR_OK;
 }
 
@@ -1426,6 +1440,9 @@ int rfsr_debug_get(rfsr_stream *s, int what, int k, void *dst)
         break;
     }
     case RFSR_DBG_REC: src = s->ring_rec[s->last_ring]; n = HW; break;
+    case RFSR_DBG_FSR_SEL:
+        if (!s->fsr_sel) return fail(RFSR_ESTATE, "debug_get: FSR selections are recorded only with fsr_trace = 1");
+        src = s->fsr_sel; n = trace_bytes(&s->cfg); break;
     default: return fail(RFSR_EINVAL, "debug_get: unknown plane");
     }
     CK(cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost));
@@ -1445,9 +1462,9 @@ int rfsr_stream_phase_ms(rfsr_stream *s, float ms[4])
     return RFSR_OK;
 }
 
-int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
-                    const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
-                    uint8_t *d_out_u8, void *cuda_stream)
+static int fsr_device_impl(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
+                           const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
+                           uint8_t *d_out_u8, uint16_t *d_sel, void *cuda_stream)
 {
     if (!cfg || !d_smp || !d_msk) return fail(RFSR_EINVAL, "fsr_device: NULL argument");
     if ((d_psum == nullptr) != (d_pcnt == nullptr))
@@ -1500,8 +1517,27 @@ int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const u
     t.cur_rec = nullptr;
     t.out_u8 = d_out_u8;
     t.status = zero;
+    t.fsr_sel = d_sel;
     CK(launch_fsr(t, (cudaStream_t)cuda_stream));
     return RFSR_OK;
+}
+
+int rfsr_fsr_device(const rfsr_stream_config *cfg, const uint8_t *d_smp, const uint8_t *d_msk,
+                    const uint16_t *d_psum, const uint8_t *d_pcnt, float *d_out_f32,
+                    uint8_t *d_out_u8, void *cuda_stream)
+{
+    return fsr_device_impl(cfg, d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, nullptr,
+                           cuda_stream);
+}
+
+int rfsr_fsr_device_trace(const rfsr_stream_config *cfg, const uint8_t *d_smp,
+                          const uint8_t *d_msk, const uint16_t *d_psum, const uint8_t *d_pcnt,
+                          float *d_out_f32, uint8_t *d_out_u8, uint16_t *d_sel, void *cuda_stream)
+{
+    if (!d_sel || ((uintptr_t)d_sel & 1u))
+        return fail(RFSR_EINVAL, "fsr_device_trace: d_sel must be a 2-byte aligned device buffer");
+    return fsr_device_impl(cfg, d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, d_sel,
+                           cuda_stream);
 }
 
 }  // extern "C"

@@ -59,6 +59,7 @@ struct FrameTask {
     int *status;               // frame status word (kStatus* bits)
     const int *prev_status;    // status word of the previous frame of the stream (poison chain)
     int *status_out;           // optional: receives the final status word (written by FSR)
+    uint16_t *fsr_sel;         // optional: selected basis pair per block and iteration (trace)
 };
 
 // A batched frame step: up to kMaxBatch frame tasks (one per stream) run by one persistent
@@ -168,7 +169,8 @@ int tiles_rme9(const FrameTask &t);
 cudaError_t launch_rme9(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st);
 cudaError_t launch_cc_batched(BatchDesc *bd, int T, cudaStream_t st);
-cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, cudaStream_t st);
+// trace: run the instantiation that records FSR selections of the tasks that ask for them
+cudaError_t launch_fsr_batched(BatchDesc *bd, int fsr_blocks, bool trace, cudaStream_t st);
 
 // FSR tables computed on the host (no device transcendentals): spatial weights rho^d over the
 // support, frequency weights over the stored half spectrum and the DFT twiddles.

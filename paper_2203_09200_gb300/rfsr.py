@@ -20,7 +20,8 @@ RFSR_OK, RFSR_EINVAL, RFSR_EMASK, RFSR_ENOMEM, RFSR_EAGAIN, RFSR_EBUSY, RFSR_ETI
 CC_MODES = {"none": 0, "rme": 1, "rmc": 2, "frmc": 3, "nnc": 4, "nnc_frmc": 5}
 DEC_MEASURED, DEC_NOT_PROJECTABLE, DEC_NNC_REJECT, DEC_CHECK_REJECT, DEC_ACCEPT = range(5)
 MASK_FIXED, MASK_DYNAMIC = 0, 1
-DBG_MV, DBG_FMV, DBG_DECISION, DBG_PSUM, DBG_PCNT, DBG_FSR, DBG_REC, DBG_RMV = range(8)
+DBG_MV, DBG_FMV, DBG_DECISION, DBG_PSUM, DBG_PCNT, DBG_FSR, DBG_REC, DBG_RMV, DBG_FSR_SEL = range(9)
+FSR_SEL_NONE = 0xFFFF
 
 _ERRNAMES = {RFSR_EINVAL: "EINVAL", RFSR_EMASK: "EMASK", RFSR_ENOMEM: "ENOMEM",
              RFSR_EAGAIN: "EAGAIN", RFSR_EBUSY: "EBUSY", RFSR_ETIMEDOUT: "ETIMEDOUT",
@@ -50,7 +51,8 @@ class rfsr_stream_config(C.Structure):
                 ("search_radius", C.c_int), ("check_radius", C.c_int),
                 ("fsr_iterations", C.c_int), ("fsr_rho", C.c_float), ("fsr_gamma", C.c_float),
                 ("fsr_proj_weight", C.c_float), ("fsr_overwrite_projected", C.c_int),
-                ("keep_f32", C.c_int), ("fsr_concealed_weight", C.c_float)]
+                ("keep_f32", C.c_int), ("fsr_concealed_weight", C.c_float),
+                ("fsr_trace", C.c_int)]
 
 
 class rfsr_batch_shape(C.Structure):
@@ -105,6 +107,8 @@ SYMBOLS = {
     "rfsr_set_history": ([_VP, _I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP)], _I),
     "rfsr_debug_get": ([_VP, _I, _I, _VP], _I),
     "rfsr_fsr_device": ([C.POINTER(rfsr_stream_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "rfsr_fsr_device_trace": ([C.POINTER(rfsr_stream_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                               _VP], _I),
     "rfsr_stream_phase_ms": ([_VP, C.POINTER(C.c_float)], _I),
     "rfsr_me_cc_project_noalloc": ([C.POINTER(rfsr_stream_config), _VP, _VP, _I, C.POINTER(_VP),
                                     C.POINTER(_VP), C.POINTER(_VP), _VP, _VP, _VP, _VP, _VP], _I),
@@ -181,7 +185,7 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
                   check_radius: Optional[int] = None, fsr_iterations: int = 100,
                   fsr_rho: float = 0.7, fsr_gamma: float = 0.5, fsr_proj_weight: float = 1.0,
                   fsr_overwrite_projected: bool = False, keep_f32: bool = False,
-                  fsr_concealed_weight: float = 0.0) -> rfsr_stream_config:
+                  fsr_concealed_weight: float = 0.0, fsr_trace: bool = False) -> rfsr_stream_config:
     c = rfsr_stream_config()
     load().rfsr_stream_config_default(C.byref(c))
     c.height, c.width = height, width
@@ -196,6 +200,7 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
     c.fsr_overwrite_projected = int(bool(fsr_overwrite_projected))
     c.keep_f32 = int(bool(keep_f32))
     c.fsr_concealed_weight = fsr_concealed_weight
+    c.fsr_trace = int(bool(fsr_trace))
     return c
 
 
@@ -348,10 +353,12 @@ class Stream:
 
     def debug_get(self, what: int, k: int = 0) -> np.ndarray:
         H, W = self.H, self.W
+        nb = (-(-H // 4)) * (-(-W // 4))
         shape, dt = {DBG_MV: ((H, W, 2), np.int8), DBG_FMV: ((H, W, 2), np.int8),
                      DBG_RMV: ((H, W, 2), np.int8), DBG_DECISION: ((H, W), np.uint8),
                      DBG_PSUM: ((H, W), np.uint16), DBG_PCNT: ((H, W), np.uint8),
-                     DBG_FSR: ((H, W), np.float32), DBG_REC: ((H, W), np.uint8)}[what]
+                     DBG_FSR: ((H, W), np.float32), DBG_REC: ((H, W), np.uint8),
+                     DBG_FSR_SEL: ((nb, max(1, self.cfg.fsr_iterations)), np.uint16)}[what]
         out = np.empty(shape, dt)
         _check(load().rfsr_debug_get(self.handle, what, k, out.ctypes.data))
         return out
@@ -385,6 +392,16 @@ def fsr_device(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, height: int, w
     cfg = stream_config(height, width, **fsr_kw)
     _check(load().rfsr_fsr_device(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
                                   _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8), cuda_stream))
+
+
+def fsr_device_trace(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, d_sel, height: int,
+                     width: int, cuda_stream: Optional[int] = None, **fsr_kw):
+    """rfsr_fsr_device_trace: stand-alone FSR that also records the selected basis pair of every
+    iteration of every block in d_sel (nblocks x iterations uint16)."""
+    cfg = stream_config(height, width, **fsr_kw)
+    _check(load().rfsr_fsr_device_trace(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
+                                        _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8),
+                                        _ptr(d_sel), cuda_stream))
 
 
 def me_cc_project_noalloc(d_smp, d_msk, refs, d_psum, d_pcnt, height: int, width: int,

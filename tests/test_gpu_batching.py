@@ -255,3 +255,56 @@ def test_bounded_waits(built):
         assert e.value.code == rfsr.RFSR_ESTATE
         eng.step()
         st.get_frame(timeout_ms=60000)
+
+
+# --------------------------------------------------------------------------------------------
+# a batched step of several streams against the oracle (not only against the streams alone)
+# --------------------------------------------------------------------------------------------
+ORACLE_SPECS = [  # (H, W, mask type, cc mode, seed): T = 9, three past frames each
+    (240, 320, synth.MASK_DYNAMIC, "nnc_frmc", 11),
+    (130, 250, synth.MASK_FIXED, "frmc", 12),
+    (96, 128, synth.MASK_DYNAMIC, "rmc", 13),
+    (66, 98, synth.MASK_DYNAMIC, "rme", 14),
+    (64, 64, synth.MASK_FIXED, "nnc", 15),
+]
+
+
+@pytest.mark.parametrize("rows,blocks,variant", [(64, 4, 0), (32, 2, 1)])
+def test_batched_step_against_oracle(built, rows, blocks, variant):
+    """One batched step over streams of uneven sizes, masks and check modes, with injected
+    generator-made past frames: every stream's motion fields, filtered fields, decisions and
+    projections equal the oracle's bit for bit, and its FSR output passes the replay rule.
+    variant 1 runs the T = 9 motion estimation as sliding-window box sums (me_variant = 1), so its
+    vectors are compared with the oracle's directly."""
+    import oracle
+    from fsr_parity import check_replay
+    t = 3
+    seqs = [synth.config2(seed=sd, H=H, W=W, F=t + 1, mask_type=mt)
+            for H, W, mt, _, sd in ORACLE_SPECS]
+    with rfsr.Engine(device=0, batched=True, autotune=False) as eng:
+        eng.set_shape(me_tile_rows=rows, fsr_blocks=blocks, me_variant=variant)
+        sts = [eng.create_stream(height=H, width=W, cc_mode=mode, keep_f32=True, fsr_trace=True)
+               for H, W, _, mode, _ in ORACLE_SPECS]
+        hists = []
+        for st, seq in zip(sts, seqs):
+            hist = [(seq.frames[t - k], seq.samples[t - k], seq.masks[t - k]) for k in (1, 2, 3)]
+            hists.append(hist)
+            st.set_history(hist)
+            st.push_frame(seq.samples[t], seq.masks[t])
+        assert eng.step() == len(ORACLE_SPECS)
+        for st, seq, hist, (H, W, _, mode, _) in zip(sts, seqs, hists, ORACLE_SPECS):
+            rec, f32 = st.get_frame(timeout_ms=60000, f32=True)
+            ref = oracle.frame_step(seq.samples[t], seq.masks[t], hist,
+                                    cc_mode=oracle.CC_NAMES[mode], T=9, R=8)
+            for k in range(3):
+                np.testing.assert_array_equal(st.debug_get(rfsr.DBG_MV, k + 1), ref.mv[k],
+                                              err_msg=f"{H}x{W} {mode} mv k={k + 1}")
+                np.testing.assert_array_equal(st.debug_get(rfsr.DBG_FMV, k + 1), ref.fmv[k])
+                np.testing.assert_array_equal(st.debug_get(rfsr.DBG_DECISION, k + 1), ref.dec[k],
+                                              err_msg=f"{H}x{W} {mode} dec k={k + 1}")
+            np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PSUM), ref.psum)
+            np.testing.assert_array_equal(st.debug_get(rfsr.DBG_PCNT), ref.pcnt)
+            check_replay(f32, st.debug_get(rfsr.DBG_FSR_SEL), seq.samples[t], seq.masks[t],
+                         ref.psum, ref.pcnt)
+            m = seq.masks[t] == 1
+            np.testing.assert_array_equal(rec[m], seq.samples[t][m])

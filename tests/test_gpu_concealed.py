@@ -2,26 +2,25 @@
 zero in Sec. 4 so that blocks are independent).
 
 With delta > 0 block (i, j) reads the reconstruction of the blocks before it in raster order, so
-the comparison with the oracle follows the same order.  A block whose support holds no block that
-diverged must be within 1e-4 of the oracle's raster-order output.  If it is not, it must be a
-result of the method at a near tie: oracle.fsr_block_concealed_valid, with the oracle's own
-earlier outputs as the concealed values.  It then counts as diverged, and every later block that
-reads it (transitively) is left out of the element-wise comparison.  Divergences must stay rare,
-and most blocks must be compared.  The output buffer is filled with a value far outside [0, 1]
-before the call, so a block that read a concealed pixel before its block was written would show.
+the oracle runs in the same order, each block replaying the selection sequence the GPU recorded
+for it and reading the oracle's own earlier outputs as concealed values.  Every block is then
+compared under the replay rule of tests/fsr_parity.py: within 1e-4 of the replay, and every
+iteration that leaves the FP64 argmax a tie within FP32 rounding.  The output buffer is filled
+with a value far outside [0, 1] before the call, so a block that read a concealed pixel before
+its block was written would show.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from fsr_parity import BOUND, check_against
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 from paper_2203_09200_gb300 import rfsr  # noqa: E402
 
-FSR_TOL = 1e-4
 B = 4
 
 
@@ -45,29 +44,11 @@ def projections(seq, msk, seed, frac=0.4):
     return psum, pcnt
 
 
-def check_raster(got, ref, P, delta, smp, msk, psum, pcnt):
-    """Raster-order comparison; returns (blocks compared, blocks diverged, blocks left out)."""
-    H, W = got.shape
-    nby, nbx = -(-H // B), -(-W // B)
-    bad = np.zeros((nby, nbx), bool)            # diverged, or reads a diverged block
-    compared = diverged = 0
-    for i in range(nby):
-        for j in range(nbx):
-            lo = max(0, j - 4)
-            if bad[max(0, i - 4):i, lo:j + 5].any() or bad[i, lo:j].any():
-                bad[i, j] = True
-                continue
-            g = got[B * i:B * i + B, B * j:B * j + B].astype(np.float64)
-            assert np.isfinite(g).all(), (i, j)
-            compared += 1
-            if np.abs(g - ref[B * i:B * i + B, B * j:B * j + B]).max() <= FSR_TOL:
-                continue
-            ok, e0, it = oracle.fsr_block_concealed_valid(P, delta, ref, smp, msk, psum, pcnt,
-                                                          i, j, np.ascontiguousarray(g))
-            assert ok, f"block ({i}, {j}) is {e0:.2e} from the oracle and no near-tie continuation"
-            bad[i, j] = True
-            diverged += 1
-    return compared, diverged, int(bad.sum()) - diverged
+def check_raster(got, sel, P, delta, smp, msk, psum, pcnt):
+    """Raster-order replay of every block against the GPU's output; returns the stats dict."""
+    assert np.isfinite(got).all()
+    out, _, rep = oracle.fsr_frame_concealed(P, delta, smp, msk, psum, pcnt, sel=sel, bound=BOUND)
+    return check_against(got, out, rep, B=B)
 
 
 def run_fsr_device(smp, msk, psum, pcnt, delta, iters):
@@ -75,12 +56,13 @@ def run_fsr_device(smp, msk, psum, pcnt, delta, iters):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out32 = torch.full((H, W), 7.0, dtype=torch.float32, device="cuda")
     out8 = torch.empty((H, W), dtype=torch.uint8, device="cuda")
-    rfsr.fsr_device(dev(smp), dev(msk), None if psum is None else dev(psum),
-                    None if pcnt is None else dev(pcnt), out32, out8, H, W,
-                    cuda_stream=torch.cuda.current_stream().cuda_stream,
-                    fsr_iterations=iters, fsr_concealed_weight=delta)
+    sel = torch.empty(((-(-H // B)) * (-(-W // B)), iters), dtype=torch.int16, device="cuda")
+    rfsr.fsr_device_trace(dev(smp), dev(msk), None if psum is None else dev(psum),
+                          None if pcnt is None else dev(pcnt), out32, out8, sel, H, W,
+                          cuda_stream=torch.cuda.current_stream().cuda_stream,
+                          fsr_iterations=iters, fsr_concealed_weight=delta)
     torch.cuda.synchronize()
-    return out32.cpu().numpy(), out8.cpu().numpy()
+    return out32.cpu().numpy(), out8.cpu().numpy(), sel.cpu().numpy().view(np.uint16)
 
 
 @pytest.mark.parametrize("H,W,delta,iters,proj", [
@@ -93,15 +75,10 @@ def test_concealed_fsr_device_matches_oracle(engine, H, W, delta, iters, proj):
     seq = synth.config2(seed=H + W, H=H, W=W, F=1)
     smp, msk = seq.samples[0], seq.masks[0]
     psum, pcnt = projections(seq, msk, seed=H) if proj else (None, None)
-    got, got8 = run_fsr_device(smp, msk, psum, pcnt, delta, iters)
+    got, got8, sel = run_fsr_device(smp, msk, psum, pcnt, delta, iters)
     P = oracle.FsrParams(iterations=iters)
-    ref, _ = oracle.fsr_frame_concealed(P, delta, smp, msk, psum, pcnt)
-    nblk = (-(-H // B)) * (-(-W // B))
-    compared, diverged, skipped = check_raster(got, ref, P, delta, smp, msk, psum, pcnt)
-    print(f"{H}x{W} delta {delta} iters {iters}: {compared}/{nblk} compared, "
-          f"{diverged} diverged at near ties, {skipped} left out")
-    assert diverged <= max(2, nblk // 20)
-    assert compared >= nblk // 4
+    stats = check_raster(got, sel, P, delta, smp, msk, psum, pcnt)
+    print(f"{H}x{W} delta {delta} iters {iters}: {stats}")
     m = msk == 1
     np.testing.assert_array_equal(got8[m], smp[m])
     # delta really changes the result (the wavefront path is not the independent-block one)
@@ -116,22 +93,21 @@ def test_concealed_stream_step(engine):
     t = 3
     smp, msk = seq.samples[t], seq.masks[t]
     hist = [(seq.frames[t - k], seq.samples[t - k], seq.masks[t - k]) for k in (1, 2, 3)]
-    st = engine.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=delta)
+    st = engine.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=delta,
+                              fsr_trace=True)
     try:
         st.set_history(hist)
         st.push_frame(smp, msk)
         rec, got = st.get_frame(timeout_ms=120000, f32=True)
         psum, pcnt = st.debug_get(rfsr.DBG_PSUM), st.debug_get(rfsr.DBG_PCNT)
+        sel = st.debug_get(rfsr.DBG_FSR_SEL)
     finally:
         st.destroy()
     P = oracle.FsrParams()
     ref = oracle.frame_step(smp, msk, hist, cc_mode=oracle.CC_NNC_FRMC, T=9, R=8, run_fsr=False)
     np.testing.assert_array_equal(psum, ref.psum)
     np.testing.assert_array_equal(pcnt, ref.pcnt)
-    ref_out, _ = oracle.fsr_frame_concealed(P, delta, smp, msk, ref.psum, ref.pcnt)
-    nblk = (H // B) * (W // B)
-    compared, diverged, _ = check_raster(got, ref_out, P, delta, smp, msk, ref.psum, ref.pcnt)
-    assert diverged <= max(2, nblk // 20) and compared >= nblk // 4
+    check_raster(got, sel, P, delta, smp, msk, ref.psum, ref.pcnt)
     np.testing.assert_array_equal(rec[msk == 1], smp[msk == 1])
 
 
@@ -140,17 +116,16 @@ def test_concealed_first_frame_of_a_stream(engine):
     H, W, delta = 40, 48, 0.5
     seq = synth.config2(seed=32, H=H, W=W, F=1)
     smp, msk = seq.samples[0], seq.masks[0]
-    st = engine.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=delta)
+    st = engine.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=delta,
+                              fsr_trace=True)
     try:
         st.push_frame(smp, msk)
         _, got = st.get_frame(timeout_ms=60000, f32=True)
+        sel = st.debug_get(rfsr.DBG_FSR_SEL)
     finally:
         st.destroy()
     P = oracle.FsrParams()
-    ref, _ = oracle.fsr_frame_concealed(P, delta, smp, msk)
-    nblk = (H // B) * (W // B)
-    compared, diverged, _ = check_raster(got, ref, P, delta, smp, msk, None, None)
-    assert diverged <= max(2, nblk // 20) and compared >= nblk // 4
+    check_raster(got, sel, P, delta, smp, msk, None, None)
 
 
 def test_concealed_errors(engine):
