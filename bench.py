@@ -65,8 +65,44 @@ def me_cost_evaluations(h=H, w=W, r=R, k=KREF):
     return k * cy * cx
 
 
-ME_OPS_PER_COST = 6        # |a-b|, mask AND, vertical and horizontal running-sum updates (2),
-                           # key formation and running minimum (2)
+# Algorithmic work of the metric's path, counted as the method states it: a template cost
+# C(p, v) is a sum of |s_t - rec| over the measured pixels of the T x T template (Sec. 2.2), so one
+# cost evaluation is n(p) masked byte absolute differences, n(p) the measured pixels in the
+# template around p (about T^2 / 4 under quarter sampling).  ME evaluates every candidate v with
+# p + v inside the frame; FRMC evaluates the 49 reverse costs C(p + d, v - d) with p + d inside
+# for every pixel it checks (Sec. 3.1.1), whatever the outcome.
+FRMC_OFFSETS = (-7, -3, -1, 0, 1, 3, 7)
+
+
+def template_counts(msk, t=T):
+    """n(p): measured pixels of the t x t template around every pixel (0 outside the frame)."""
+    h = t // 2
+    m = np.pad(np.asarray(msk, np.int64) != 0, h).astype(np.int64)
+    c = np.pad(m.cumsum(0).cumsum(1), ((1, 0), (1, 0)))
+    Hh, Ww = np.asarray(msk).shape
+    return c[t:t + Hh, t:t + Ww] - c[:Hh, t:t + Ww] - c[t:t + Hh, :Ww] + c[:Hh, :Ww]
+
+
+def me_byteops(msk, t=T, r=R):
+    """Masked byte |a-b| of forward ME against one past frame: sum over p of n(p) |V(p)|."""
+    n = template_counts(msk, t)
+    Hh, Ww = n.shape
+    cy = np.array([min(y + r, Hh - 1) - max(y - r, 0) + 1 for y in range(Hh)], np.int64)
+    cx = np.array([min(x + r, Ww - 1) - max(x - r, 0) + 1 for x in range(Ww)], np.int64)
+    return int((n * cy[:, None] * cx[None, :]).sum())
+
+
+def frmc_source_work(msk, t=T):
+    """S(p) = sum over the FRMC offsets d with p + d inside of n(p + d): the masked byte |a-b| of
+    one pixel's FRMC check."""
+    n = template_counts(msk, t)
+    Hh, Ww = n.shape
+    pad = np.pad(n, 7)
+    S = np.zeros_like(n)
+    for dy in FRMC_OFFSETS:
+        for dx in FRMC_OFFSETS:
+            S += pad[7 + dy:7 + dy + Hh, 7 + dx:7 + dx + Ww]
+    return S
 
 
 def fsr_flops_per_block(iters=ITERS):
@@ -650,6 +686,8 @@ def run_ours(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     phases = []
+    frames_run = []
+    checked = []                                # pixels FRMC checked, per timed frame
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -662,6 +700,11 @@ def run_ours(args, rank, world, local_rank):
         ev[i][1].record(stream)
         st.get_frame_device(timeout_ms=120000)
         phases.append(st.phase_ms())
+        frames_run.append((nwarm + i) % F)
+        # the work count of this frame (outside the events): NNC+FRMC decides ACCEPT or
+        # CHECK_REJECT exactly for the pixels its FRMC checked
+        dec = np.stack([st.debug_get(rfsr.DBG_DECISION, k) for k in range(1, KREF + 1)])
+        checked.append(((dec == rfsr.DEC_ACCEPT) | (dec == rfsr.DEC_CHECK_REJECT)).sum(axis=0))
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = rfsr.kernel_launches() - launches0
@@ -718,24 +761,43 @@ def run_ours(args, rank, world, local_rank):
         return
     hbm, mhz, src = load_peaks()
     nb = (H // 4) * (W // 4)
-    me_ops = ME_OPS_PER_COST * me_cost_evaluations()
     fsr_flops = fsr_flops_per_block() * nb
-    int_peak = SMS * INT32_LANES_PER_SM * mhz * 1e6
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6
+    # the metric's path as one unit: ME (me9_kernel) + checks and projection (cc_project_kernel),
+    # algorithmic masked byte |a-b| per frame over their summed CUDA-event time per frame
+    me_w, cc_w = {}, []
+    for f, chk in zip(frames_run, checked):
+        key = seq.masks[f].tobytes()
+        if key not in me_w:
+            me_w[key] = (KREF * me_byteops(seq.masks[f]), frmc_source_work(seq.masks[f]))
+        cc_w.append(int((me_w[key][1] * chk).sum()))
+    me_ops = float(np.mean([me_w[seq.masks[f].tobytes()][0] for f in frames_run]))
+    cc_ops = float(np.mean(cc_w))
+    _, vabs_clk = rfsr.alu_peak("vabsdiffu4", device=local_rank)
+    byte_peak = vabs_clk * 4 * SMS * mhz * 1e6
     me_s, cc_s, fsr_s = ph_mean[1] / 1e3, ph_mean[2] / 1e3, ph_mean[3] / 1e3
-    kern = {"me": (me_ops / me_s / 1e12, int_peak / 1e12, "Tops/s (int32)"),
-            "fsr": (fsr_flops / fsr_s / 1e12, fp32_peak / 1e12, "TFLOP/s (fp32)")}
-    dom = "me" if me_s >= fsr_s else "fsr"
-    ach, peak, unit = kern[dom]
-    roof = {"kernel": {"me": "me9_kernel", "fsr": "fsr_kernel"}[dom], "bound": "alu",
-            "achieved": round(ach, 3), "peak": round(peak, 3), "unit": unit,
-            "frac": round(ach / peak, 4),
-            "traffic": profiled_traffic({"me": "me9_kernel", "fsr": "fsr_kernel"}[dom]),
-            "peak_source": f"derived: {SMS} SMs x "
-                           f"{INT32_LANES_PER_SM if dom == 'me' else FP32_LANES_PER_SM * 2} "
-                           f"ops/clk x {mhz:.0f} MHz ({src} max clock)",
-            "other": {k: {"achieved": round(v[0], 3), "peak": round(v[1], 3), "unit": v[2],
-                          "frac": round(v[0] / v[1], 4)} for k, v in kern.items() if k != dom}}
+    ach = (me_ops + cc_ops) / (me_s + cc_s)
+    tr_me, tr_cc = profiled_traffic("me9_kernel"), profiled_traffic("cc_project_kernel")
+    roof = {"kernel": "me9_kernel + cc_project_kernel<9> (ME + checks + projection, one launch "
+                      "each per frame: the metric's path)",
+            "bound": "alu", "achieved": round(ach / 1e12, 3), "peak": round(byte_peak / 1e12, 3),
+            "unit": "T masked byte |a-b| per s", "frac": round(ach / byte_peak, 4),
+            "traffic": (tr_me + tr_cc) if tr_me and tr_cc else None,
+            "work_per_frame": {"me_byteops": me_ops, "frmc_byteops": cc_ops,
+                               "frmc_checked_pixels": float(np.mean([c.sum() for c in checked]))},
+            "peak_source": f"__vabsdiffu4 (4 byte |a-b| per instruction) measured by rfsr_alu_peak: "
+                           f"{vabs_clk:.1f} per clock per SM x 4 bytes x {SMS} SMs x {mhz:.0f} MHz "
+                           f"({src} max clock)",
+            "other": {"me9_kernel": {"achieved": round(me_ops / me_s / 1e12, 3),
+                                     "peak": round(byte_peak / 1e12, 3),
+                                     "unit": "T masked byte |a-b| per s",
+                                     "frac": round(me_ops / me_s / byte_peak, 4)},
+                      "fsr_kernel": {"achieved": round(fsr_flops / fsr_s / 1e12, 3),
+                                     "peak": round(fp32_peak / 1e12, 3), "unit": "TFLOP/s (fp32)",
+                                     "frac": round(fsr_flops / fsr_s / fp32_peak, 4),
+                                     "traffic": profiled_traffic("fsr_kernel"),
+                                     "peak_source": f"derived: {SMS} SMs x "
+                                                    f"{FP32_LANES_PER_SM * 2} flop/clk x {mhz:.0f} MHz"}}}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, full, tot = oracle_crop_rate(seq, 8, (96, 96), seed=5)

@@ -214,23 +214,33 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
     if (*t.status) return;
     const uint8_t *__restrict__ ref = t.ref_rec[k];
 
-    // past frame around the CTA: rows y0-4-R .., columns x0-4-R .., clamped coordinates
+    // past frame around the CTA: rows y0-4-R .., columns x0-4-R .., clamped coordinates.  A word
+    // inside the frame is one aligned 32-bit load when the plane's rows and the window start are
+    // 4-byte aligned (W % 4 == 0, R % 4 == 0); words across a border take clamped bytes.
     const int rx0 = x0 - 4 - R, ry0 = y0 - 4 - R;
     const int nrows = S_OUTH + 8 + 2 * R;
+    const bool al_ref = ((W | rx0) & 3) == 0 && ((uintptr_t)ref & 3) == 0;
     for (int i = threadIdx.x; i < nrows * S_RWORDS; i += S_NT) {
         const int r = i / S_RWORDS, w = i - r * S_RWORDS;
         const uint8_t *row = ref + (size_t)min(max(ry0 + r, 0), H - 1) * W;
         const int gx = rx0 + 4 * w;
         uint32_t v = 0;
+        if (al_ref && gx >= 0 && gx + 4 <= W) {
+            v = *reinterpret_cast<const uint32_t *>(row + gx);
+        } else {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+            for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        }
         sm.rf[0][i] = v;
     }
     build_tie_order(sm.vord, R);
 
-    // current frame: this lane's 16 rows of 4 columns (masked samples, byte masks; 0 outside)
+    // current frame: this lane's 16 rows of 4 columns (masked samples, byte masks; 0 outside),
+    // one aligned 32-bit load per plane and row where the word lies inside a 4-byte aligned frame
     const int cx = x0 - 4 + 4 * lane;                     // first column of the lane's word
     const int cy0 = y0 + S_ROWS * warp - 4;               // first D row of the warp
+    const bool al_cur = (W & 3) == 0 && (((uintptr_t)t.cur_smp | (uintptr_t)t.cur_msk) & 3) == 0 &&
+                        cx >= 0 && cx + 4 <= W;           // cx is a multiple of 4
     uint32_t cs[S_DROWS], cmk[S_DROWS];
 #pragma unroll
     for (int i = 0; i < S_DROWS; ++i) {
@@ -238,12 +248,17 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
         uint32_t a = 0, m = 0;
         if (y >= 0 && y < H) {
             const size_t ro = (size_t)y * W;
+            if (al_cur) {
+                a = *reinterpret_cast<const uint32_t *>(t.cur_smp + ro + cx);
+                m = *reinterpret_cast<const uint32_t *>(t.cur_msk + ro + cx);
+            } else {
 #pragma unroll
-            for (int b = 0; b < 4; b += 2) {
-                const int x = cx + b;
-                if (x >= 0 && x < W) {        // W even, x even: pixel pairs never straddle
-                    a |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_smp + ro + x)) << (8 * b);
-                    m |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_msk + ro + x)) << (8 * b);
+                for (int b = 0; b < 4; b += 2) {
+                    const int x = cx + b;
+                    if (x >= 0 && x < W) {    // W even, x even: pixel pairs never straddle
+                        a |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_smp + ro + x)) << (8 * b);
+                        m |= (uint32_t)(*reinterpret_cast<const uint16_t *>(t.cur_msk + ro + x)) << (8 * b);
+                    }
                 }
             }
         }
