@@ -379,7 +379,8 @@ int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const uint8_t *d_s
  * 4 byte SAD (__vsadu4) + add, 5 16-bit x2 3-way max, 6 16-bit x2 3-way min, 7 integer multiply-add,
  * 8 |a-b|+c (__sad), 9 32-bit min, 10 xor, 11 FP32 fused multiply-add, 12 3-input adds and
  * integer multiply-adds interleaved (one each per pair of chains), 13 byte SAD with accumulate
- * (one vabsdiff4.add).  Synchronous; allocates
+ * (one vabsdiff4.add), 14 signed 16-bit x2 minimum (min.s16x2), 15 sum of the two signed 16-bit
+ * |a-b| with accumulate (vabsdiff2.add), 16 signed 16-bit x2 3-way max.  Synchronous; allocates
  * and frees its own small buffers.  Errors: EINVAL, EDEVICE. */
 int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_sec, double *ops_per_clk_sm);
 

@@ -40,11 +40,30 @@ __device__ __forceinline__ uint32_t sad4_acc(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
+// kind 14: signed 16-bit x2 minimum; kind 15: sum of the two signed 16-bit |a-b| plus c (the L1
+// distance of two packed vectors) as one SIMD-video instruction
+__device__ __forceinline__ uint32_t min_s16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t sad2_acc(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("vabsdiff2.s32.s32.s32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 template <int OP>
 __device__ __forceinline__ uint32_t op_chain(int i, uint32_t a, uint32_t b, uint32_t c)
 {
     if constexpr (OP == 12) return (i & 1) ? a * b + c : a + b + c;
     else if constexpr (OP == 13) return sad4_acc(a, b, c);
+    else if constexpr (OP == 14) return min_s16x2(a, b);
+    else if constexpr (OP == 15) return sad2_acc(a, b, c);
+    else if constexpr (OP == 16) return (uint32_t)__vimax3_s16x2((int)a, (int)b, (int)c);
     else return op<OP>(a, b, c);
 }
 
@@ -139,7 +158,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
                              double *ops_per_clk_sm)
 {
     using namespace rfsr;
-    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 13)
+    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 16)
         return RFSR_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return RFSR_EDEVICE;
     int sms = 0;
@@ -158,6 +177,9 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
     case 8: e = run(int_kernel<8>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 12: e = run(int_kernel<12>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 13: e = run(int_kernel<13>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 14: e = run(int_kernel<14>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 15: e = run(int_kernel<15>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 16: e = run(int_kernel<16>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 9: e = run(int_kernel<9>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 10: e = run(int_kernel<10>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     default: e = run(ffma_kernel, sms, iters, ops_per_sec, ops_per_clk_sm); break;

@@ -62,7 +62,9 @@ constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel ha
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
 // Box-sum FRMC checks (T = 9)
-constexpr int BOX_MIN = 128;                  // listed pixels of one vector that pay for a box pass
+constexpr int BOX_MIN = 64;                   // listed pixels of one vector that pay for a box pass
+                                              // (1080p checks: 0.553 ms at 64 and 96, 0.559 at 128,
+                                              // 0.623 at 192)
 constexpr int HS = 2 * kMaxRadius + 1;        // side of the vector histogram
 
 // FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
@@ -170,56 +172,100 @@ struct Smem {
     uint2 csm[4 * CPYC];          // (masked samples, byte mask) words, byte-shifted copies
     uint32_t rf[4 * CPY];         // past frame (clamped coordinates), byte-shifted copies
     uint8_t nsrc[NS][NS];         // measured pixels in the template around each source
-    char2 mv[MT][MT];
-    char2 md[MD][MD];
+    uint32_t mv[MT][MT];          // ME field, (v_y + 16, v_x + 16) as 16-bit halves
+    uint32_t md[MD][MD];          // its 3x3 median, the same packing
     uint16_t list[TP * TP];       // tile pixels that need a reverse check
     uint8_t rej[TP * TP];
     CandOrder ord;                // reverse-check lane order of this tile's mode
     uint32_t e0n0[TP][TP];        // box checks: cost | count << 16 of d = 0 per tile pixel
-    uint32_t rejw[TP][TP / 4];    // box checks: rejected bits of each 4-pixel word
+    uint16_t ecand[NW][TP][TP];   // box checks: each warp's current candidate cost per tile pixel
+    uint16_t blist[TP * TP];      // box checks: listed pixels whose vector is the box vector
+    uint32_t rejb[32];            // box checks: rejected bits of blist entries e (word e % 32)
     int hist[HS * HS];            // listed pixels per filtered vector
     int boxv;                     // vector (histogram bin) checked by box sums, -1: none
     int nlist;
+    int nblist;
 };
 static_assert(offsetof(Smem, e0n0) % 16 == 0, "d = 0 costs are read in 16-byte words");
+static_assert(offsetof(Smem, ecand) % 8 == 0, "candidate costs are written in 8-byte words");
 
 static_assert(offsetof(Smem, ord) % 16 == 0, "the lane order is written in 16-byte words");
 
 __device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
 
-__device__ __forceinline__ void cswap(int &a, int &b)
+// Motion vectors in shared memory are (v_y + 16, v_x + 16) as the low and high 16-bit halves of
+// a word, so that the median and the neighbour test run on both components at once (min.u16x2 /
+// max.u16x2 are single instructions).  The offset keeps both halves positive, so subtracting
+// packed words never borrows across the halves; the median commutes with it.
+constexpr int MV_BIAS = 16;
+__device__ __forceinline__ uint32_t pack_mv(char2 c)
 {
-    const int lo = min(a, b), hi = max(a, b);
+    return (uint32_t)((int)c.x + MV_BIAS) | ((uint32_t)((int)c.y + MV_BIAS) << 16);
+}
+__device__ __forceinline__ int mv_y(uint32_t w) { return (int)(w & 0xffffu) - MV_BIAS; }
+__device__ __forceinline__ int mv_x(uint32_t w) { return (int)(w >> 16) - MV_BIAS; }
+__device__ __forceinline__ uint32_t pmin(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t pmax(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ void pswap(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = pmin(a, b), hi = pmax(a, b);
     a = lo;
     b = hi;
 }
-
-__device__ __forceinline__ int med3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
-
-// median of nine values: sort each group of three, then the median of (largest minimum,
-// median of medians, smallest maximum) -- exact for any input, ties included
-__device__ __forceinline__ int median9(int p0, int p1, int p2, int p3, int p4, int p5, int p6,
-                                       int p7, int p8)
+__device__ __forceinline__ uint32_t pmed3(uint32_t a, uint32_t b, uint32_t c)
 {
-    cswap(p0, p1); cswap(p1, p2); cswap(p0, p1);
-    cswap(p3, p4); cswap(p4, p5); cswap(p3, p4);
-    cswap(p6, p7); cswap(p7, p8); cswap(p6, p7);
-    const int lo = max(max(p0, p3), p6);
-    const int hi = min(min(p2, p5), p8);
-    return med3(lo, med3(p1, p4, p7), hi);
+    return pmax(pmin(a, b), pmin(pmax(a, b), c));
+}
+// component-wise median of nine packed vectors: sort each group of three, then the median of
+// (largest minimum, median of medians, smallest maximum) -- exact for any input, ties included
+__device__ __forceinline__ uint32_t pmedian9(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3,
+                                             uint32_t p4, uint32_t p5, uint32_t p6, uint32_t p7,
+                                             uint32_t p8)
+{
+    pswap(p0, p1); pswap(p1, p2); pswap(p0, p1);
+    pswap(p3, p4); pswap(p4, p5); pswap(p3, p4);
+    pswap(p6, p7); pswap(p7, p8); pswap(p6, p7);
+    const uint32_t lo = __vimax3_u16x2(p0, p3, p6);
+    const uint32_t hi = __vimin3_u16x2(p2, p5, p8);
+    return pmed3(lo, pmed3(p1, p4, p7), hi);
+}
+// |a_y - b_y| + |a_x - b_x| <= 1 for packed vectors: max - min per half is |a - b| (no borrow
+// between the halves: each half of the maximum is at least that of the minimum, as unsigned
+// numbers); times 0x10001 puts the sum of the halves in the high half
+__device__ __forceinline__ bool near1(uint32_t a, uint32_t b)
+{
+    const uint32_t d = pmax(a, b) - pmin(a, b);
+    return d * 0x10001u < 0x20000u;
 }
 
 // Stage the past frame around the tile (rows y0-HC.., cols x0-HC.., clamped coordinates) into
-// four byte-shifted copies: copy j, word w of a row holds region bytes 4w+j .. 4w+j+3.
+// four byte-shifted copies: copy j, word w of a row holds region bytes 4w+j .. 4w+j+3.  A word
+// inside the frame is one aligned 32-bit load when the rows are 4-byte aligned (the region starts
+// at a multiple of 4); words across a border take clamped bytes.
 __device__ void stage_past(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
 {
+    const bool al = (W & 3) == 0 && ((uintptr_t)src & 3) == 0;
     for (int i = threadIdx.x; i < RS * NWD; i += NT) {
         const int r = i / NWD, w = i - r * NWD;
         const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
         uint32_t v = 0;
         const uint8_t *row = src + (size_t)min(max(gy, 0), H - 1) * W;
+        if (al && gx >= 0 && gx + 4 <= W) {
+            v = *reinterpret_cast<const uint32_t *>(row + gx);
+        } else {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+            for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        }
         dst[r * RWD + w] = v;
     }
     __syncthreads();
@@ -237,19 +283,25 @@ __device__ void stage_past(uint32_t *dst, const uint8_t *__restrict__ src, int H
 __device__ void stage_current(uint2 *dst, const uint8_t *__restrict__ smp,
                               const uint8_t *__restrict__ msk, int H, int W, int y0, int x0)
 {
+    const bool al = (W & 3) == 0 && (((uintptr_t)smp | (uintptr_t)msk) & 3) == 0;
     for (int i = threadIdx.x; i < RS * NWD; i += NT) {
         const int r = i / NWD, w = i - r * NWD;
         const int gy = y0 - HC + r, gx = x0 - HC + 4 * w;
         uint32_t vs = 0, vm = 0;
         if (gy >= 0 && gy < H) {
-            // 16-bit loads: W is even and gx is even, so a pixel pair never straddles the border
             const size_t ro = (size_t)gy * W;
+            if (al && gx >= 0 && gx + 4 <= W) {          // one aligned word per plane
+                vs = *reinterpret_cast<const uint32_t *>(smp + ro + gx);
+                vm = *reinterpret_cast<const uint32_t *>(msk + ro + gx);
+            } else {
+                // 16-bit loads: W and gx are even, so a pixel pair never straddles the border
 #pragma unroll
-            for (int b = 0; b < 4; b += 2) {
-                const int x = gx + b;
-                if (x >= 0 && x < W) {
-                    vs |= (uint32_t)(*reinterpret_cast<const uint16_t *>(smp + ro + x)) << (8 * b);
-                    vm |= (uint32_t)(*reinterpret_cast<const uint16_t *>(msk + ro + x)) << (8 * b);
+                for (int b = 0; b < 4; b += 2) {
+                    const int x = gx + b;
+                    if (x >= 0 && x < W) {
+                        vs |= (uint32_t)(*reinterpret_cast<const uint16_t *>(smp + ro + x)) << (8 * b);
+                        vm |= (uint32_t)(*reinterpret_cast<const uint16_t *>(msk + ro + x)) << (8 * b);
+                    }
                 }
             }
         }
@@ -341,13 +393,16 @@ __device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy,
     }
 }
 
-// FRMC reverse checks by box sums for every tile pixel whose filtered vector is v (T = 9).  The
+// FRMC reverse checks by box sums for the listed pixels whose filtered vector is v (T = 9).  The
 // cost of candidate d at pixel p is C(p + d, v - d) = sum over o of F_d(p + o), a 9 x 9 box sum of
 // one plane per candidate: the same integers the per-pixel path adds up, so the decisions are
 // identical.  First each warp computes the d = 0 costs of 4 tile rows (lanes 0..9 hold the words)
-// and stores them with the template counts; then warp w takes candidates 1 + w, 9 + w, ... over
-// the whole tile (lane = 3 chunks of 11 rows x 10 words) and keeps the verdicts of its pixels as
-// bits; they are merged into rejw and written to sm.rej for the pixels with vector v.
+// and stores them with the template counts, while the listed pixels with vector v are collected;
+// then warp w takes candidates 1 + w, 9 + w, ... over the whole tile (lane = 3 chunks of 11 rows x
+// 10 words), writes the candidate's cost at every tile pixel to its own plane, and compares only
+// the collected pixels (at most a third of the unmeasured pixels of a tile are projectable, so a
+// quarter of the tile or less): lane l keeps the verdicts of entries l, l + 32, ... as bits.
+// They are merged over the warps and written to sm.rej for those pixels.
 __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy, int vx,
                             bool use_nnc)
 {
@@ -366,12 +421,20 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
                                (h02 >> 16) | (uint32_t)nr[2] << 16, (h13 >> 16) | (uint32_t)nr[3] << 16);
             }
         });
-        sm.rejw[tid >> 3][tid & 7] = 0;
+        if (tid < 32) sm.rejb[tid] = 0;
+        const int nl = sm.nlist;
+        for (int li = tid; li < nl; li += NT) {
+            const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
+            const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
+            if (mv_y(c) == vy && mv_x(c) == vx) sm.blist[atomicAdd(&sm.nblist, 1)] = (uint16_t)pi;
+        }
     }
     __syncthreads();
+    const int nb = sm.nblist;
     const int ch = min(lane / 10, 2), wi = lane < 30 ? lane - 10 * ch : 9;
     const bool out = lane < 30 && wi >= 1 && wi <= 8;
-    uint32_t rb0 = 0, rb1 = 0;                       // verdict bits: row j, pixel q at 4 j + q
+    uint32_t rej = 0;                                // bit i: entry lane + 32 i rejected
+    uint16_t (&ec)[TP][TP] = sm.ecand[warp];
     // instantiated for interior tiles (every source p + d in the frame) and for the others
     auto candidates = [&](auto inner_tag) {
         constexpr bool INNER = decltype(inner_tag)::value;
@@ -379,47 +442,30 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
             const int ci = i <= 24 ? i - 1 : i;      // the 48 offsets d != 0
             const int dy = frmc_offset(ci / 7), dx = frmc_offset(ci % 7);
             box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
-                const int r = 11 * ch + j, x = 4 * (wi - 1);
-                if (!out || r >= TP) return;
-                const uint4 z = *reinterpret_cast<const uint4 *>(&sm.e0n0[r][x]);
-                const uint32_t zz[4] = {z.x, z.y, z.z, z.w};
-                const int e[4] = {(int)(h02 & 0xffffu), (int)(h13 & 0xffffu), (int)(h02 >> 16),
-                                  (int)(h13 >> 16)};
-                const uint8_t *nr = &sm.nsrc[r + dy + kMaxRadius][x + dx + kMaxRadius];
-                uint32_t bits = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    bool valid = true;
-                    if constexpr (!INNER)
-                        valid = (unsigned)(y0 + r + dy) < (unsigned)H &&
-                                (unsigned)(x0 + x + q + dx) < (unsigned)W;
-                    const int c0 = (int)(zz[q] & 0xffffu), n0 = (int)(zz[q] >> 16);
-                    if (valid && e[q] * n0 < c0 * (int)nr[q]) bits |= 1u << q;
-                }
-                if (j < 8) rb0 |= bits << (4 * j);
-                else rb1 |= bits << (4 * (j - 8));
+                const int r = 11 * ch + j;
+                if (out && r < TP)                   // (H0, H1, H2, H3) of columns 4 (wi - 1) ..
+                    *reinterpret_cast<uint2 *>(&ec[r][4 * (wi - 1)]) =
+                        make_uint2(__byte_perm(h02, h13, 0x5410), __byte_perm(h02, h13, 0x7632));
             });
+            __syncwarp();
+            for (int e = lane, b = 0; e < nb; e += 32, ++b) {
+                const int pi = sm.blist[e], py = pi / TP, px = pi - py * TP;
+                bool valid = true;
+                if constexpr (!INNER)
+                    valid = (unsigned)(y0 + py + dy) < (unsigned)H && (unsigned)(x0 + px + dx) < (unsigned)W;
+                const uint32_t z = sm.e0n0[py][px];
+                const int ev = ec[py][px];
+                const int nr = sm.nsrc[py + dy + kMaxRadius][px + dx + kMaxRadius];
+                if (valid && ev * (int)(z >> 16) < (int)(z & 0xffffu) * nr) rej |= 1u << b;
+            }
+            __syncwarp();                            // the plane is rewritten by the next candidate
         }
     };
     if (inner) candidates(std::true_type{});
     else candidates(std::false_type{});
-    if (out) {
-#pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const int r = 11 * ch + j;
-            const uint32_t bits = (j < 8 ? rb0 >> (4 * j) : rb1 >> (4 * (j - 8))) & 15u;
-            if (r < TP && bits) atomicOr(&sm.rejw[r][wi - 1], bits);
-        }
-    }
+    if (rej) atomicOr(&sm.rejb[lane], rej);
     __syncthreads();
-    const int pr = tid >> 3, pw = tid & 7;
-    const uint32_t bits = sm.rejw[pr][pw];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int px = 4 * pw + q;
-        const char2 c = use_nnc ? sm.md[pr + 1][px + 1] : sm.mv[pr + 2][px + 2];
-        if (c.x == vy && c.y == vx) sm.rej[pr * TP + px] = (bits >> q) & 1u;
-    }
+    for (int e = tid; e < nb; e += NT) sm.rej[sm.blist[e]] = (sm.rejb[e & 31] >> (e >> 5)) & 1u;
 }
 
 template <int T>
@@ -442,21 +488,33 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
     }
     stage_current(sm.csm, t.cur_smp, t.cur_msk, H, W, y0, x0);
     __syncthreads();
-    // template counts n around every source position of the tile +- 9 (current mask, 0 outside)
-    for (int i = tid; i < NS * NS; i += NT) {
-        const int sy = i / NS, sx = i - sy * NS;
-        const int ry = sy + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
-        int n = 0;
-        for (int r = 0; r < T; ++r) {
-            const uint2 *cm = sm.csm + (rx & 3) * CPYC + (ry + r) * RWDC + (rx >> 2);
+    // template counts n around every source position of the tile +- 9 (current mask, 0 outside),
+    // separably: T-column counts of every staged row the sources need, then T-row sums of those
+    {
+        constexpr int HR = NS + T - 1;                     // staged rows the sources' templates span
+        static_assert(HR * NS <= (int)sizeof(sm.e0n0), "row counts fit the box-check buffer");
+        uint8_t *hc = reinterpret_cast<uint8_t *>(sm.e0n0);   // unused until the checks
+        for (int i = tid; i < HR * NS; i += NT) {
+            const int r = i / NS, sx = i - r * NS;
+            const int ry = r + HC - kMaxRadius - h, rx = sx + HC - kMaxRadius - h;
+            const uint2 *cm = sm.csm + (rx & 3) * CPYC + ry * RWDC + (rx >> 2);
+            int n = 0;
 #pragma unroll
             for (int b = 0; b < (T + 3) / 4; ++b) {
                 uint32_t m = cm[b].y;
                 if (4 * b + 4 > T) m &= (1u << (8 * (T - 4 * b))) - 1u;
                 n += __popc(m);
             }
+            hc[i] = (uint8_t)(n >> 3);
         }
-        sm.nsrc[sy][sx] = (uint8_t)(n >> 3);
+        __syncthreads();
+        for (int i = tid; i < NS * NS; i += NT) {
+            const int sy = i / NS, sx = i - sy * NS;
+            int n = 0;
+#pragma unroll
+            for (int r = 0; r < T; ++r) n += hc[(sy + r) * NS + sx];
+            sm.nsrc[sy][sx] = (uint8_t)n;
+        }
     }
 
     int sum[PPT], cnt[PPT];
@@ -469,7 +527,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         for (int i = tid; i < MT * MT; i += NT) {
             const int r = i / MT, c = i - r * MT;
             const int gy = min(max(y0 - 2 + r, 0), H - 1), gx = min(max(x0 - 2 + c, 0), W - 1);
-            sm.mv[r][c] = mvk[(size_t)gy * W + gx];
+            sm.mv[r][c] = pack_mv(mvk[(size_t)gy * W + gx]);
         }
         if (tid == 0) sm.nlist = 0;
         if (frmc || rmc) stage_past(sm.rf, t.ref_rec[k], H, W, y0, x0);
@@ -477,77 +535,92 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         if (use_nnc) {
             for (int i = tid; i < MD * MD; i += NT) {
                 const int r = i / MD, c = i - r * MD;
-                const char2 a0 = sm.mv[r][c], a1 = sm.mv[r][c + 1], a2 = sm.mv[r][c + 2];
-                const char2 a3 = sm.mv[r + 1][c], a4 = sm.mv[r + 1][c + 1], a5 = sm.mv[r + 1][c + 2];
-                const char2 a6 = sm.mv[r + 2][c], a7 = sm.mv[r + 2][c + 1], a8 = sm.mv[r + 2][c + 2];
-                const int my = median9(a0.x, a1.x, a2.x, a3.x, a4.x, a5.x, a6.x, a7.x, a8.x);
-                const int mx = median9(a0.y, a1.y, a2.y, a3.y, a4.y, a5.y, a6.y, a7.y, a8.y);
-                sm.md[r][c] = make_char2((signed char)my, (signed char)mx);
+                sm.md[r][c] = pmedian9(sm.mv[r][c], sm.mv[r][c + 1], sm.mv[r][c + 2],
+                                       sm.mv[r + 1][c], sm.mv[r + 1][c + 1], sm.mv[r + 1][c + 2],
+                                       sm.mv[r + 2][c], sm.mv[r + 2][c + 1], sm.mv[r + 2][c + 2]);
             }
             __syncthreads();
         }
-        // decide every pixel; list the ones that need a reverse check
+        // decide every pixel; list the ones that need a reverse check.  First the filtered vector,
+        // the NNC verdict and q = p + v of all pixels of the thread, with the loads of the past
+        // mask at q (and of the reverse field in RME mode) issued together; then the decisions.
         uint8_t dec[PPT];
         int qv[PPT];
+        uint32_t fv[PPT];
+        bool pass[PPT], meas[PPT], pend[PPT];
+        uint8_t qm[PPT];
+        char2 rw[PPT];
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
             const int pi = tid + i * NT, py = pi / TP, px = pi - py * TP;
             const int y = y0 + py, x = x0 + px;
-            dec[i] = 255;
             qv[i] = -1;
+            pend[i] = false;
+            pass[i] = true;
+            meas[i] = false;
+            qm[i] = 0;
             if (y >= H || x >= W) continue;
-            int fy, fx;
-            bool pass = true;
+            uint32_t c;
             if (use_nnc) {
-                const char2 c = sm.md[py + 1][px + 1];
-                fy = c.x;
-                fx = c.y;
+                c = sm.md[py + 1][px + 1];
                 const int nb[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int yy = y + nb[j][0], xx = x + nb[j][1];
                     if ((unsigned)yy >= (unsigned)H || (unsigned)xx >= (unsigned)W) continue;
-                    const char2 u = sm.md[py + 1 + nb[j][0]][px + 1 + nb[j][1]];
-                    if (iabs(fy - u.x) + iabs(fx - u.y) > 1) pass = false;
+                    if (!near1(c, sm.md[py + 1 + nb[j][0]][px + 1 + nb[j][1]])) pass[i] = false;
                 }
             } else {
-                const char2 c = sm.mv[py + 2][px + 2];
-                fy = c.x;
-                fx = c.y;
+                c = sm.mv[py + 2][px + 2];
             }
+            fv[i] = c;
+            const int fy = mv_y(c), fx = mv_x(c);
             const size_t gi = (size_t)y * W + x;
             reinterpret_cast<char2 *>(t.fmv[k])[gi] = make_char2((signed char)fy, (signed char)fx);
             const int qy = y + fy, qx = x + fx;
             const uint32_t mword = sm.csm[(py + HC) * RWDC + ((px + HC) >> 2)].y;
-            const bool measured = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
-            if (measured) {
-                dec[i] = 0;
-            } else if ((unsigned)qy >= (unsigned)H || (unsigned)qx >= (unsigned)W ||
-                       !t.ref_msk[k][(size_t)qy * W + qx]) {
-                dec[i] = 1;
-            } else if (use_nnc && !pass) {
-                dec[i] = 2;
-            } else {
+            meas[i] = ((mword >> (8 * ((px + HC) & 3))) & 0xffu) != 0;
+            if (!meas[i] && (unsigned)qy < (unsigned)H && (unsigned)qx < (unsigned)W) {
                 qv[i] = qy * W + qx;
-                if (rme) {
-                    const char2 w = reinterpret_cast<const char2 *>(t.rmv[k])[(size_t)qy * W + qx];
-                    dec[i] = (w.x == -fy && w.y == -fx) ? 4 : 3;
-                } else if (frmc || rmc) {
-                    dec[i] = 254;                               // pending reverse check
-                    sm.rej[pi] = 0;
-                    sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)pi;
-                } else {
-                    dec[i] = 4;
-                }
+                qm[i] = t.ref_msk[k][qv[i]];
+                if (rme) rw[i] = reinterpret_cast<const char2 *>(t.rmv[k])[qv[i]];
             }
+        }
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const int pi = tid + i * NT, py = pi / TP, px = pi - py * TP;
+            dec[i] = 255;
+            if (y0 + py >= H || x0 + px >= W) continue;
+            if (meas[i]) {
+                dec[i] = 0;
+            } else if (qv[i] < 0 || !qm[i]) {
+                dec[i] = 1;
+                qv[i] = -1;
+            } else if (use_nnc && !pass[i]) {
+                dec[i] = 2;
+            } else if (rme) {
+                dec[i] = (rw[i].x == -mv_y(fv[i]) && rw[i].y == -mv_x(fv[i])) ? 4 : 3;
+            } else if (frmc || rmc) {
+                dec[i] = 254;                                   // pending reverse check
+                pend[i] = true;
+            } else {
+                dec[i] = 4;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            if (!pend[i]) continue;
+            const int pi = tid + i * NT;
+            sm.rej[pi] = 0;
+            sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)pi;
         }
         __syncthreads();
         const int nl = sm.nlist;
         // FRMC, T = 9: box-sum checks for the vector that most listed pixels share, if at least
-        // BOX_MIN do.  The cost of a candidate over the whole tile is one box sum, so the 49 candidates
-        // cost about as much as 130 per-pixel checks.  Under quarter sampling at most a third of
-        // the unmeasured pixels of a tile are projectable per past frame (256), so one vector at
-        // most pays for it in practice.  RMC stays per pixel: its 289 candidates make the box
+        // BOX_MIN do.  The cost of a candidate over the whole tile is one box sum, so the 49
+        // candidates cost about as much as 70 per-pixel checks.  Under quarter sampling at most a
+        // third of the unmeasured pixels of a tile are projectable per past frame (256), so one
+        // vector pays for it in most tiles.  RMC stays per pixel: its 289 candidates make the box
         // pass dearer than per-pixel checks, which stop at the first better candidate.
         int boxbin = -1;
         if constexpr (T == 9) {
@@ -556,8 +629,8 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                 __syncthreads();
                 for (int li = tid; li < nl; li += NT) {
                     const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
-                    const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
-                    atomicAdd(&sm.hist[(c.x + kMaxRadius) * HS + c.y + kMaxRadius], 1);
+                    const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
+                    atomicAdd(&sm.hist[(mv_y(c) + kMaxRadius) * HS + mv_x(c) + kMaxRadius], 1);
                 }
                 __syncthreads();
                 if (warp == 0) {                                  // the most frequent bin
@@ -565,7 +638,10 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                     for (int i = lane; i < HS * HS; i += 32)
                         key = max(key, ((uint32_t)sm.hist[i] << 10) | (1023u - i));
                     key = __reduce_max_sync(0xffffffffu, key);
-                    if (lane == 0) sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
+                    if (lane == 0) {
+                        sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
+                        sm.nblist = 0;
+                    }
                 }
                 __syncthreads();
                 boxbin = sm.boxv;
@@ -577,8 +653,8 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         // reverse checks of the other listed pixels: one warp per pixel
         for (int li = warp; li < nl; li += NW) {
             const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
-            const char2 c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
-            const int fy = c.x, fx = c.y;
+            const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
+            const int fy = mv_y(c), fx = mv_x(c);
             if ((fy + kMaxRadius) * HS + fx + kMaxRadius == boxbin) continue;   // done above
             uint32_t P[T][3];                          // past-frame patch around q
             {
