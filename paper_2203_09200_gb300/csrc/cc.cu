@@ -66,6 +66,7 @@ constexpr int BOX_MIN = 64;                   // listed pixels of one vector tha
                                               // (1080p checks: 0.553 ms at 64 and 96, 0.559 at 128,
                                               // 0.623 at 192)
 constexpr int HS = 2 * kMaxRadius + 1;        // side of the vector histogram
+constexpr int NLMAX = TP * TP * 3 / 4;        // listed pixels of a tile at most (the unmeasured)
 
 // FRMC offsets {-7,-3,-1,0,1,3,7}[i] (Sec. 3.1.1): 0 at i = 3, +-(2^|i-3| - 1) elsewhere
 __host__ __device__ constexpr int frmc_offset(int i)
@@ -180,6 +181,8 @@ struct Smem {
     uint32_t e0n0[TP][TP];        // box checks: cost | count << 16 of d = 0 per tile pixel
     uint16_t ecand[NW][TP][TP];   // box checks: each warp's current candidate cost per tile pixel
     uint16_t blist[TP * TP];      // box checks: listed pixels whose vector is the box vector
+    uint32_t be0n0[NLMAX];        // box checks: e0n0 of entry e (read without bank conflicts)
+    uint16_t bnoff[NLMAX];        // box checks: offset of entry e's own source in nsrc
     uint32_t rejb[32];            // box checks: rejected bits of blist entries e (word e % 32)
     int hist[HS * HS];            // listed pixels per filtered vector
     int boxv;                     // vector (histogram bin) checked by box sums, -1: none
@@ -431,10 +434,17 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
     }
     __syncthreads();
     const int nb = sm.nblist;
+    for (int e = tid; e < nb; e += NT) {             // per-entry copies for the compares below
+        const int pi = sm.blist[e], py = pi / TP, px = pi - py * TP;
+        sm.be0n0[e] = sm.e0n0[py][px];
+        sm.bnoff[e] = (uint16_t)((py + kMaxRadius) * NS + px + kMaxRadius);
+    }
+    __syncthreads();
     const int ch = min(lane / 10, 2), wi = lane < 30 ? lane - 10 * ch : 9;
     const bool out = lane < 30 && wi >= 1 && wi <= 8;
     uint32_t rej = 0;                                // bit i: entry lane + 32 i rejected
-    uint16_t (&ec)[TP][TP] = sm.ecand[warp];
+    const uint16_t *ec = &sm.ecand[warp][0][0];
+    const uint8_t *ns = &sm.nsrc[0][0];
     // instantiated for interior tiles (every source p + d in the frame) and for the others
     auto candidates = [&](auto inner_tag) {
         constexpr bool INNER = decltype(inner_tag)::value;
@@ -444,18 +454,21 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
             box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
                 const int r = 11 * ch + j;
                 if (out && r < TP)                   // (H0, H1, H2, H3) of columns 4 (wi - 1) ..
-                    *reinterpret_cast<uint2 *>(&ec[r][4 * (wi - 1)]) =
+                    *reinterpret_cast<uint2 *>(&sm.ecand[warp][r][4 * (wi - 1)]) =
                         make_uint2(__byte_perm(h02, h13, 0x5410), __byte_perm(h02, h13, 0x7632));
             });
             __syncwarp();
+            const int doff = dy * NS + dx;
             for (int e = lane, b = 0; e < nb; e += 32, ++b) {
-                const int pi = sm.blist[e], py = pi / TP, px = pi - py * TP;
+                const int pi = sm.blist[e];
                 bool valid = true;
-                if constexpr (!INNER)
+                if constexpr (!INNER) {
+                    const int py = pi / TP, px = pi - py * TP;
                     valid = (unsigned)(y0 + py + dy) < (unsigned)H && (unsigned)(x0 + px + dx) < (unsigned)W;
-                const uint32_t z = sm.e0n0[py][px];
-                const int ev = ec[py][px];
-                const int nr = sm.nsrc[py + dy + kMaxRadius][px + dx + kMaxRadius];
+                }
+                const uint32_t z = sm.be0n0[e];
+                const int ev = ec[pi];
+                const int nr = ns[sm.bnoff[e] + doff];
                 if (valid && ev * (int)(z >> 16) < (int)(z & 0xffffu) * nr) rej |= 1u << b;
             }
             __syncwarp();                            // the plane is rewritten by the next candidate

@@ -174,8 +174,8 @@ constexpr int S_OUTW = 120;                // output columns per CTA
 constexpr int S_DROWS = S_ROWS + 8;        // D rows per warp (T = 9)
 constexpr int S_RWORDS = (128 + 2 * kMaxRadius + 3) / 4 + 1;   // words per staged row
 template <int WARPS> __host__ __device__ constexpr int s_nt() { return 32 * WARPS; }
-template <int WARPS> __host__ __device__ constexpr int s_outh() { return S_ROWS * WARPS; }          // tile rows
-template <int WARPS> __host__ __device__ constexpr int s_rrows() { return S_ROWS * WARPS + 8 + 2 * kMaxRadius; }
+template <int WARPS, int ROWS = S_ROWS> __host__ __device__ constexpr int s_outh() { return ROWS * WARPS; }   // tile rows
+template <int WARPS, int ROWS = S_ROWS> __host__ __device__ constexpr int s_rrows() { return ROWS * WARPS + 8 + 2 * kMaxRadius; }
 
 // lane masks from the guard bits of a packed pair: 0xffff in each 16-bit lane whose bit 15 (lo)
 // or bit 31 (hi) is set (prmt's default mode replicates the sign bit when a selector's msb is set)
@@ -198,16 +198,17 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c)
 
 // The staged past-frame window in four byte-shifted copies: copy j, word w of a row holds row
 // bytes 4 w + j .. 4 w + j + 3, so the word a lane compares at any column is one aligned load.
-template <int WARPS>
+template <int WARPS, int ROWS = S_ROWS>
 struct Smem9 {
-    uint32_t rf[4][s_rrows<WARPS>() * S_RWORDS];
+    uint32_t rf[4][s_rrows<WARPS, ROWS>() * S_RWORDS];
     short2 vord[NVMAX];
 };
 
-template <int WARPS>
-__device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, int tbx, int tby, int k)
+template <int WARPS, int ROWS = S_ROWS>
+__device__ __forceinline__ void me9_tile(Smem9<WARPS, ROWS> &sm, const FrameTask &t, int tbx, int tby, int k)
 {
-    constexpr int S_NT = s_nt<WARPS>(), S_OUTH = s_outh<WARPS>();
+    constexpr int S_NT = s_nt<WARPS>(), S_OUTH = s_outh<WARPS, ROWS>();
+    constexpr int DROWS = ROWS + 8;                       // D rows per warp (T = 9)
     const int x0 = tbx * S_OUTW, y0 = tby * S_OUTH;
     const int H = t.H, W = t.W, R = t.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -238,12 +239,12 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
     // current frame: this lane's 16 rows of 4 columns (masked samples, byte masks; 0 outside),
     // one aligned 32-bit load per plane and row where the word lies inside a 4-byte aligned frame
     const int cx = x0 - 4 + 4 * lane;                     // first column of the lane's word
-    const int cy0 = y0 + S_ROWS * warp - 4;               // first D row of the warp
+    const int cy0 = y0 + ROWS * warp - 4;               // first D row of the warp
     const bool al_cur = (W & 3) == 0 && (((uintptr_t)t.cur_smp | (uintptr_t)t.cur_msk) & 3) == 0 &&
                         cx >= 0 && cx + 4 <= W;           // cx is a multiple of 4
-    uint32_t cs[S_DROWS], cmk[S_DROWS];
+    uint32_t cs[DROWS], cmk[DROWS];
 #pragma unroll
-    for (int i = 0; i < S_DROWS; ++i) {
+    for (int i = 0; i < DROWS; ++i) {
         const int y = cy0 + i;
         uint32_t a = 0, m = 0;
         if (y >= 0 && y < H) {
@@ -277,14 +278,14 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
 
     // border handling: candidates with p + v outside the frame are not allowed
     const bool border = (x0 - 4 - R < 0) || (x0 + 124 + R > W) || (y0 - R < 0) || (y0 + S_OUTH + R > H);
-    uint32_t best02[S_ROWS], best13[S_ROWS], idx02[S_ROWS], idx13[S_ROWS];
+    uint32_t best02[ROWS], best13[ROWS], idx02[ROWS], idx13[ROWS];
 #pragma unroll
-    for (int j = 0; j < S_ROWS; ++j) {
+    for (int j = 0; j < ROWS; ++j) {
         best02[j] = best13[j] = 0x7fff7fffu;
         idx02[j] = idx13[j] = 0u;
     }
     const int nv = (2 * R + 1) * (2 * R + 1);
-    const int oy = y0 + S_ROWS * warp;                     // first output row of the warp
+    const int oy = y0 + ROWS * warp;                     // first output row of the warp
     const uint32_t one = (uint32_t)(W > 0), m1 = 0u - one;  // 1 and -1 (W > 0 always)
     // the candidate loop, instantiated for border CTAs (some p + v outside the frame) and for
     // interior ones (no invalid-column or invalid-row masking at all)
@@ -294,7 +295,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
             const short2 v = sm.vord[o];
             const int vy = v.x, vx = v.y;
             const int sh = (vx + R) & 3, q = (vx + R) >> 2;
-            const uint32_t *rrow = sm.rf[sh] + (S_ROWS * warp + vy + R) * S_RWORDS + lane + q;
+            const uint32_t *rrow = sm.rf[sh] + (ROWS * warp + vy + R) * S_RWORDS + lane + q;
             uint32_t inv02 = 0, inv13 = 0;                     // lanes of invalid columns -> 0x7fff
             if constexpr (BORDER) {
                 const int c0 = cx + vx;
@@ -304,10 +305,10 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
                         ((unsigned)(c0 + 3) >= (unsigned)W ? 0x7fff0000u : 0u);
             }
             uint32_t lo = 0, hi = 0;                           // vertical sums, columns (0,2) (1,3)
-            uint32_t dlo[S_DROWS], dhi[S_DROWS];
+            uint32_t dlo[DROWS], dhi[DROWS];
             const uint32_t o2 = (uint32_t)o * 0x00010001u;
     #pragma unroll
-            for (int i = 0; i < S_DROWS; ++i) {
+            for (int i = 0; i < DROWS; ++i) {
                 const uint32_t d4 = __vabsdiffu4(cs[i], rrow[i * S_RWORDS]) & cmk[i];
                 dlo[i] = __byte_perm(d4, 0u, 0x4240);
                 dhi[i] = __byte_perm(d4, 0u, 0x4341);
@@ -348,7 +349,7 @@ __device__ __forceinline__ void me9_tile(Smem9<WARPS> &sm, const FrameTask &t, i
     if (lane == 0 || lane == 31) return;
     char2 *mv = reinterpret_cast<char2 *>(t.mv[k]);
 #pragma unroll
-    for (int j = 0; j < S_ROWS; ++j) {
+    for (int j = 0; j < ROWS; ++j) {
         const int y = oy + j;
         if (y >= H) continue;
         const uint32_t id[4] = {idx02[j] & 0xffffu, idx13[j] & 0xffffu, idx02[j] >> 16, idx13[j] >> 16};
@@ -369,15 +370,19 @@ __global__ void __launch_bounds__(NT) me_kernel(FrameTask t)
     me_tile(sm, t, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// Warp strips per CTA of the single-stream launch: 4 (32-row tiles, four CTAs per SM) measured
-// 0.672 ms per 1080p frame against 0.716 (8), 0.728 (6), 0.712 (5) and 0.696 (3).
+// Tile of the single-stream launch: 4 warp strips of 8 rows (32-row tiles, four CTAs per SM)
+// measured 0.672 ms per 1080p frame, against 0.716 / 0.728 / 0.712 / 0.696 ms for 8 / 6 / 5 / 3
+// strips of 8 rows, and 0.83 - 1.0 ms for strips of 12 or 16 rows (168 registers, 12 warps per
+// SM).
 constexpr int kMeWarps = 4;
+constexpr int kMeRows = 8;                   // output rows per warp strip
+constexpr int kMeMinBlocks = 16 / kMeWarps;  // resident CTAs the register budget is set for
 
-__global__ void __launch_bounds__(s_nt<kMeWarps>(), 16 / kMeWarps) me9_kernel(FrameTask t)
+__global__ void __launch_bounds__(s_nt<kMeWarps>(), kMeMinBlocks) me9_kernel(FrameTask t)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    me9_tile<kMeWarps>(*reinterpret_cast<Smem9<kMeWarps> *>(smem_raw), t, blockIdx.x, blockIdx.y,
-                       blockIdx.z);
+    me9_tile<kMeWarps, kMeRows>(*reinterpret_cast<Smem9<kMeWarps, kMeRows> *>(smem_raw), t,
+                                blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // batched forms on the tile queue: tiles of a task flattened as (k, by, bx), bx fastest
@@ -603,7 +608,7 @@ cudaError_t init_me(int dev)
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (ready[dev]) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(me9_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem9<kMeWarps>));
+                                         (int)sizeof(Smem9<kMeWarps, kMeRows>));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(me9_batched_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(Smem9<8>));
@@ -630,8 +635,9 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = init_me(dev);
         if (e != cudaSuccess) return e;
-        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + s_outh<kMeWarps>() - 1) / s_outh<kMeWarps>(), t.K);
-        me9_kernel<<<grid, s_nt<kMeWarps>(), sizeof(Smem9<kMeWarps>), st>>>(t);
+        constexpr int outh = s_outh<kMeWarps, kMeRows>();
+        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + outh - 1) / outh, t.K);
+        me9_kernel<<<grid, s_nt<kMeWarps>(), sizeof(Smem9<kMeWarps, kMeRows>), st>>>(t);
     } else {
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);
