@@ -338,7 +338,7 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     constexpr uint32_t w1 = T >= 8 ? 0xffffffffu : (T > 4 ? (1u << (8 * (T - 4))) - 1u : 0u);
     constexpr uint32_t w2 = T >= 12 ? 0xffffffffu : (T > 8 ? (1u << (8 * (T - 8))) - 1u : 0u);
     const int j = sx & 3, w = sx >> 2;
-    int acc = 0;
+    int acc = 0, acc1 = 0, acc2 = 0;          // one chain per template word: shorter latency
 #pragma unroll
     for (int r = 0; r < T; ++r) {
         const uint2 *c = sm.csm + j * CPYC + (sy + r) * RWDC + w;
@@ -346,14 +346,14 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
         acc = sad4_acc(c0.x & w0, P[r][0] & c0.y & w0, acc);
         if (w1) {
             const uint2 c1 = c[1];
-            acc = sad4_acc(c1.x & w1, P[r][1] & c1.y & w1, acc);
+            acc1 = sad4_acc(c1.x & w1, P[r][1] & c1.y & w1, acc1);
         }
         if (w2) {
             const uint2 c2 = c[2];
-            acc = sad4_acc(c2.x & w2, P[r][2] & c2.y & w2, acc);
+            acc2 = sad4_acc(c2.x & w2, P[r][2] & c2.y & w2, acc2);
         }
     }
-    return acc;
+    return acc + acc1 + acc2;
 }
 
 // Box sums of F_d over the tile for one candidate d (T = 9).  F_d(y) = b_t(y + d) |s_t(y + d) -
@@ -459,6 +459,7 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
             });
             __syncwarp();
             const int doff = dy * NS + dx;
+#pragma unroll 4
             for (int e = lane, b = 0; e < nb; e += 32, ++b) {
                 const int pi = sm.blist[e];
                 bool valid = true;
