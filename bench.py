@@ -433,6 +433,17 @@ def run_concealed(rfsr, torch, delta=0.5, frames=3):
     return res
 
 
+def run_serving_all(rfsr, torch, frame_scale=0.1):
+    """The serving report: paced cameras first (the latency a stream sees below saturation), then
+    the saturated closed loop with the whole memory and under a 2 GB budget, then the unloaded
+    service time per size."""
+    return {"paced_30fps": run_serving(rfsr, torch, n_streams=64, rate_hz=5.0, pace_fps=30.0,
+                                       frame_scale=frame_scale),
+            "closed_loop": run_serving(rfsr, torch, frame_scale=frame_scale),
+            "budget_2gb": run_serving(rfsr, torch, memory_budget=2 << 30, frame_scale=frame_scale),
+            "unloaded": run_unloaded_latency(rfsr, torch)}
+
+
 def run_unloaded_latency(rfsr, torch, frames=12):
     """Per-frame latency of the serving engine with one stream alone and one frame in flight
     (host buffers, push -> collected), per size of the arrival mix: the service time that the
@@ -468,25 +479,28 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
     import time as _t
     arr = synth.config5_arrivals(seed=seed, n_streams=n_streams, rate_hz=rate_hz)
     nf = [max(2, int(round(a.spec.frames * frame_scale))) for a in arr]
-    # shared content per size: the 1/f^2 + moving objects recipe at the largest size, cropped
-    base = synth.config3(seed=55, H=2160, W=3840, F=8)
-    content = {}
-    for (H, W) in SIZES5:
-        content[(H, W)] = [np.ascontiguousarray(base.frames[t, :H, :W]) for t in range(8)]
-    # masks and sample planes shared by the streams of one (size, mask type) class
-    cls = {}
-    for (H, W) in SIZES5:
-        for mt in (synth.MASK_FIXED, synth.MASK_DYNAMIC):
-            rng = np.random.default_rng(H * 7 + W + mt)
-            if mt == synth.MASK_FIXED:
-                ms = [synth.positions_to_mask(synth.fixed_positions(H, W, rng))]
-            else:
-                perm = synth.dynamic_permutations(H, W, rng)
-                ms = [synth.positions_to_mask(synth.dynamic_positions(perm, t)) for t in range(4)]
-            sm = [np.ascontiguousarray(content[(H, W)][t] * ms[t % len(ms)]) for t in range(8)]
-            cls[(H, W, mt)] = (sm, ms)
-    masks = {i: cls[(a.spec.H, a.spec.W, a.spec.mask_type)][1] for i, a in enumerate(arr)}
-    samples = {i: cls[(a.spec.H, a.spec.W, a.spec.mask_type)][0] for i, a in enumerate(arr)}
+    # content: the 1/f^2 + moving objects recipe at the largest size; every stream is a crop at
+    # its own seeded offset, starting at its own seeded frame, with its own seeded mask(s).  The
+    # frame is pushed whole as the sample plane (the library ignores unmeasured bytes).
+    nbase = 16
+    base = synth.config3(seed=55, H=2160, W=3840, F=nbase)
+    crops, masks = {}, {}
+    for i, a in enumerate(arr):
+        sp = a.spec
+        rng = np.random.default_rng(sp.seed)
+        y0 = int(rng.integers(0, 2160 - sp.H + 1)) & ~1
+        x0 = int(rng.integers(0, 3840 - sp.W + 1)) & ~1
+        crops[i] = (y0, x0, int(rng.integers(0, nbase)))
+        if sp.mask_type == synth.MASK_FIXED:
+            masks[i] = [synth.positions_to_mask(synth.fixed_positions(sp.H, sp.W, rng))]
+        else:
+            perm = synth.dynamic_permutations(sp.H, sp.W, rng)
+            masks[i] = [synth.positions_to_mask(synth.dynamic_positions(perm, t)) for t in range(4)]
+
+    def frame_of(i, n):
+        y0, x0, t0 = crops[i]
+        sp = arr[i].spec
+        return base.frames[(t0 + n) % nbase, y0:y0 + sp.H, x0:x0 + sp.W]
     eng = rfsr.Engine(device=torch.cuda.current_device(), serve=True, max_inflight=2,
                       memory_budget=memory_budget)
     n_queued, max_queue = 0, 0
@@ -515,8 +529,7 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             st, sent, inflight, t0 = active[i]
             due = pace_fps <= 0 or _t.perf_counter() - t0 >= sent / pace_fps
             if sent < nf[i] and len(inflight) < 2 and due:
-                k = sent % 8
-                st.push_frame(samples[i][k], masks[i][k % len(masks[i])])
+                st.push_frame(frame_of(i, sent), masks[i][sent % len(masks[i])])
                 inflight.append(_t.perf_counter())
                 active[i][1] = sent + 1
             if inflight:
@@ -543,9 +556,11 @@ def run_serving(rfsr, torch, n_streams=256, rate_hz=20.0, frame_scale=0.1, seed=
             "memory_budget": memory_budget or "80% of free device memory",
             "streams_queued": n_queued, "max_queue": max_queue,
             "workload": (f"{n_streams} streams arriving Poisson at {rate_hz:g}/s, sizes "
-                         "320x240..3840x2160, fixed or dynamic mask 50/50, 1/f^2 texture + "
-                         f"moving objects, frames U{{30..300}} x {frame_scale:g}, {loop}, host "
-                         "buffers, serving engine (continuous batching, memory admission)")}
+                         "320x240..3840x2160, fixed or dynamic mask 50/50 (seeded per stream), "
+                         "1/f^2 texture + moving objects (each stream its own seeded crop and "
+                         f"start frame of a 16-frame 4K sequence), frames U{{30..300}} x "
+                         f"{frame_scale:g}, {loop}, host buffers, serving engine (continuous "
+                         "batching, memory admission)")}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -750,10 +765,7 @@ def run_ours(args, rank, world, local_rank):
         batching = run_batching(rfsr, torch)
         batching["small_frames"] = run_batching(
             rfsr, torch, small_streams(), what="256 streams of 320x240, half fixed / half dynamic masks")
-        serving = run_serving(rfsr, torch)
-        serving["budget_2gb"] = run_serving(rfsr, torch, memory_budget=2 << 30)
-        serving["paced_30fps"] = run_serving(rfsr, torch, n_streams=64, rate_hz=5.0, pace_fps=30.0)
-        serving["unloaded"] = run_unloaded_latency(rfsr, torch)
+        serving = run_serving_all(rfsr, torch)
         check_modes = run_check_modes(rfsr, torch)
         concealed = run_concealed(rfsr, torch)
 
@@ -923,6 +935,9 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--streams", type=int, default=64, help="streams of --ncu-case batched")
     ap.add_argument("--cc-mode", default="nnc_frmc", choices=list(MODES),
                     help="consistency-check mode of --ncu-case frame_step")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="print the serving report with every stream's full U{30..300} frames and "
+                         "exit (the default run plays a tenth of each stream's frames)")
     ap.add_argument("--quality", action="store_true",
                     help="print the reconstruction-quality table (PSNR / SSIM per method) and exit")
     ap.add_argument("--summarize-launches", metavar="CSV",
@@ -938,6 +953,15 @@ def main():
         return
     if args.ncu_case:
         run_ncu_case(args)
+        return
+    if args.serving_full:
+        import torch
+        from paper_2203_09200_gb300 import build as pbuild
+        from paper_2203_09200_gb300 import rfsr
+        torch.cuda.set_device(0)
+        pbuild.build()
+        print(json.dumps({"serving_full": run_serving_all(rfsr, torch, frame_scale=1.0)}),
+              flush=True)
         return
     if args.quality:
         import torch

@@ -64,6 +64,7 @@ __device__ __forceinline__ uint32_t op_chain(int i, uint32_t a, uint32_t b, uint
     else if constexpr (OP == 14) return min_s16x2(a, b);
     else if constexpr (OP == 15) return sad2_acc(a, b, c);
     else if constexpr (OP == 16) return (uint32_t)__vimax3_s16x2((int)a, (int)b, (int)c);
+    else if constexpr (OP == 17) return __vimax3_u32(a, b, c);
     else return op<OP>(a, b, c);
 }
 
@@ -158,7 +159,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
                              double *ops_per_clk_sm)
 {
     using namespace rfsr;
-    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 16)
+    if (!ops_per_sec || !ops_per_clk_sm || iters <= 0 || kind < 0 || kind > 17)
         return RFSR_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess) return RFSR_EDEVICE;
     int sms = 0;
@@ -180,6 +181,7 @@ extern "C" int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_se
     case 14: e = run(int_kernel<14>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 15: e = run(int_kernel<15>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 16: e = run(int_kernel<16>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
+    case 17: e = run(int_kernel<17>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 9: e = run(int_kernel<9>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     case 10: e = run(int_kernel<10>, sms, iters, ops_per_sec, ops_per_clk_sm); break;
     default: e = run(ffma_kernel, sms, iters, ops_per_sec, ops_per_clk_sm); break;

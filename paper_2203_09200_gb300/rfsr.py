@@ -422,7 +422,7 @@ def me_cc_project_noalloc(d_smp, d_msk, refs, d_psum, d_pcnt, height: int, width
 
 ALU_KINDS = ["iadd3", "lop3", "prmt", "vabsdiffu4", "vsadu4+add", "vimax3_u16x2",
              "vimin3_u16x2", "imad", "sad", "imin", "xor", "ffma", "iadd3+imad",
-             "vabsdiff4.add", "min.s16x2", "vabsdiff2.add", "vimax3_s16x2"]
+             "vabsdiff4.add", "min.s16x2", "vabsdiff2.add", "vimax3_s16x2", "vimax3_u32"]
 
 
 def alu_peak(kind: str, device: int = 0, iters: int = 2000):
