@@ -142,8 +142,9 @@ typedef struct {
                               in raster order that are neither measured nor projected join the
                               support with weight delta rho^d and their reconstruction as value;
                               blocks then run as wavefronts (block (i, j) after (i-1, j+4) and
-                              (i, j-1)), one launch per wave, far slower.  Unbatched engines only
-                              (EINVAL on batched ones); rfsr_fsr_device then needs d_out_f32.    */
+                              (i, j-1)), one launch per wave, far slower.  On batched and serving
+                              engines such a stream's FSR runs as its own wavefront launches right
+                              after each batched step; rfsr_fsr_device then needs d_out_f32.     */
     int fsr_trace;         /* 1: record, for every 4x4 block of every frame, the basis pair the FSR
                               selected in each iteration (debug plane RFSR_DBG_FSR_SEL): the
                               selection is an argmax, so this makes the FP32 result checkable
@@ -380,7 +381,8 @@ int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const uint8_t *d_s
  * 8 |a-b|+c (__sad), 9 32-bit min, 10 xor, 11 FP32 fused multiply-add, 12 3-input adds and
  * integer multiply-adds interleaved (one each per pair of chains), 13 byte SAD with accumulate
  * (one vabsdiff4.add), 14 signed 16-bit x2 minimum (min.s16x2), 15 sum of the two signed 16-bit
- * |a-b| with accumulate (vabsdiff2.add), 16 signed 16-bit x2 3-way max.  Synchronous; allocates
+ * |a-b| with accumulate (vabsdiff2.add), 16 signed 16-bit x2 3-way max, 17 32-bit 3-way max.
+ * Synchronous; allocates
  * and frees its own small buffers.  Errors: EINVAL, EDEVICE. */
 int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_sec, double *ops_per_clk_sm);
 

@@ -597,14 +597,17 @@ int step_batch_locked(rfsr_engine *e)
     double me_units = 0, fsr_units = 0;
     for (int i = 0; i < n; ++i) {
         const FrameTask &t = bd->task[i];
+        // a stream with concealed weighting > 0 gets no FSR tiles: its blocks run as wavefronts
+        // after the batch (below)
+        const bool conc = t.fsr_concealed > 0.f;
         const int c[kPhases] = {tiles_ingest(t), tiles_me(t, sh.me_warps, sh.me_box), tiles_rme(t), tiles_cc(t),
-                                tiles_fsr(t, sh.fsr_blocks)};
+                                conc ? 0 : tiles_fsr(t, sh.fsr_blocks)};
         for (int p = 0; p < kPhases; ++p) {
             bd->off[p][i] = tot[p];
             tot[p] += c[p];
         }
         me_units += (double)t.H * t.W * t.K;
-        fsr_units += (double)((t.H + kFsrB - 1) / kFsrB) * ((t.W + kFsrB - 1) / kFsrB);
+        if (!conc) fsr_units += (double)((t.H + kFsrB - 1) / kFsrB) * ((t.W + kFsrB - 1) / kFsrB);
     }
     for (int p = 0; p < kPhases; ++p) {
         bd->off[p][n] = tot[p];
@@ -651,6 +654,10 @@ int step_batch_locked(rfsr_engine *e)
         CK(cudaMemcpyAsync(set.d, set.h, sizeof(BatchDesc), cudaMemcpyHostToDevice, e->stream));
         CK(launch_batch_phases(set.d, T, rme, trace, sh, e->stream, tuning ? set.ph : nullptr));
     }
+    // concealed weighting > 0 (Sec. 4 sets it to 0; the original FSR): each such stream's FSR runs
+    // as its own wavefront launches, on the same stream right after the batch's checks and FSR
+    for (int i = 0; i < n; ++i)
+        if (bd->task[i].fsr_concealed > 0.f) CK(launch_fsr(bd->task[i], e->stream));
     if (tuning) {
         set.tune_pending = true;
         set.tune_me = cme;
@@ -1005,8 +1012,6 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
     }
     int rc = check_stream_config(cfg);
     if (rc) return rc;
-    if (cfg->fsr_concealed_weight > 0.f && batched(e))
-        return fail(RFSR_EINVAL, "create_stream: concealed weighting > 0 needs an unbatched engine");
     CK(cudaSetDevice(e->cfg.device));
     auto *s = new rfsr_stream();
     s->eng = e;

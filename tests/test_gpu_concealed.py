@@ -128,10 +128,38 @@ def test_concealed_first_frame_of_a_stream(engine):
     check_raster(got, sel, P, delta, smp, msk, None, None)
 
 
+@pytest.mark.parametrize("serve", [False, True])
+def test_concealed_streams_in_batched_steps_equal_alone(engine, serve):
+    """Batched and serving engines: streams with delta > 0 (their FSR runs as wavefront launches
+    after each batched step) next to delta = 0 streams give the same bits as each stream alone on
+    an unbatched engine, frame after frame (the recursion included)."""
+    specs = [(64, 80, 0.5, 41), (48, 96, 0.0, 42), (40, 64, 1.0, 43)]
+    F = 4
+    seqs = [synth.config2(seed=sd, H=H, W=W, F=F) for H, W, _, sd in specs]
+    alone = []
+    for (H, W, d, _), seq in zip(specs, seqs):
+        st = engine.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=d)
+        res = []
+        for t in range(F):
+            st.push_frame(seq.samples[t], seq.masks[t])
+            res.append(st.get_frame(timeout_ms=60000, f32=True))
+        st.destroy()
+        alone.append(res)
+    with rfsr.Engine(device=0, batched=not serve, serve=serve) as beng:
+        sts = [beng.create_stream(height=H, width=W, keep_f32=True, fsr_concealed_weight=d)
+               for H, W, d, _ in specs]
+        for t in range(F):
+            for st, seq in zip(sts, seqs):
+                st.push_frame(seq.samples[t], seq.masks[t])
+            if not serve:
+                beng.step()
+            for i, st in enumerate(sts):
+                rec, f32 = st.get_frame(timeout_ms=60000, f32=True)
+                np.testing.assert_array_equal(rec, alone[i][t][0], err_msg=f"stream {i} t {t}")
+                np.testing.assert_array_equal(f32, alone[i][t][1], err_msg=f"stream {i} t {t}")
+
+
 def test_concealed_errors(engine):
-    with rfsr.Engine(device=0, batched=True) as beng:
-        with pytest.raises(rfsr.RfsrError, match="unbatched"):
-            beng.create_stream(height=32, width=32, fsr_concealed_weight=0.5)
     with pytest.raises(rfsr.RfsrError, match="fsr_concealed_weight"):
         engine.create_stream(height=32, width=32, fsr_concealed_weight=-1.0)
     d = torch.zeros((32, 32), dtype=torch.uint8, device="cuda")
