@@ -928,7 +928,8 @@ cudaError_t launch_cc_batched_t(BatchDesc *bd, cudaStream_t st)
     static std::atomic<bool> attr[64];
     cudaError_t e = set_smem(cc_batched_kernel<T>, attr);
     if (e != cudaSuccess) return e;
-    static const int grid = persistent_grid(cc_batched_kernel<T>, NT, sizeof(Smem));
+    static std::atomic<int> grids[64];
+    const int grid = persistent_grid_cached(cc_batched_kernel<T>, NT, sizeof(Smem), grids);
     cc_batched_kernel<T><<<grid, NT, sizeof(Smem), st>>>(bd);
     return cudaGetLastError();
 }
@@ -1015,7 +1016,8 @@ cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st)
 cudaError_t launch_rme_batched(BatchDesc *bd, int T, cudaStream_t st)
 {
     if (T == 9) return launch_rme9_batched(bd, st);
-    static const int grid = persistent_grid(rme_batched_kernel, NT, 0);
+    static std::atomic<int> grids[64];
+    const int grid = persistent_grid_cached(rme_batched_kernel, NT, 0, grids);
     rme_batched_kernel<<<grid, NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();

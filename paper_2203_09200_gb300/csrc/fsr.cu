@@ -734,7 +734,8 @@ namespace {
 template <int WPB, bool TRACE>
 void launch_fsr_batched_t(BatchDesc *bd, cudaStream_t st)
 {
-    static const int grid = persistent_grid(fsr_batched_kernel<WPB, TRACE>, WPB * 32, sizeof(Smem<WPB>));
+    static std::atomic<int> grids[64];
+    const int grid = persistent_grid_cached(fsr_batched_kernel<WPB, TRACE>, WPB * 32, sizeof(Smem<WPB>), grids);
     fsr_batched_kernel<WPB, TRACE><<<grid, WPB * 32, sizeof(Smem<WPB>), st>>>(bd);
 }
 

@@ -87,7 +87,8 @@ cudaError_t launch_ingest(const FrameTask &t, cudaStream_t st)
 
 cudaError_t launch_ingest_batched(BatchDesc *bd, cudaStream_t st)
 {
-    static const int grid = persistent_grid(ingest_batched_kernel, kIngestThreads, 0);
+    static std::atomic<int> grids[64];
+    const int grid = persistent_grid_cached(ingest_batched_kernel, kIngestThreads, 0, grids);
     ingest_batched_kernel<<<grid, kIngestThreads, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();

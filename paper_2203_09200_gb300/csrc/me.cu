@@ -663,7 +663,8 @@ cudaError_t launch_rme9(const FrameTask &t, cudaStream_t st)
 
 cudaError_t launch_rme9_batched(BatchDesc *bd, cudaStream_t st)
 {
-    static const int grid = persistent_grid(rme9_batched_kernel, R9_NT, 0);
+    static std::atomic<int> grids[64];
+    const int grid = persistent_grid_cached(rme9_batched_kernel, R9_NT, 0, grids);
     rme9_batched_kernel<<<grid, R9_NT, 0, st>>>(bd);
     count_launch();
     return cudaGetLastError();
@@ -679,13 +680,16 @@ cudaError_t launch_me_batched(BatchDesc *bd, int T, int me_warps, int me_box, cu
         if (e != cudaSuccess) return e;
     }
     if (T == 9 && me_warps == 4) {
-        static const int grid = persistent_grid(me9_batched_kernel<4>, s_nt<4>(), sizeof(Smem9<4>));
+        static std::atomic<int> grids[64];
+        const int grid = persistent_grid_cached(me9_batched_kernel<4>, s_nt<4>(), sizeof(Smem9<4>), grids);
         me9_batched_kernel<4><<<grid, s_nt<4>(), sizeof(Smem9<4>), st>>>(bd);
     } else if (T == 9) {
-        static const int grid = persistent_grid(me9_batched_kernel<8>, s_nt<8>(), sizeof(Smem9<8>));
+        static std::atomic<int> grids[64];
+        const int grid = persistent_grid_cached(me9_batched_kernel<8>, s_nt<8>(), sizeof(Smem9<8>), grids);
         me9_batched_kernel<8><<<grid, s_nt<8>(), sizeof(Smem9<8>), st>>>(bd);
     } else {
-        static const int grid = persistent_grid(me_batched_kernel, NT, 0);
+        static std::atomic<int> grids[64];
+        const int grid = persistent_grid_cached(me_batched_kernel, NT, 0, grids);
         me_batched_kernel<<<grid, NT, 0, st>>>(bd);
     }
     count_launch();

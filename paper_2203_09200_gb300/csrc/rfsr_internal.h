@@ -2,6 +2,7 @@
 // translation units.  Not part of the public ABI (include/rfsr.h is).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -155,6 +156,23 @@ int persistent_grid(K kernel, int threads, size_t smem)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1)
         per = 1;
     return sms * per;
+}
+
+// The persistent grid of a batched kernel on the calling thread's current device, computed once
+// per device and call site (cache: one slot per device ordinal, 0 = not computed yet), so that an
+// engine on another device gets its own device's figure.
+template <typename K>
+int persistent_grid_cached(K kernel, int threads, size_t smem, std::atomic<int> (&cache)[64])
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return persistent_grid(kernel, threads, smem);
+    int g = cache[dev].load();
+    if (g <= 0) {
+        g = persistent_grid(kernel, threads, smem);
+        cache[dev].store(g);
+    }
+    return g;
 }
 
 // batched launchers: one persistent launch per phase over all tasks of bd (device pointer; the
