@@ -519,6 +519,82 @@ def test_fsr_border_block_ignores_outside():
     assert not tr.w[:o, :].any() and not tr.w[:, :o].any()
 
 
+def _canonical_energy(R, N=32):
+    """wf |R|^2 over canonical members of conjugate pairs (-1 elsewhere), written out in numpy."""
+    k = np.arange(N)
+    kn = np.minimum(k, N - k) / (N / 2)
+    wf = (1 - np.sqrt(2) / 2 * np.sqrt(kn[:, None] ** 2 + kn[None, :] ** 2)) ** 2
+    lin = k[:, None] * N + k[None, :]
+    conj = ((N - k[:, None]) % N) * N + (N - k[None, :]) % N
+    return np.where(lin <= conj, wf * np.abs(R) ** 2, -1.0).ravel()
+
+
+def test_fsr_replay_of_its_own_selections_is_the_plain_run():
+    """Replaying the oracle's own selection sequence gives its own output bit for bit, with no
+    divergence, block by block and over a frame."""
+    _, smp, msk = _block_scene(seed=8)
+    tr = oracle.fsr_block(P0, smp, msk, None, None, 6, 5)
+    out, rep = oracle.fsr_block_replay(P0, smp, msk, None, None, 6, 5,
+                                       tr.selected.astype(np.uint16))
+    np.testing.assert_array_equal(out, tr.out)
+    assert rep.divergences == 0 and rep.first_div == -1 and not rep.invalid
+    assert rep.iterations_run == P0.iterations
+    plain, _ = oracle.fsr_frame(P0, smp, msk)
+    nb = 16 * 16
+    sel = np.stack([oracle.fsr_block(P0, smp, msk, None, None, b // 16, b % 16).selected
+                    for b in range(nb)]).astype(np.uint16)
+    rout, reps = oracle.fsr_frame_replay(P0, smp, msk, None, None, sel)
+    np.testing.assert_array_equal(rout, plain)
+    assert not reps["divergences"].any()
+
+
+@pytest.mark.parametrize("it", [0, 9, 37])
+def test_fsr_replay_follows_a_second_best_selection(it):
+    """Forcing the second-best pair at iteration `it`: the replay reports its first divergence
+    there, with the criterion gap (best - second) / best of the residual after `it` iterations,
+    computed here from the oracle's residual spectrum by numpy; the output changes."""
+    _, smp, msk = _block_scene(seed=9)
+    by, bx = 7, 8
+    tr = oracle.fsr_block(P0, smp, msk, None, None, by, bx)
+    Rit = oracle.fsr_block(oracle.FsrParams(iterations=it), smp, msk, None, None, by, bx).R
+    e = _canonical_energy(Rit)
+    order = np.argsort(-e, kind="stable")
+    assert order[0] == tr.selected[it]
+    follow = tr.selected.astype(np.uint16).copy()
+    follow[it] = order[1]
+    out, rep = oracle.fsr_block_replay(P0, smp, msk, None, None, by, bx, follow,
+                                       bound=(2.0 ** -17, 2.0 ** -24))
+    assert rep.first_div == it and rep.divergences >= 1 and not rep.invalid
+    gap = (e[order[0]] - e[order[1]]) / e[order[0]]
+    assert rep.first_gap == pytest.approx(gap, rel=1e-9)
+    assert rep.max_gap >= rep.first_gap
+    assert rep.max_excess >= rep.first_gap / (2.0 ** -17 + 2.0 ** -24 * rep.max_scale) * (1 - 1e-12)
+    assert np.abs(out - tr.out).max() > 0
+
+
+def test_fsr_replay_stops_at_no_selection_and_flags_bad_indices():
+    """0xFFFF at iteration i ends the replay there: the output equals i plain iterations.  A
+    selection that is not the canonical member of its conjugate pair is flagged invalid."""
+    _, smp, msk = _block_scene(seed=10)
+    tr = oracle.fsr_block(P0, smp, msk, None, None, 5, 6)
+    follow = tr.selected.astype(np.uint16).copy()
+    follow[12:] = 0xFFFF
+    out, rep = oracle.fsr_block_replay(P0, smp, msk, None, None, 5, 6, follow)
+    assert rep.iterations_run == 12 and rep.divergences == 0
+    np.testing.assert_array_equal(
+        out, oracle.fsr_block(oracle.FsrParams(iterations=12), smp, msk, None, None, 5, 6).out)
+    bad = tr.selected.astype(np.uint16).copy()
+    k, l = divmod(int(bad[3]), 32)
+    conj = ((32 - k) % 32) * 32 + (32 - l) % 32
+    if conj != bad[3]:                              # the other member of the pair
+        bad[3] = conj
+        _, rep = oracle.fsr_block_replay(P0, smp, msk, None, None, 5, 6, bad)
+        assert rep.invalid
+    bad[3] = 32 * 32                                # outside the spectrum
+    _, rep = oracle.fsr_block_replay(P0, smp, msk, None, None, 5, 6, bad)
+    assert rep.invalid
+
+
 def test_quantize_rounding():
     x = np.array([[2.5, 3.5, -0.2, 300.0, 0.1, 17.0]]) / 255.0
     msk = np.array([[0, 0, 0, 0, 0, 1]], np.uint8)
