@@ -26,12 +26,14 @@
 // three aligned 8-byte loads; the template counts n are computed once per tile.  Per past frame the
 // CTA stages the ME field with a 2-pixel halo and the past frame around the tile (for interior
 // tiles fetched with cp.async during the previous past frame's checks), computes the median field
-// once, decides every pixel, and compacts the pixels that need a reverse check into a list.  A warp then takes one listed pixel at a time: the past-frame patch around q sits in
-// registers, lane 0 scores d = 0 and the other lanes split the remaining offsets, each costing T
-// rows of (AND, byte SAD); a warp vote ends the check as soon as a candidate beats d = 0.  The
-// current frame's copies use a row stride of 19 and a copy stride of 12 mod 16 units, and the
-// offsets are dealt to lanes (per column phase, nearest first) so that the 16 lanes of each
-// half-warp read 16 distinct bank pairs for every template word.
+// once, decides every pixel, and compacts the pixels that need a reverse check into a list.  For
+// FRMC (T = 9) the vector most listed pixels share is checked by box sums over the tile
+// (box_checks9).  For the other listed pixels a warp takes one pixel at a time: the past-frame
+// patch around q sits in registers, lane 0 scores d = 0 and the other lanes split the remaining
+// offsets, each costing T rows of (AND, byte SAD); a warp vote ends the check as soon as a
+// candidate beats d = 0.  The current frame's copies use a row stride of 19 and a copy stride of
+// 12 mod 16 units, and the offsets are dealt to lanes (per column phase, nearest first) so that
+// the 16 lanes of each half-warp read 16 distinct bank pairs for every template word.
 #include <atomic>
 #include <type_traits>
 

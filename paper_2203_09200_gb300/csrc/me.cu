@@ -155,7 +155,8 @@ __device__ __forceinline__ void me_tile(Smem &sm, const FrameTask &t, int tbx, i
 
 // ---------------------------------------------------------------------------------------------
 // T = 9: warp-strip kernel with byte SIMD.  Lane l of a warp owns four adjacent columns (one
-// 32-bit word of bytes) of a 128-column strip, the warp owns 8 output rows, the CTA 8 warps.
+// 32-bit word of bytes) of a 128-column strip, the warp owns 8 output rows, the CTA 4 warps (8 in
+// one of the batched tile shapes).
 // For each candidate the lane walks the 16 rows of D_v its outputs need: one aligned load of the
 // past-frame word from the byte-shifted copy of its column phase, __vabsdiffu4, AND with the
 // mask, and running vertical sums kept as two packed 16-bit words (columns 0,2 and 1,3).  The
