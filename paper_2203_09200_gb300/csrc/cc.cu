@@ -63,6 +63,9 @@ constexpr int NS = TP + 2 * kMaxRadius;       // source-count plane side (tile +
 constexpr int MT = TP + 4;                    // ME field tile with a 2-pixel halo
 constexpr int MD = TP + 2;                    // median field with a 1-pixel halo
 constexpr int PPT = TP * TP / NT;             // pixels owned per thread
+constexpr int MSEG = 5;                       // medians per thread task (one row, consecutive)
+constexpr int MNSEG = (MD + MSEG - 1) / MSEG; // tasks per median row
+static_assert(MD * MNSEG <= NT, "the median field is one pass of the CTA");
 // Box-sum FRMC checks (T = 9)
 constexpr int BOX_MIN = 64;                   // listed pixels of one vector that pay for a box pass
                                               // (1080p checks: 0.553 ms at 64 and 96, 0.559 at 128,
@@ -189,10 +192,12 @@ struct Smem {
     uint32_t mvraw[MT * MT / 2];  // the next past frame's ME field around the tile (raw char2
                                   // pairs), fetched asynchronously during the current one's checks
     uint32_t rfraw[RS * NWD];     // the next past frame around the tile (raw words), likewise
-    int hist[HS * HS];            // listed pixels per filtered vector
+    int hist[HS * HS];            // listed pixels per filtered vector; once the box vector is
+                                  // chosen, the listed pixels with other vectors (plist)
     int boxv;                     // vector (histogram bin) checked by box sums, -1: none
     int nlist;
     int nblist;
+    int nplist;
 };
 static_assert(offsetof(Smem, e0n0) % 16 == 0, "d = 0 costs are read in 16-byte words");
 static_assert(offsetof(Smem, ecand) % 8 == 0, "candidate costs are written in 8-byte words");
@@ -201,14 +206,22 @@ static_assert(offsetof(Smem, ord) % 16 == 0, "the lane order is written in 16-by
 
 __device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
 
-// Motion vectors in shared memory are (v_y + 16, v_x + 16) as the low and high 16-bit halves of
-// a word, so that the median and the neighbour test run on both components at once (min.u16x2 /
-// max.u16x2 are single instructions).  The offset keeps both halves positive, so subtracting
-// packed words never borrows across the halves; the median commutes with it.
-constexpr int MV_BIAS = 16;
-__device__ __forceinline__ uint32_t pack_mv(char2 c)
+// the listed pixels left to the per-pixel checks after a box pass (the histogram is dead by then;
+// at most NLMAX - BOX_MIN entries)
+__device__ __forceinline__ uint16_t *plist(Smem &sm) { return reinterpret_cast<uint16_t *>(sm.hist); }
+static_assert((NLMAX - BOX_MIN) * sizeof(uint16_t) <= sizeof(Smem::hist), "plist fits the histogram");
+
+// Motion vectors in shared memory are (v_y + 128, v_x + 128) as the low and high 16-bit halves
+// of a word, so that the median and the neighbour test run on both components at once
+// (min.u16x2 / max.u16x2 are single instructions).  The offset keeps both halves positive, so
+// subtracting packed words never borrows across the halves; the median commutes with it.  The
+// ME field stores a vector as two signed bytes (v_y, v_x); XOR 0x80 turns each into v + 128 and a
+// byte permute spreads the pair into the halves.
+constexpr int MV_BIAS = 128;
+// the vector whose bytes sit at bytes 2j, 2j + 1 of w (j = 0, 1)
+__device__ __forceinline__ uint32_t pack_mv(uint32_t w, int j)
 {
-    return (uint32_t)((int)c.x + MV_BIAS) | ((uint32_t)((int)c.y + MV_BIAS) << 16);
+    return __byte_perm(w ^ 0x80808080u, 0u, 0x4140u + 0x0202u * (unsigned)j);
 }
 __device__ __forceinline__ int mv_y(uint32_t w) { return (int)(w & 0xffffu) - MV_BIAS; }
 __device__ __forceinline__ int mv_x(uint32_t w) { return (int)(w >> 16) - MV_BIAS; }
@@ -234,18 +247,25 @@ __device__ __forceinline__ uint32_t pmed3(uint32_t a, uint32_t b, uint32_t c)
 {
     return pmax(pmin(a, b), pmin(pmax(a, b), c));
 }
-// component-wise median of nine packed vectors: sort each group of three, then the median of
-// (largest minimum, median of medians, smallest maximum) -- exact for any input, ties included
-__device__ __forceinline__ uint32_t pmedian9(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3,
-                                             uint32_t p4, uint32_t p5, uint32_t p6, uint32_t p7,
-                                             uint32_t p8)
+// Component-wise median of the nine packed vectors of three sorted triples (lo <= mid <= hi per
+// half): the median of (largest minimum, median of medians, smallest maximum).  This holds for
+// any split of the nine into triples, ties included, so the triples may be the columns of the
+// 3x3 window, each sorted once and shared by the three windows that contain it.
+struct Sorted3 {
+    uint32_t lo, mid, hi;
+};
+__device__ __forceinline__ Sorted3 psort3(uint32_t a, uint32_t b, uint32_t c)
 {
-    pswap(p0, p1); pswap(p1, p2); pswap(p0, p1);
-    pswap(p3, p4); pswap(p4, p5); pswap(p3, p4);
-    pswap(p6, p7); pswap(p7, p8); pswap(p6, p7);
-    const uint32_t lo = __vimax3_u16x2(p0, p3, p6);
-    const uint32_t hi = __vimin3_u16x2(p2, p5, p8);
-    return pmed3(lo, pmed3(p1, p4, p7), hi);
+    pswap(a, b);
+    pswap(b, c);
+    pswap(a, b);
+    return {a, b, c};
+}
+__device__ __forceinline__ uint32_t pmedian9(const Sorted3 &a, const Sorted3 &b, const Sorted3 &c)
+{
+    const uint32_t lo = __vimax3_u16x2(a.lo, b.lo, c.lo);
+    const uint32_t hi = __vimin3_u16x2(a.hi, b.hi, c.hi);
+    return pmed3(lo, pmed3(a.mid, b.mid, c.mid), hi);
 }
 // |a_y - b_y| + |a_x - b_x| <= 1 for packed vectors: max - min per half is |a - b| (no borrow
 // between the halves: each half of the maximum is at least that of the minimum, as unsigned
@@ -440,6 +460,7 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
             const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
             const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
             if (mv_y(c) == vy && mv_x(c) == vx) sm.blist[atomicAdd(&sm.nblist, 1)] = (uint16_t)pi;
+            else plist(sm)[atomicAdd(&sm.nplist, 1)] = (uint16_t)pi;
         }
     }
     __syncthreads();
@@ -581,14 +602,13 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
     for (int i = 0; i < PPT; ++i) sum[i] = cnt[i] = 0;
 
     for (int k = 0; k < t.K; ++k) {
-        const char2 *mvk = reinterpret_cast<const char2 *>(t.mv[k]);
+        const uint16_t *mvk = reinterpret_cast<const uint16_t *>(t.mv[k]);   // (v_y, v_x) bytes
         if (pf) cp_wait_all();
         __syncthreads();
         if (pf) {
             for (int i = tid; i < MT * MT; i += NT) {
                 const int r = i / MT, c = i - r * MT;
-                const uint32_t pair = sm.mvraw[r * (MT / 2) + (c >> 1)] >> (16 * (c & 1));
-                sm.mv[r][c] = pack_mv(make_char2((signed char)(pair & 0xffu), (signed char)(pair >> 8)));
+                sm.mv[r][c] = pack_mv(sm.mvraw[r * (MT / 2) + (c >> 1)], c & 1);
             }
             if (frmc || rmc)
                 for (int i = tid; i < RS * NWD; i += NT) {
@@ -599,7 +619,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             for (int i = tid; i < MT * MT; i += NT) {
                 const int r = i / MT, c = i - r * MT;
                 const int gy = min(max(y0 - 2 + r, 0), H - 1), gx = min(max(x0 - 2 + c, 0), W - 1);
-                sm.mv[r][c] = pack_mv(mvk[(size_t)gy * W + gx]);
+                sm.mv[r][c] = pack_mv(mvk[(size_t)gy * W + gx], 0);
             }
             if (frmc || rmc) stage_past0(sm.rf, t.ref_rec[k], H, W, y0, x0);
         }
@@ -609,11 +629,19 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         if (frmc || rmc) shift_past(sm.rf);
         __syncthreads();
         if (use_nnc) {
-            for (int i = tid; i < MD * MD; i += NT) {
-                const int r = i / MD, c = i - r * MD;
-                sm.md[r][c] = pmedian9(sm.mv[r][c], sm.mv[r][c + 1], sm.mv[r][c + 2],
-                                       sm.mv[r + 1][c], sm.mv[r + 1][c + 1], sm.mv[r + 1][c + 2],
-                                       sm.mv[r + 2][c], sm.mv[r + 2][c + 1], sm.mv[r + 2][c + 2]);
+            // a thread slides along MSEG medians of one row: each sorted column serves three
+            for (int i = tid; i < MD * MNSEG; i += NT) {
+                const int r = i / MNSEG, c0 = (i - r * MNSEG) * MSEG;
+                auto col = [&](int c) { return psort3(sm.mv[r][c], sm.mv[r + 1][c], sm.mv[r + 2][c]); };
+                Sorted3 a = col(c0), b = col(c0 + 1);
+#pragma unroll
+                for (int j = 0; j < MSEG; ++j) {
+                    if (c0 + j >= MD) break;
+                    const Sorted3 c = col(c0 + j + 2);
+                    sm.md[r][c0 + j] = pmedian9(a, b, c);
+                    a = b;
+                    b = c;
+                }
             }
             __syncthreads();
         }
@@ -717,6 +745,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                     if (lane == 0) {
                         sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
                         sm.nblist = 0;
+                        sm.nplist = 0;
                     }
                 }
                 __syncthreads();
@@ -727,11 +756,12 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             }
         }
         // reverse checks of the other listed pixels: one warp per pixel
-        for (int li = warp; li < nl; li += NW) {
-            const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
+        const uint16_t *pl = boxbin >= 0 ? plist(sm) : sm.list;
+        const int np = boxbin >= 0 ? sm.nplist : nl;
+        for (int li = warp; li < np; li += NW) {
+            const int pi = pl[li], py = pi / TP, px = pi - py * TP;
             const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
             const int fy = mv_y(c), fx = mv_x(c);
-            if ((fy + kMaxRadius) * HS + fx + kMaxRadius == boxbin) continue;   // done above
             uint32_t P[T][3];                          // past-frame patch around q
             {
                 const int ry = py + HC + fy - h, rx = px + HC + fx - h;
@@ -743,34 +773,46 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                     P[r][2] = base[r * RWD + 2];
                 }
             }
-            int s0 = 0, n0 = 0;
-            bool rej = false;
-            // round 0, lane 0 scores d = 0; the lane order of the pixel's column phase
+            // candidate of round rd of this lane: its cost, template count and validity
             const int ph = (px + HC - h) & 3;
-            const int nround = sm.ord.nround[ph];
-            for (int rd = 0; rd < nround; ++rd) {
+            auto score = [&](int rd, int &s, int &n) {
                 const int e = sm.ord.lane[ph][rd][lane];
-                const int cc = e == NOCAND ? -1 : e;         // candidate, row-major in the window
-                int s = 0, n = 0;
-                bool valid = false;
-                if (cc >= 0) {
-                    const int dy = cand_dy(cc, frmc, t.Rc), dx = cand_dx(cc, frmc, t.Rc);
-                    const int sy = y0 + py + dy, sx = x0 + px + dx;
-                    if ((unsigned)sy < (unsigned)H && (unsigned)sx < (unsigned)W) {
-                        s = sad_against<T>(sm, py + dy + HC - h, px + dx + HC - h, P);
-                        n = sm.nsrc[py + dy + kMaxRadius][px + dx + kMaxRadius];
-                        valid = true;
+                s = n = 0;
+                if (e == NOCAND) return false;
+                const int dy = cand_dy(e, frmc, t.Rc), dx = cand_dx(e, frmc, t.Rc);
+                const int sy = y0 + py + dy, sx = x0 + px + dx;
+                if ((unsigned)sy >= (unsigned)H || (unsigned)sx >= (unsigned)W) return false;
+                s = sad_against<T>(sm, py + dy + HC - h, px + dx + HC - h, P);
+                n = sm.nsrc[py + dy + kMaxRadius][px + dx + kMaxRadius];
+                return true;
+            };
+            bool rej = false;
+            const int nround = sm.ord.nround[ph];
+            if (frmc) {
+                // FRMC fills two rounds (49 candidates): both are scored in one pass, so that
+                // their shared-memory loads and SAD chains overlap
+                int s0, n0, s1, n1;
+                bool v0 = score(0, s0, n0);
+                const bool v1 = score(1, s1, n1);
+                const int sc = __shfl_sync(0xffffffffu, s0, 0), nc = __shfl_sync(0xffffffffu, n0, 0);
+                if (lane == 0) v0 = false;                  // round 0, lane 0 scores d = 0
+                const bool better = (v0 && s0 * nc < sc * n0) || (v1 && s1 * nc < sc * n1);
+                rej = __any_sync(0xffffffffu, better);
+            } else {
+                int sc = 0, nc = 0;
+                for (int rd = 0; rd < nround; ++rd) {
+                    int s, n;
+                    bool valid = score(rd, s, n);
+                    if (rd == 0) {
+                        sc = __shfl_sync(0xffffffffu, s, 0);
+                        nc = __shfl_sync(0xffffffffu, n, 0);
+                        if (lane == 0) valid = false;
                     }
-                }
-                if (rd == 0) {
-                    s0 = __shfl_sync(0xffffffffu, s, 0);
-                    n0 = __shfl_sync(0xffffffffu, n, 0);
-                    if (lane == 0) valid = false;
-                }
-                const bool better = valid && s * n0 < s0 * n;
-                if (__any_sync(0xffffffffu, better)) {
-                    rej = true;
-                    break;
+                    const bool better = valid && s * nc < sc * n;
+                    if (__any_sync(0xffffffffu, better)) {
+                        rej = true;
+                        break;
+                    }
                 }
             }
             if (lane == 0) sm.rej[pi] = rej ? 1 : 0;
