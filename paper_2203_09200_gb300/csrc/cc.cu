@@ -386,25 +386,30 @@ __device__ __forceinline__ int sad_against(const Smem &sm, int sy, int sx, const
     return acc + acc1 + acc2;
 }
 
+// first past-frame word of this lane's rows r0 - 4 .. (F_d's second operand, independent of d)
+__device__ __forceinline__ const uint32_t *box_ref(const Smem &sm, int r0, int wi, int vy, int vx)
+{
+    const int jr = (HC - 4 + vx) & 3, wr = wi + ((HC - 4 + vx) >> 2);
+    return sm.rf + jr * CPY + (r0 - 4 + HC + vy) * RWD + wr;
+}
 // Box sums of F_d over the tile for one candidate d (T = 9).  F_d(y) = b_t(y + d) |s_t(y + d) -
 // rec(y + v)| for tile rows r0 - 4 .. r0 + rows + 3 and the 4 columns 4 wi - 4 .. 4 wi - 1 of
 // this lane (wi = 0 and 9 are the halo words), kept as vertical 9-sums in two packed 16-bit words
 // (columns 0, 2 and 1, 3); the horizontal 9-sums come from the neighbouring lanes (lanes lane - 1
-// and lane + 1 hold words wi - 1 and wi + 1) as in the forward ME.  fn(j, h02, h13) receives the window sums (H0, H2) and
-// (H1, H3) of output row r0 + j.
-template <int ROWS, typename Fn>
-__device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy, int dx, int vy,
-                                         int vx, Fn &&fn)
+// and lane + 1 hold words wi - 1 and wi + 1) as in the forward ME.  refw(i) gives the past-frame
+// word of row r0 - 4 + i; fn(j, h02, h13) receives the window sums (H0, H2) and (H1, H3) of
+// output row r0 + j.
+template <int ROWS, typename RefFn, typename Fn>
+__device__ __forceinline__ void box_rows_ref(const Smem &sm, int r0, int wi, int dy, int dx, RefFn &&refw,
+                                             Fn &&fn)
 {
     const int jc = (HC - 4 + dx) & 3, wc = wi + ((HC - 4 + dx) >> 2);
-    const int jr = (HC - 4 + vx) & 3, wr = wi + ((HC - 4 + vx) >> 2);
     const uint2 *cur = sm.csm + jc * CPYC + (r0 - 4 + HC + dy) * RWDC + wc;
-    const uint32_t *ref = sm.rf + jr * CPY + (r0 - 4 + HC + vy) * RWD + wr;
     uint32_t dlo[ROWS + 8], dhi[ROWS + 8], lo = 0, hi = 0;
 #pragma unroll
     for (int i = 0; i < ROWS + 8; ++i) {
         const uint2 c = cur[i * RWDC];
-        const uint32_t d4 = __vabsdiffu4(c.x, ref[i * RWD]) & c.y;
+        const uint32_t d4 = __vabsdiffu4(c.x, refw(i)) & c.y;
         dlo[i] = __byte_perm(d4, 0u, 0x4240);
         dhi[i] = __byte_perm(d4, 0u, 0x4341);
         lo += dlo[i];
@@ -424,6 +429,13 @@ __device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy,
             fn(i - 8, h02, h02 + Qr - lol - lor);
         }
     }
+}
+template <int ROWS, typename Fn>
+__device__ __forceinline__ void box_rows(const Smem &sm, int r0, int wi, int dy, int dx, int vy,
+                                         int vx, Fn &&fn)
+{
+    const uint32_t *ref = box_ref(sm, r0, wi, vy, vx);
+    box_rows_ref<ROWS>(sm, r0, wi, dy, dx, [&](int i) { return ref[i * RWD]; }, fn);
 }
 
 // FRMC reverse checks by box sums for the listed pixels whose filtered vector is v (T = 9).  The
@@ -477,12 +489,21 @@ __device__ void box_checks9(Smem &sm, const FrameTask &t, int x0, int y0, int vy
     const uint16_t *ec = &sm.ecand[warp][0][0];
     const uint8_t *ns = &sm.nsrc[0][0];
     // instantiated for interior tiles (every source p + d in the frame) and for the others
+    // the past-frame words of the lane's rows are the same for every candidate d (the patch
+    // around q = p + v stays fixed): loaded once, kept in registers (-3 % at 1080p)
+    uint32_t refc[11 + 8];
+    {
+        const uint32_t *ref = box_ref(sm, 11 * ch, wi, vy, vx);
+#pragma unroll
+        for (int i = 0; i < 11 + 8; ++i) refc[i] = ref[i * RWD];
+    }
     auto candidates = [&](auto inner_tag) {
         constexpr bool INNER = decltype(inner_tag)::value;
         for (int i = 1 + warp; i < 49; i += NW) {
             const int ci = i <= 24 ? i - 1 : i;      // the 48 offsets d != 0
             const int dy = frmc_offset(ci / 7), dx = frmc_offset(ci % 7);
-            box_rows<11>(sm, 11 * ch, wi, dy, dx, vy, vx, [&](int j, uint32_t h02, uint32_t h13) {
+            box_rows_ref<11>(sm, 11 * ch, wi, dy, dx, [&](int i) { return refc[i]; },
+                             [&](int j, uint32_t h02, uint32_t h13) {
                 const int r = 11 * ch + j;
                 if (out && r < TP)                   // (H0, H1, H2, H3) of columns 4 (wi - 1) ..
                     *reinterpret_cast<uint2 *>(&sm.ecand[warp][r][4 * (wi - 1)]) =
@@ -627,9 +648,9 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         __syncthreads();
         if (pf && k + 1 < t.K) prefetch_past(sm, t, k + 1, x0, y0, frmc || rmc);   // buffers read
         if (frmc || rmc) shift_past(sm.rf);
-        __syncthreads();
         if (use_nnc) {
-            // a thread slides along MSEG medians of one row: each sorted column serves three
+            // in the same phase as the shifted copies (it reads only the staged field): a thread
+            // slides along MSEG medians of one row, each sorted column serving three of them
             for (int i = tid; i < MD * MNSEG; i += NT) {
                 const int r = i / MNSEG, c0 = (i - r * MNSEG) * MSEG;
                 auto col = [&](int c) { return psort3(sm.mv[r][c], sm.mv[r + 1][c], sm.mv[r + 2][c]); };
@@ -643,8 +664,8 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                     b = c;
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         // decide every pixel; list the ones that need a reverse check.  First the filtered vector,
         // the NNC verdict and q = p + v of all pixels of the thread, with the loads of the past
         // mask at q (and of the reverse field in RME mode) issued together; then the decisions.
