@@ -644,7 +644,7 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             }
             if (frmc || rmc) stage_past0(sm.rf, t.ref_rec[k], H, W, y0, x0);
         }
-        if (tid == 0) sm.nlist = 0;
+        if (tid == 0) sm.nlist = sm.nblist = sm.nplist = 0;
         __syncthreads();
         if (pf && k + 1 < t.K) prefetch_past(sm, t, k + 1, x0, y0, frmc || rmc);   // buffers read
         if (frmc || rmc) shift_past(sm.rf);
@@ -664,6 +664,10 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
                     b = c;
                 }
             }
+        }
+        if constexpr (T == 9) {                 // vector histogram of the listed pixels (below)
+            if (frmc)
+                for (int i = tid; i < HS * HS; i += NT) sm.hist[i] = 0;
         }
         __syncthreads();
         // decide every pixel; list the ones that need a reverse check.  First the filtered vector,
@@ -738,6 +742,9 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
             const int pi = tid + i * NT;
             sm.rej[pi] = 0;
             sm.list[atomicAdd(&sm.nlist, 1)] = (uint16_t)pi;
+            if constexpr (T == 9) {
+                if (frmc) atomicAdd(&sm.hist[(mv_y(fv[i]) + kMaxRadius) * HS + mv_x(fv[i]) + kMaxRadius], 1);
+            }
         }
         __syncthreads();
         const int nl = sm.nlist;
@@ -750,26 +757,14 @@ __device__ __forceinline__ void cc_tile(Smem &sm, const FrameTask &t, int tbx, i
         int boxbin = -1;
         if constexpr (T == 9) {
             if (frmc && nl >= BOX_MIN) {
-                for (int i = tid; i < HS * HS; i += NT) sm.hist[i] = 0;
-                __syncthreads();
-                for (int li = tid; li < nl; li += NT) {
-                    const int pi = sm.list[li], py = pi / TP, px = pi - py * TP;
-                    const uint32_t c = use_nnc ? sm.md[py + 1][px + 1] : sm.mv[py + 2][px + 2];
-                    atomicAdd(&sm.hist[(mv_y(c) + kMaxRadius) * HS + mv_x(c) + kMaxRadius], 1);
-                }
-                __syncthreads();
                 if (warp == 0) {                                  // the most frequent bin
                     uint32_t key = 0;                              // count << 10 | 1023 - bin
                     for (int i = lane; i < HS * HS; i += 32)
                         key = max(key, ((uint32_t)sm.hist[i] << 10) | (1023u - i));
                     key = __reduce_max_sync(0xffffffffu, key);
-                    if (lane == 0) {
-                        sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
-                        sm.nblist = 0;
-                        sm.nplist = 0;
-                    }
+                    if (lane == 0) sm.boxv = (int)(key >> 10) >= BOX_MIN ? 1023 - (int)(key & 1023u) : -1;
                 }
-                __syncthreads();
+                __syncthreads();                                  // before plist overwrites hist
                 boxbin = sm.boxv;
                 if (boxbin >= 0)
                     box_checks9(sm, t, x0, y0, boxbin / HS - kMaxRadius, boxbin % HS - kMaxRadius,
