@@ -103,6 +103,9 @@ def _load():
         lib.orc_better.argtypes = [I] * 8
         lib.orc_me_pixel.argtypes = [u8p, u8p, u8p, I, I, I, I, I, I, i8p, i8p]
         lib.orc_me_field.argtypes = [u8p, u8p, u8p, I, I, I, I, i8p]
+        lib.orc_me_pixel_predictive.argtypes = [u8p, u8p, u8p, I, I, I, I, I, I, I, I, I, I, i8p,
+                                                i8p]
+        lib.orc_me_field_predictive.argtypes = [u8p, u8p, u8p, I, I, I, I, I, I, i8p, i8p]
         lib.orc_nnc_field.argtypes = [i8p, I, I, i8p, u8p]
         lib.orc_check_frmc.argtypes = [u8p, u8p, u8p, I, I, I, I, I, I, I]
         lib.orc_check_rmc.argtypes = [u8p, u8p, u8p, I, I, I, I, I, I, I, I]
@@ -181,6 +184,31 @@ def me_field(smp, msk, ref, T, R) -> np.ndarray:
     mv = np.zeros((H, W, 2), dtype=np.int8)
     lib.orc_me_field(_p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(ref, C.c_uint8), H, W, T, R,
                      _p(mv, C.c_int8))
+    return mv
+
+
+def me_pixel_predictive(smp, msk, ref, T, R, Rp, k, v1, py, px) -> Tuple[int, int]:
+    """Predictive-centre search of pixel (py, px) in past frame t-k (k >= 2) around k * v1, v1 the
+    full-search vector to t-1 (an opt-in variant outside the paper)."""
+    lib = _load()
+    smp, msk, ref = _u8(smp), _u8(msk), _u8(ref)
+    H, W = smp.shape
+    a, b = C.c_int8(), C.c_int8()
+    lib.orc_me_pixel_predictive(_p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(ref, C.c_uint8), H, W,
+                                T, R, Rp, k, int(v1[0]), int(v1[1]), py, px, C.byref(a),
+                                C.byref(b))
+    return a.value, b.value
+
+
+def me_field_predictive(smp, msk, ref, T, R, Rp, k, mv1) -> np.ndarray:
+    """Predictive-centre field of past frame t-k from mv1, the full-search field of t-1."""
+    lib = _load()
+    smp, msk, ref = _u8(smp), _u8(msk), _u8(ref)
+    H, W = smp.shape
+    mv1 = np.ascontiguousarray(mv1, dtype=np.int8)
+    mv = np.zeros((H, W, 2), dtype=np.int8)
+    lib.orc_me_field_predictive(_p(smp, C.c_uint8), _p(msk, C.c_uint8), _p(ref, C.c_uint8), H, W,
+                                T, R, Rp, k, _p(mv1, C.c_int8), _p(mv, C.c_int8))
     return mv
 
 
@@ -503,8 +531,10 @@ class StepResult:
 
 def frame_step(smp, msk, history: Sequence[Tuple[np.ndarray, np.ndarray, np.ndarray]],
                cc_mode: int = CC_NNC_FRMC, T: int = 9, R: int = 8, Rc: Optional[int] = None,
-               fsr: Optional[FsrParams] = None, run_fsr: bool = True) -> StepResult:
-    """history[k-1] = (reconstructed frame, sample plane, mask) of frame t-k, k = 1..K_eff."""
+               fsr: Optional[FsrParams] = None, run_fsr: bool = True,
+               me_predict_radius: int = 0) -> StepResult:
+    """history[k-1] = (reconstructed frame, sample plane, mask) of frame t-k, k = 1..K_eff.
+    me_predict_radius > 0: past frames t-2.. use the predictive-centre search around k v_1."""
     Rc = R if Rc is None else Rc
     fsr = FsrParams() if fsr is None else fsr
     smp, msk = _u8(smp), _u8(msk)
@@ -512,8 +542,11 @@ def frame_step(smp, msk, history: Sequence[Tuple[np.ndarray, np.ndarray, np.ndar
     psum = np.zeros((H, W), np.uint16)
     pcnt = np.zeros((H, W), np.uint8)
     mvs, fmvs, decs = [], [], []
-    for rec_k, smp_k, msk_k in history:
-        mv = me_field(smp, msk, rec_k, T, R)
+    for k, (rec_k, smp_k, msk_k) in enumerate(history, start=1):
+        if me_predict_radius > 0 and k >= 2:
+            mv = me_field_predictive(smp, msk, rec_k, T, R, me_predict_radius, k, mvs[0])
+        else:
+            mv = me_field(smp, msk, rec_k, T, R)
         fmv, dec, psum, pcnt = cc_project(cc_mode, T, R, Rc, smp, msk, rec_k, smp_k, msk_k, mv,
                                           psum, pcnt)
         mvs.append(mv)

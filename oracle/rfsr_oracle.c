@@ -12,6 +12,7 @@
  *   orc_cost ........ template-matching cost of Sec. 2.2 (masked SAD over a T x T template of the
  *                     current frame's measured pixels against a reconstructed past frame)
  *   orc_me_pixel .... pixel-wise motion estimation of Sec. 2.2 (argmin over the search window)
+ *   orc_me_pixel_predictive  the opt-in predictive-centre search (not in the paper)
  *   orc_nnc_field ... nearest neighbour check, Sec. 3.1.2 and Eq. (1)
  *   orc_check_* ..... reverse motion estimation RME (Sec. 2.2), reverse motion check RMC and fast
  *                     reverse motion check FRMC (Sec. 3.1.1, Fig. 2b/2c)
@@ -139,6 +140,46 @@ void orc_me_field(const uint8_t *smp, const uint8_t *msk, const uint8_t *ref, in
         for (int x = 0; x < W; ++x)
             orc_me_pixel(smp, msk, ref, H, W, T, R, y, x, &mv[2 * ((size_t)y * W + x)],
                          &mv[2 * ((size_t)y * W + x) + 1]);
+}
+
+/* Predictive-centre search, an opt-in variant that the paper does not describe (it changes the
+ * method's results): past frame t-k, k >= 2, is searched only within radius Rp of the prediction
+ * k v1(p), where v1 is the full-search vector of p to frame t-1.  The prediction is clamped into
+ * [-R, R]^2 and so that p + c lies in the frame; the candidates are the v of c + [-Rp, Rp]^2 that
+ * lie in [-R, R]^2 with p + v in the frame, ranked by the same cost and tie order as
+ * orc_me_pixel.  k is the past frame's distance (2 for t-2). */
+void orc_me_pixel_predictive(const uint8_t *smp, const uint8_t *msk, const uint8_t *ref, int H,
+                             int W, int T, int R, int Rp, int k, int v1y, int v1x, int py, int px,
+                             int8_t *vy_out, int8_t *vx_out)
+{
+    int cy = clampi(k * v1y, -R > -py ? -R : -py, R < H - 1 - py ? R : H - 1 - py);
+    int cx = clampi(k * v1x, -R > -px ? -R : -px, R < W - 1 - px ? R : W - 1 - px);
+    int bs = 0, bn = 0, by = 0, bx = 0, have = 0;
+    for (int vy = cy - Rp; vy <= cy + Rp; ++vy) {
+        for (int vx = cx - Rp; vx <= cx + Rp; ++vx) {
+            if (iabs(vy) > R || iabs(vx) > R || !inside(py + vy, px + vx, H, W)) continue;
+            int s, n;
+            orc_cost(smp, msk, ref, H, W, T, py, px, vy, vx, &s, &n);
+            if (!have || orc_better(s, n, vy, vx, bs, bn, by, bx)) {
+                bs = s; bn = n; by = vy; bx = vx; have = 1;
+            }
+        }
+    }
+    *vy_out = (int8_t)by;
+    *vx_out = (int8_t)bx;
+}
+
+/* the predictive field of past frame t-k from the field mv1 of t-1 (same layout as mv) */
+void orc_me_field_predictive(const uint8_t *smp, const uint8_t *msk, const uint8_t *ref, int H,
+                             int W, int T, int R, int Rp, int k, const int8_t *mv1, int8_t *mv)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t i = 2 * ((size_t)y * W + x);
+            orc_me_pixel_predictive(smp, msk, ref, H, W, T, R, Rp, k, mv1[i], mv1[i + 1], y, x,
+                                    &mv[i], &mv[i + 1]);
+        }
 }
 
 /* ---------------------------------------------------------------------------------------------
