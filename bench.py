@@ -398,6 +398,49 @@ def run_check_modes(rfsr, torch, steps=8):
     return out
 
 
+def run_me_predictive(rfsr, torch, radii=(0, 2, 4), steps=8):
+    """The opt-in predictive-centre ME (past frames t-2, t-3 searched within radius Rp of k v_1;
+    not the paper's method) on the 1080p workload: device time of ME and of checks + projection,
+    the ME+CC+PR rate and the projected fraction over frames with 3 past frames (free-running),
+    and, on one teacher-forced frame, the share of t-2 / t-3 vectors that differ from the full
+    search.  Rp = 0 is the full search (the metric's configuration)."""
+    seq = synth.config3(seed=1, F=3 + steps)
+    h, w = seq.shape
+    d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
+    t = 3 + steps - 1
+    hist = [(seq.frames[t - k], seq.samples[t - k], seq.masks[t - k]) for k in (1, 2, 3)]
+    out, exact = {}, None
+    for rp in radii:
+        with rfsr.Engine(device=torch.cuda.current_device(), profile=True) as eng:
+            st = eng.create_stream(height=h, width=w, cc_mode="nnc_frmc", template_size=T,
+                                   search_radius=R, num_refs=KREF, me_predict_radius=rp)
+            ph, proj = [], []
+            for f in range(3 + steps):
+                st.push_frame_device(d_smp[f], d_msk[f])
+                st.get_frame_device(timeout_ms=120000)
+                if f >= 3:
+                    ph.append(st.phase_ms())
+                    miss = seq.masks[f] == 0
+                    proj.append(float((st.debug_get(rfsr.DBG_PCNT)[miss] > 0).mean()))
+            st.set_history(hist)
+            st.push_frame(seq.samples[t], seq.masks[t])
+            st.get_frame(timeout_ms=120000)
+            mv = [st.debug_get(rfsr.DBG_MV, k) for k in (2, 3)]
+        a = np.array(ph).mean(axis=0)
+        if exact is None:
+            exact = mv
+        out[f"rp_{rp}"] = {
+            "me_ms": round(float(a[1]), 4), "cc_pr_ms": round(float(a[2]), 4),
+            "me_cc_pr_mpix_s": round(h * w / ((a[0] + a[1] + a[2]) / 1e3) / 1e6, 3),
+            "projected_frac": round(float(np.mean(proj)), 4),
+            "vectors_changed_frac": [round(float((m != e).any(axis=-1).mean()), 4)
+                                     for m, e in zip(mv, exact)]}
+    out["workload"] = (f"1920x1080 workload, NNC+FRMC, K=3, T=9, R=8, frames 3..{2 + steps} "
+                       f"free-running; changed vectors of t-2 / t-3 on frame {t} with the "
+                       f"generator's frames as history; rp_0 = the full search")
+    return out
+
+
 def run_concealed(rfsr, torch, delta=0.5, frames=3):
     """Stand-alone FSR (rfsr_fsr_device) of one 1080p frame of the workload with concealed weighting
     delta > 0 (wavefronts, one launch per wave) against delta = 0 (all blocks in one launch):
@@ -760,7 +803,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = job_rate(args.steps, world, HW, e_s)
     eng.destroy()
     del d_smp, d_msk, flush
-    batching = serving = check_modes = concealed = None
+    batching = serving = check_modes = concealed = me_predictive = None
     if not args.no_serving:
         batching = run_batching(rfsr, torch)
         batching["small_frames"] = run_batching(
@@ -768,6 +811,7 @@ def run_ours(args, rank, world, local_rank):
         serving = run_serving_all(rfsr, torch)
         check_modes = run_check_modes(rfsr, torch)
         concealed = run_concealed(rfsr, torch)
+        me_predictive = run_me_predictive(rfsr, torch)
 
     if rank != 0:
         return
@@ -852,6 +896,7 @@ def run_ours(args, rank, world, local_rank):
         "serving": serving,
         "check_modes": check_modes,
         "concealed_fsr": concealed,
+        "me_predictive": me_predictive,
     }
     print(json.dumps(line), flush=True)
 

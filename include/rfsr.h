@@ -150,6 +150,13 @@ typedef struct {
                               selection is an argmax, so this makes the FP32 result checkable
                               against an FP64 replay of the same selections.  Costs
                               2 * iterations bytes per block of device memory.  0 (default): off */
+    int me_predict_radius; /* 0 (default): every past frame gets the full ME search of Sec. 2.2.
+                              Rp > 0: an opt-in variant that the paper does not describe and that
+                              changes its results: frame t-k, k >= 2, is searched only within
+                              radius Rp of the prediction k v_1(p) (v_1 = the vector to t-1,
+                              clamped to [-R, R]^2 and into the frame), still inside [-R, R]^2,
+                              same cost and tie order; Rp >= 2R equals the full search.  1..18;
+                              needs template_size 9 and an unbatched engine (EINVAL otherwise) */
 } rfsr_stream_config;
 
 /* Fill a config with the defaults above (1280x720, NNC_FRMC, K=3, T=9, R=8). */
@@ -311,7 +318,7 @@ typedef struct {
     int64_t frames;              /* frames the exported stream had processed                       */
 } rfsr_state_header;
 #define RFSR_STATE_MAGIC 0x54534652u   /* "RFST" */
-#define RFSR_STATE_VERSION 3u
+#define RFSR_STATE_VERSION 4u
 
 /* Export s into buf (cap bytes); *bytes receives the size needed (buf == NULL: size query).
  * Taken between frames: every pushed frame must have been collected.

@@ -601,6 +601,152 @@ __global__ void __launch_bounds__(R9_NT, 2) rme9_batched_kernel(BatchDesc *bd)
     });
 }
 
+// ---------------------------------------------------------------------------------------------
+// Predictive-centre search for references k >= 2 (an opt-in variant that the paper does not
+// describe; it changes the method's results).  Motion to frame t-k is predicted as k v_1(p),
+// v_1 the exact vector to frame t-1, and only the window of radius Rp around that prediction is
+// searched, within [-R, R]^2 so that every later stage keeps its layout:
+//     c = (clamp(k v_1y, max(-R, -y), min(R, H-1-y)), clamp(k v_1x, max(-R, -x), min(R, W-1-x)))
+//     v_k(p) = argmin over v in (c + [-Rp, Rp]^2) n [-R, R]^2 with p + v inside the frame of
+//              C(p, v), the same cost and tie order as the full search (Sec. 2.2).
+// The clamp keeps p + c inside the frame, so the centre is always a candidate, and Rp >= 2R
+// covers the whole window: the result is then the full search's.
+// GB300 design: one CTA per 32x32 output tile and reference; a thread takes four pixels, keeps
+// each pixel's template (masked samples and byte masks, 9 rows of 3 words) in registers and
+// scores the window's candidates with three `vabsdiff4.add` per row against the past-frame
+// window staged in four byte-shifted copies.  Candidates differ per pixel, so the strip and
+// box-sum layouts (which share candidates across pixels) do not apply; the window is small.
+// ---------------------------------------------------------------------------------------------
+constexpr int P_TS = 32;                           // output tile side
+constexpr int P_NT = 256;
+constexpr int P_RROWS = P_TS + 8 + 2 * kMaxRadius; // staged past-frame rows (58)
+constexpr int P_RWORDS = 17;                       // words per staged past-frame row (from x0 - 16)
+constexpr int P_RCPY = P_RROWS * P_RWORDS + 14;    // copy stride = 8 (mod 32) words: the four
+                                                   // copies of one word lie in distinct banks
+constexpr int P_CROWS = P_TS + 8;                  // staged current rows (40)
+constexpr int P_CWORDS = 11;                       // words per staged current row (from x0 - 4)
+static_assert(P_RCPY % 32 == 8, "past-frame copy stride");
+static_assert((P_TS - 1) + 12 + kMaxRadius + 11 < 4 * (P_RWORDS - 1), "shifted past-frame words cover the reads");
+
+struct SmemP {
+    uint32_t rf[4 * P_RCPY];                       // past frame, clamped coordinates
+    uint2 cur[4][P_CROWS * P_CWORDS];              // (masked samples, byte mask) words
+    short2 vord[NVMAX];
+    uint16_t rank[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];   // tie-order position of v
+};
+
+__device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t acc)
+{
+    uint32_t d;
+    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(acc));
+    return d;
+}
+
+__global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
+{
+    __shared__ __align__(16) SmemP sm;
+    const int k = blockIdx.z + 1;                  // reference t-(k+1); its field is t.mv[k]
+    const int x0 = blockIdx.x * P_TS, y0 = blockIdx.y * P_TS;
+    const int H = t.H, W = t.W, R = t.R, Rp = t.me_pred, tid = threadIdx.x;
+    if (*t.status) return;
+    const uint8_t *ref = t.ref_rec[k];
+
+    // past frame: rows y0 - 4 - 9 .., words from column x0 - 16, clamped coordinates
+    const bool al = (W & 3) == 0 && ((uintptr_t)ref & 3) == 0;
+    for (int i = tid; i < P_RROWS * P_RWORDS; i += P_NT) {
+        const int r = i / P_RWORDS, w = i - r * P_RWORDS;
+        const uint8_t *row = ref + (size_t)min(max(y0 - 4 - kMaxRadius + r, 0), H - 1) * W;
+        const int gx = x0 - 16 + 4 * w;
+        uint32_t v = 0;
+        if (al && gx >= 0 && gx + 4 <= W) {
+            v = *reinterpret_cast<const uint32_t *>(row + gx);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v |= (uint32_t)row[min(max(gx + b, 0), W - 1)] << (8 * b);
+        }
+        sm.rf[i] = v;
+    }
+    // current frame: rows y0 - 4 .., words from column x0 - 4 (0 outside the frame)
+    for (int i = tid; i < P_CROWS * P_CWORDS; i += P_NT) {
+        const int r = i / P_CWORDS, w = i - r * P_CWORDS;
+        const int gy = y0 - 4 + r, gx = x0 - 4 + 4 * w;
+        uint32_t a = 0, m = 0;
+        if (gy >= 0 && gy < H) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int x = gx + b;
+                if (x >= 0 && x < W) {
+                    a |= (uint32_t)t.cur_smp[(size_t)gy * W + x] << (8 * b);
+                    m |= (uint32_t)t.cur_msk[(size_t)gy * W + x] << (8 * b);
+                }
+            }
+        }
+        sm.cur[0][i] = make_uint2(a, m);
+    }
+    build_tie_order(sm.vord, R);
+    __syncthreads();
+    for (int i = tid; i < 3 * P_RROWS * (P_RWORDS - 1); i += P_NT) {
+        const int j = 1 + i / (P_RROWS * (P_RWORDS - 1));
+        const int rem = i - (j - 1) * P_RROWS * (P_RWORDS - 1);
+        const int r = rem / (P_RWORDS - 1), w = rem - r * (P_RWORDS - 1);
+        sm.rf[j * P_RCPY + r * P_RWORDS + w] =
+            __funnelshift_r(sm.rf[r * P_RWORDS + w], sm.rf[r * P_RWORDS + w + 1], 8 * j);
+    }
+    for (int i = tid; i < 3 * P_CROWS * (P_CWORDS - 1); i += P_NT) {
+        const int j = 1 + i / (P_CROWS * (P_CWORDS - 1));
+        const int rem = i - (j - 1) * P_CROWS * (P_CWORDS - 1);
+        const int r = rem / (P_CWORDS - 1), w = rem - r * (P_CWORDS - 1);
+        const uint2 a = sm.cur[0][r * P_CWORDS + w], b = sm.cur[0][r * P_CWORDS + w + 1];
+        sm.cur[j][r * P_CWORDS + w] = make_uint2(__funnelshift_r(a.x, b.x, 8 * j),
+                                                 __funnelshift_r(a.y, b.y, 8 * j));
+    }
+    const int nv = (2 * R + 1) * (2 * R + 1);
+    for (int i = tid; i < nv; i += P_NT) {
+        const short2 v = sm.vord[i];
+        sm.rank[(v.x + kMaxRadius) * (2 * kMaxRadius + 1) + v.y + kMaxRadius] = (uint16_t)i;
+    }
+    __syncthreads();
+
+    const char2 *mv1 = reinterpret_cast<const char2 *>(t.mv[0]);
+    char2 *mvk = reinterpret_cast<char2 *>(t.mv[k]);
+    for (int pi = tid; pi < P_TS * P_TS; pi += P_NT) {
+        const int py = pi / P_TS, px = pi - py * P_TS, y = y0 + py, x = x0 + px;
+        if (y >= H || x >= W) continue;
+        uint32_t cs[9][3], cm[9][3];               // template: masked samples and byte masks
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                const uint2 c = sm.cur[px & 3][(py + r) * P_CWORDS + (px >> 2) + w];
+                const uint32_t keep = w == 2 ? 0xffu : 0xffffffffu;   // template columns 0..8
+                cs[r][w] = c.x & keep;
+                cm[r][w] = c.y & keep;
+            }
+        const char2 p1 = mv1[(size_t)y * W + x];
+        const int cy = min(max((k + 1) * (int)p1.x, max(-R, -y)), min(R, H - 1 - y));
+        const int cx = min(max((k + 1) * (int)p1.y, max(-R, -x)), min(R, W - 1 - x));
+        uint32_t best = 0xffffffffu;               // SAD << 9 | position in the tie order
+        for (int vy = max(cy - Rp, -R); vy <= min(cy + Rp, R); ++vy) {
+            if ((unsigned)(y + vy) >= (unsigned)H) continue;
+            for (int vx = max(cx - Rp, -R); vx <= min(cx + Rp, R); ++vx) {
+                if ((unsigned)(x + vx) >= (unsigned)W) continue;
+                const int rc = px + 12 + vx;      // staged column of the template's first byte
+                const uint32_t *rr = sm.rf + (rc & 3) * P_RCPY + (py + vy + kMaxRadius) * P_RWORDS + (rc >> 2);
+                uint32_t acc = 0;
+#pragma unroll
+                for (int r = 0; r < 9; ++r)
+#pragma unroll
+                    for (int w = 0; w < 3; ++w) acc = sad4(cs[r][w], rr[r * P_RWORDS + w] & cm[r][w], acc);
+                const uint32_t key = (acc << 9) |
+                    sm.rank[(vy + kMaxRadius) * (2 * kMaxRadius + 1) + vx + kMaxRadius];
+                best = min(best, key);
+            }
+        }
+        const short2 v = sm.vord[best & 511u];
+        mvk[(size_t)y * W + x] = make_char2((signed char)v.x, (signed char)v.y);
+    }
+}
+
 }  // namespace
 
 cudaError_t init_me(int dev)
@@ -637,8 +783,17 @@ cudaError_t launch_me(const FrameTask &t, cudaStream_t st)
         if (e == cudaSuccess) e = init_me(dev);
         if (e != cudaSuccess) return e;
         constexpr int outh = s_outh<kMeWarps, kMeRows>();
-        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + outh - 1) / outh, t.K);
+        // predictive-centre variant: the full search for t-1 only, then the windows around k v_1
+        const bool pred = t.me_pred > 0 && t.K > 1;
+        dim3 grid((t.W + S_OUTW - 1) / S_OUTW, (t.H + outh - 1) / outh, pred ? 1 : t.K);
         me9_kernel<<<grid, s_nt<kMeWarps>(), sizeof(Smem9<kMeWarps, kMeRows>), st>>>(t);
+        if (pred) {
+            count_launch();
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            dim3 pgrid((t.W + P_TS - 1) / P_TS, (t.H + P_TS - 1) / P_TS, t.K - 1);
+            me_pred_kernel<<<pgrid, P_NT, 0, st>>>(t);
+        }
     } else {
         dim3 grid((t.W + TW - 1) / TW, (t.H + TH - 1) / TH, t.K);
         me_kernel<<<grid, NT, 0, st>>>(t);

@@ -87,6 +87,9 @@ extern "C" int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const u
     if (cfg->search_radius < 1 || cfg->search_radius > kMaxRadius ||
         cfg->check_radius < 1 || cfg->check_radius > kMaxRadius)
         return set_error(RFSR_EINVAL, std::string(what) + "search / check radius must be 1..9");
+    if (cfg->me_predict_radius < 0 || cfg->me_predict_radius > 2 * kMaxRadius ||
+        (cfg->me_predict_radius > 0 && cfg->template_size != 9))
+        return set_error(RFSR_EINVAL, std::string(what) + "me_predict_radius must be 0..18 (T = 9 when > 0)");
     if ((((uintptr_t)d_smp | (uintptr_t)d_msk | (uintptr_t)d_psum) & 1u) ||
         ((uintptr_t)d_status & 3u))
         return set_error(RFSR_EINVAL, std::string(what) + "misaligned buffer");
@@ -118,6 +121,7 @@ extern "C" int rfsr_me_cc_project_noalloc(const rfsr_stream_config *cfg, const u
     t.T = cfg->template_size;
     t.R = cfg->search_radius;
     t.Rc = cfg->check_radius;
+    t.me_pred = cfg->me_predict_radius;
     t.cc_mode = cfg->cc_mode;
     t.status = reinterpret_cast<int *>(take(kAlign));
     t.prev_status = nullptr;

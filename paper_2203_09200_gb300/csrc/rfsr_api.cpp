@@ -400,6 +400,7 @@ void prepare_frame(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const ui
     t.T = s->cfg.template_size;
     t.R = s->cfg.search_radius;
     t.Rc = s->cfg.check_radius;
+    t.me_pred = s->cfg.me_predict_radius;
     t.cc_mode = s->cfg.cc_mode;
     t.fsr_iters = s->cfg.fsr_iterations;
     t.fsr_gamma = s->cfg.fsr_gamma;
@@ -976,6 +977,10 @@ static int check_stream_config(const rfsr_stream_config *c)
     if (!(c->fsr_concealed_weight >= 0.f && c->fsr_concealed_weight <= 1e6f))
         return fail(RFSR_EINVAL, "stream config: fsr_concealed_weight must be >= 0");
     if (c->fsr_trace != 0 && c->fsr_trace != 1) return fail(RFSR_EINVAL, "stream config: fsr_trace must be 0 or 1");
+    if (c->me_predict_radius < 0 || c->me_predict_radius > 2 * kMaxRadius)
+        return fail(RFSR_EINVAL, "stream config: me_predict_radius must be 0..18");
+    if (c->me_predict_radius > 0 && c->template_size != 9)
+        return fail(RFSR_EINVAL, "stream config: me_predict_radius needs template_size 9");
     return RFSR_OK;
 }
 
@@ -1012,6 +1017,8 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
     }
     int rc = check_stream_config(cfg);
     if (rc) return rc;
+    if (cfg->me_predict_radius > 0 && batched(e))
+        return fail(RFSR_EINVAL, "create_stream: me_predict_radius needs an unbatched engine");
     CK(cudaSetDevice(e->cfg.device));
     auto *s = new rfsr_stream();
     s->eng = e;

@@ -28,6 +28,7 @@ struct FrameTask {
     int H, W;
     int K;              // references actually used for this frame (0..kMaxRefs)
     int T, R, Rc;
+    int me_pred;        // predictive-centre window radius for references 2..K (0: full search)
     int cc_mode;
     // FSR
     int fsr_iters;

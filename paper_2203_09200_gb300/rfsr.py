@@ -52,7 +52,7 @@ class rfsr_stream_config(C.Structure):
                 ("fsr_iterations", C.c_int), ("fsr_rho", C.c_float), ("fsr_gamma", C.c_float),
                 ("fsr_proj_weight", C.c_float), ("fsr_overwrite_projected", C.c_int),
                 ("keep_f32", C.c_int), ("fsr_concealed_weight", C.c_float),
-                ("fsr_trace", C.c_int)]
+                ("fsr_trace", C.c_int), ("me_predict_radius", C.c_int)]
 
 
 class rfsr_batch_shape(C.Structure):
@@ -185,7 +185,8 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
                   check_radius: Optional[int] = None, fsr_iterations: int = 100,
                   fsr_rho: float = 0.7, fsr_gamma: float = 0.5, fsr_proj_weight: float = 1.0,
                   fsr_overwrite_projected: bool = False, keep_f32: bool = False,
-                  fsr_concealed_weight: float = 0.0, fsr_trace: bool = False) -> rfsr_stream_config:
+                  fsr_concealed_weight: float = 0.0, fsr_trace: bool = False,
+                  me_predict_radius: int = 0) -> rfsr_stream_config:
     c = rfsr_stream_config()
     load().rfsr_stream_config_default(C.byref(c))
     c.height, c.width = height, width
@@ -201,6 +202,7 @@ def stream_config(height: int, width: int, cc_mode="nnc_frmc", mask_type: int = 
     c.keep_f32 = int(bool(keep_f32))
     c.fsr_concealed_weight = fsr_concealed_weight
     c.fsr_trace = int(bool(fsr_trace))
+    c.me_predict_radius = me_predict_radius
     return c
 
 
