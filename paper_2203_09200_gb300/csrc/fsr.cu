@@ -216,6 +216,30 @@ __device__ __forceinline__ void column_dft(float2 *a, int c)
     for (int k = 0; k < N; ++k) a[k * NH + c] = make_float2(re[k], im[k]);
 }
 
+// 32-point complex DFTs of columns c and c + 1 of a [32][17] array, in place, by the whole warp:
+// lane m holds element m of both; radix-2 decimation in frequency over shuffles leaves X[k] in
+// lane bitrev(k).  Every lane runs the same instructions (the butterfly's sum and its twiddled
+// difference are both formed and one is kept), with the twiddles from the shared-memory table.
+__device__ __forceinline__ void warp_column_dft2(float2 *a, int c, const float *cs, const float *sn,
+                                                 int lane)
+{
+    float2 x = a[lane * NH + c], y = a[lane * NH + c + 1];
+#pragma unroll
+    for (int h = N / 2; h >= 1; h >>= 1) {
+        const float xr = __shfl_xor_sync(0xffffffffu, x.x, h), xi = __shfl_xor_sync(0xffffffffu, x.y, h);
+        const float yr = __shfl_xor_sync(0xffffffffu, y.x, h), yi = __shfl_xor_sync(0xffffffffu, y.y, h);
+        const bool upper = (lane & h) != 0;               // element b of its butterfly
+        const int j = (lane & (h - 1)) * (N / (2 * h));   // W_{2h}^(t - h) = W_32^j
+        const float wr = cs[j], wi = -sn[j];
+        const float dxr = xr - x.x, dxi = xi - x.y, dyr = yr - y.x, dyi = yi - y.y;
+        x = upper ? make_float2(dxr * wr - dxi * wi, dxr * wi + dxi * wr) : make_float2(x.x + xr, x.y + xi);
+        y = upper ? make_float2(dyr * wr - dyi * wi, dyr * wi + dyi * wr) : make_float2(y.x + yr, y.y + yi);
+    }
+    const int k = (int)(__brev((unsigned)lane) >> (32 - 5));
+    a[k * NH + c] = x;
+    a[k * NH + c + 1] = y;
+}
+
 // Support row m (frame row y) at support column `lane` (frame column x) of block (bi, bj): the
 // weight rho^d (x mu for projected pixels, x delta for concealed ones) and the weighted value.
 __device__ __forceinline__ void support_row(WarpSmem &ws, const FsrArgs &a, int m, int x, int y,
@@ -308,9 +332,10 @@ __device__ __forceinline__ void fsr_block(const Twiddles &tw, WarpSmem &ws, cons
     }
     __syncwarp();
 
-    // 3. column DFTs in place: 34 columns over 32 lanes (17 of W, then 17 of R)
+    // 3. column DFTs in place: 34 columns (17 of W, then 17 of R): one per lane, and the last two
+    //    by the whole warp together, rather than by two lanes while the other 30 wait
     column_dft(lane < NH ? ws.dft.w : ws.dft.f, lane < NH ? lane : lane - NH);
-    if (lane < 2) column_dft(ws.dft.f, N - NH + lane);
+    warp_column_dft2(ws.dft.f, N - NH, tw.cs, tw.sn, lane);
     __syncwarp();
 
     // 4. 17 bins of the half spectrum per lane in registers.  Lane k <= 16 holds R(k, s), lane
