@@ -929,7 +929,8 @@ def summarize_launches(path):
 
 def run_ncu_case(args):
     """A short, untimed kernel sequence for an ncu capture: 'frame_step' runs `frames` frames of
-    the 1080p workload on one unbatched stream (device-resident inputs, check mode --cc-mode);
+    the 1080p workload on one unbatched stream (device-resident inputs, check mode --cc-mode,
+    predictive-centre ME radius --me-predict-radius);
     'batched' runs `frames` batched steps of --streams streams of the uneven-size mix (default
     tile shape, no autotuning)."""
     import torch
@@ -943,7 +944,8 @@ def run_ncu_case(args):
         d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
         with rfsr.Engine(device=0) as eng:
             st = eng.create_stream(height=H, width=W, cc_mode=args.cc_mode, template_size=T,
-                                   search_radius=R, num_refs=KREF, fsr_iterations=ITERS)
+                                   search_radius=R, num_refs=KREF, fsr_iterations=ITERS,
+                                   me_predict_radius=args.me_predict_radius)
             for f in range(nf):
                 st.push_frame_device(d_smp[f], d_msk[f])
                 st.get_frame_device(timeout_ms=120000)
@@ -980,6 +982,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--streams", type=int, default=64, help="streams of --ncu-case batched")
     ap.add_argument("--cc-mode", default="nnc_frmc", choices=list(MODES),
                     help="consistency-check mode of --ncu-case frame_step")
+    ap.add_argument("--me-predict-radius", type=int, default=0,
+                    help="predictive-centre ME radius of --ncu-case frame_step (0: full search)")
     ap.add_argument("--serving-full", action="store_true",
                     help="print the serving report with every stream's full U{30..300} frames and "
                          "exit (the default run plays a tenth of each stream's frames)")

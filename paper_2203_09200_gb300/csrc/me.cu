@@ -611,28 +611,69 @@ __global__ void __launch_bounds__(R9_NT, 2) rme9_batched_kernel(BatchDesc *bd)
 //              C(p, v), the same cost and tie order as the full search (Sec. 2.2).
 // The clamp keeps p + c inside the frame, so the centre is always a candidate, and Rp >= 2R
 // covers the whole window: the result is then the full search's.
-// GB300 design: one CTA per 32x32 output tile and reference; a thread takes four pixels, keeps
-// each pixel's template (masked samples and byte masks, 9 rows of 3 words) in registers and
-// scores the window's candidates with three `vabsdiff4.add` per row against the past-frame
-// window staged in four byte-shifted copies.  Candidates differ per pixel, so the strip and
-// box-sum layouts (which share candidates across pixels) do not apply; the window is small.
+// GB300 design: one CTA per 32x32 output tile and reference, the current frame and the past
+// frame (with its +-9 margin) staged in four byte-shifted copies.  Each pixel has its own window,
+// so the candidate sharing of the full search does not carry over directly.  Most pixels of a
+// tile share one predicted centre, however (coherent motion), and for the most frequent centre
+// c* of a tile, if at least P_DENSE_MIN pixels have it, the window c* + [-Rp, Rp]^2 is searched
+// densely: each warp takes some of its candidates and computes the candidate's cost at every
+// tile pixel by separable 9 x 9 box sums of the masked absolute-difference plane (the forward
+// ME's packed vertical sums and shuffle horizontal sums), keeping per pixel the smallest key
+// SAD << 9 | tie position; the warps' keys meet in shared memory (atomicMin).  The other pixels
+// are searched one by one: a thread keeps the pixel's template (masked samples and byte masks,
+// 9 rows of 3 words) in registers and scores its window with `vabsdiff4.add` per word.
 // ---------------------------------------------------------------------------------------------
 constexpr int P_TS = 32;                           // output tile side
 constexpr int P_NT = 256;
-constexpr int P_RROWS = P_TS + 8 + 2 * kMaxRadius; // staged past-frame rows (58)
+constexpr int P_NW = P_NT / 32;
+constexpr int P_RROWS = P_TS + 8 + 2 * kMaxRadius + 2;   // staged past-frame rows (60; the dense
+                                                   // pass's third row band reads one row past)
 constexpr int P_RWORDS = 17;                       // words per staged past-frame row (from x0 - 16)
-constexpr int P_RCPY = P_RROWS * P_RWORDS + 14;    // copy stride = 8 (mod 32) words: the four
+constexpr int P_RCPY = P_RROWS * P_RWORDS + 12;    // copy stride = 8 (mod 32) words: the four
                                                    // copies of one word lie in distinct banks
-constexpr int P_CROWS = P_TS + 8;                  // staged current rows (40)
+constexpr int P_CROWS = P_TS + 8 + 2;              // staged current rows (42, likewise)
 constexpr int P_CWORDS = 11;                       // words per staged current row (from x0 - 4)
+constexpr int P_DENSE_MIN = 128;                   // pixels of one centre that pay for a dense pass
+constexpr int P_HS = 2 * kMaxRadius + 1;
 static_assert(P_RCPY % 32 == 8, "past-frame copy stride");
 static_assert((P_TS - 1) + 12 + kMaxRadius + 11 < 4 * (P_RWORDS - 1), "shifted past-frame words cover the reads");
+
+// The tie order (|v|_1, v_y, v_x) over [-9, 9]^2, built at compile time: position of every v and
+// the vector at every position.  Restricted to [-R, R]^2 it keeps its relative order, so it
+// ranks the candidates of every R.
+struct TieTables {
+    uint16_t rank[P_HS * P_HS];                    // bin (v_y + 9) * 19 + v_x + 9 -> position
+    uint16_t bin[P_HS * P_HS];                     // position -> bin
+};
+constexpr TieTables make_tie_tables()
+{
+    TieTables t{};
+    int n = 0;
+    for (int L = 0; L <= 2 * kMaxRadius; ++L)
+        for (int vy = -kMaxRadius; vy <= kMaxRadius; ++vy) {
+            const int ax = L - (vy < 0 ? -vy : vy);
+            if (ax < 0 || ax > kMaxRadius) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                if (ax == 0 && s > 0) break;
+                const int b = (vy + kMaxRadius) * P_HS + s * ax + kMaxRadius;
+                t.rank[b] = (uint16_t)n;
+                t.bin[n++] = (uint16_t)b;
+            }
+        }
+    return t;
+}
+__constant__ TieTables c_tie = make_tie_tables();
 
 struct SmemP {
     uint32_t rf[4 * P_RCPY];                       // past frame, clamped coordinates
     uint2 cur[4][P_CROWS * P_CWORDS];              // (masked samples, byte mask) words
-    short2 vord[NVMAX];
-    uint16_t rank[(2 * kMaxRadius + 1) * (2 * kMaxRadius + 1)];   // tie-order position of v
+    TieTables tie;
+    uint16_t cen[P_TS * P_TS];                     // predicted centre of each tile pixel (bin)
+    uint16_t plist[P_TS * P_TS];                   // pixels searched one by one
+    int hist[P_HS * P_HS];                         // tile pixels per centre
+    uint32_t dkey[P_TS * P_TS];                    // dense pass: best key per tile pixel
+    int cstar;                                     // centre searched densely (bin), -1: none
+    int np;
 };
 
 __device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t acc)
@@ -642,14 +683,24 @@ __device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b, uint32_t acc)
     return d;
 }
 
+// predicted centre of pixel (y, x) for reference distance kk from its t-1 vector p1
+__device__ __forceinline__ int pred_centre(char2 p1, int kk, int y, int x, int H, int W, int R)
+{
+    const int cy = min(max(kk * (int)p1.x, max(-R, -y)), min(R, H - 1 - y));
+    const int cx = min(max(kk * (int)p1.y, max(-R, -x)), min(R, W - 1 - x));
+    return (cy + kMaxRadius) * P_HS + cx + kMaxRadius;
+}
+
 __global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
 {
     __shared__ __align__(16) SmemP sm;
     const int k = blockIdx.z + 1;                  // reference t-(k+1); its field is t.mv[k]
     const int x0 = blockIdx.x * P_TS, y0 = blockIdx.y * P_TS;
     const int H = t.H, W = t.W, R = t.R, Rp = t.me_pred, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     if (*t.status) return;
     const uint8_t *ref = t.ref_rec[k];
+    const char2 *mv1 = reinterpret_cast<const char2 *>(t.mv[0]);
 
     // past frame: rows y0 - 4 - 9 .., words from column x0 - 16, clamped coordinates
     const bool al = (W & 3) == 0 && ((uintptr_t)ref & 3) == 0;
@@ -667,23 +718,35 @@ __global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
         sm.rf[i] = v;
     }
     // current frame: rows y0 - 4 .., words from column x0 - 4 (0 outside the frame)
+    const bool alc = (W & 3) == 0 && (((uintptr_t)t.cur_smp | (uintptr_t)t.cur_msk) & 3) == 0;
     for (int i = tid; i < P_CROWS * P_CWORDS; i += P_NT) {
         const int r = i / P_CWORDS, w = i - r * P_CWORDS;
         const int gy = y0 - 4 + r, gx = x0 - 4 + 4 * w;
         uint32_t a = 0, m = 0;
         if (gy >= 0 && gy < H) {
+            const size_t ro = (size_t)gy * W;
+            if (alc && gx >= 0 && gx + 4 <= W) {       // gx is a multiple of 4
+                a = *reinterpret_cast<const uint32_t *>(t.cur_smp + ro + gx);
+                m = *reinterpret_cast<const uint32_t *>(t.cur_msk + ro + gx);
+            } else {
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int x = gx + b;
-                if (x >= 0 && x < W) {
-                    a |= (uint32_t)t.cur_smp[(size_t)gy * W + x] << (8 * b);
-                    m |= (uint32_t)t.cur_msk[(size_t)gy * W + x] << (8 * b);
+                for (int b = 0; b < 4; ++b) {
+                    const int x = gx + b;
+                    if (x >= 0 && x < W) {
+                        a |= (uint32_t)t.cur_smp[ro + x] << (8 * b);
+                        m |= (uint32_t)t.cur_msk[ro + x] << (8 * b);
+                    }
                 }
             }
         }
         sm.cur[0][i] = make_uint2(a, m);
     }
-    build_tie_order(sm.vord, R);
+    for (int i = tid; i < P_HS * P_HS; i += P_NT) {
+        sm.hist[i] = 0;
+        sm.tie.rank[i] = c_tie.rank[i];
+        sm.tie.bin[i] = c_tie.bin[i];
+    }
+    if (tid == 0) sm.np = 0;
     __syncthreads();
     for (int i = tid; i < 3 * P_RROWS * (P_RWORDS - 1); i += P_NT) {
         const int j = 1 + i / (P_RROWS * (P_RWORDS - 1));
@@ -700,18 +763,112 @@ __global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
         sm.cur[j][r * P_CWORDS + w] = make_uint2(__funnelshift_r(a.x, b.x, 8 * j),
                                                  __funnelshift_r(a.y, b.y, 8 * j));
     }
-    const int nv = (2 * R + 1) * (2 * R + 1);
-    for (int i = tid; i < nv; i += P_NT) {
-        const short2 v = sm.vord[i];
-        sm.rank[(v.x + kMaxRadius) * (2 * kMaxRadius + 1) + v.y + kMaxRadius] = (uint16_t)i;
-    }
-    __syncthreads();
-
-    const char2 *mv1 = reinterpret_cast<const char2 *>(t.mv[0]);
-    char2 *mvk = reinterpret_cast<char2 *>(t.mv[k]);
+    // predicted centres and their histogram (lanes with the same centre add up first)
     for (int pi = tid; pi < P_TS * P_TS; pi += P_NT) {
         const int py = pi / P_TS, px = pi - py * P_TS, y = y0 + py, x = x0 + px;
-        if (y >= H || x >= W) continue;
+        uint32_t c = 0xffffu;
+        if (y < H && x < W) c = (uint32_t)pred_centre(mv1[(size_t)y * W + x], k + 1, y, x, H, W, R);
+        const unsigned same = __match_any_sync(0xffffffffu, c);
+        if (c != 0xffffu && lane == __ffs(same) - 1) atomicAdd(&sm.hist[c], __popc(same));
+        sm.cen[pi] = (uint16_t)c;
+        sm.dkey[pi] = 0xffffffffu;
+    }
+    __syncthreads();
+    if (warp == 0) {                               // the most frequent centre
+        uint32_t key = 0;                          // count << 10 | 1023 - bin
+        for (int i = lane; i < P_HS * P_HS; i += 32)
+            key = max(key, ((uint32_t)sm.hist[i] << 10) | (1023u - i));
+        key = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0) sm.cstar = (int)(key >> 10) >= P_DENSE_MIN ? 1023 - (int)(key & 1023u) : -1;
+    }
+    __syncthreads();
+    const int cstar = sm.cstar;
+
+    // dense pass over the window of c*: lanes 0..29 are three bands of 11 rows x 10 words (the
+    // 8 words of the tile and a halo word on each side), one candidate at a time per warp
+    if (cstar >= 0) {
+        const int csy = cstar / P_HS - kMaxRadius, csx = cstar % P_HS - kMaxRadius;
+        const int ch = min(lane / 10, 2), wi = lane < 30 ? lane - 10 * ch : 9, r0 = 11 * ch;
+        const bool out = lane < 30 && wi >= 1 && wi <= 8;
+        const bool inner = y0 - R >= 0 && x0 - R >= 0 && y0 + P_TS + R <= H && x0 + P_TS + R <= W;
+        uint32_t best[11][4];
+#pragma unroll
+        for (int j = 0; j < 11; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) best[j][c] = 0xffffffffu;
+        const int side = 2 * Rp + 1;
+        for (int i = warp; i < side * side; i += P_NW) {
+            const int vy = csy + i / side - Rp, vx = csx + i % side - Rp;
+            if (vy < -R || vy > R || vx < -R || vx > R) continue;      // uniform over the warp
+            const uint32_t rk = c_tie.rank[(vy + kMaxRadius) * P_HS + vx + kMaxRadius];
+            const uint32_t *rr = sm.rf + ((vx + 12) & 3) * P_RCPY + (r0 + vy + kMaxRadius) * P_RWORDS +
+                                 wi + ((vx + 12) >> 2);
+            const uint2 *cc = sm.cur[0] + r0 * P_CWORDS + wi;
+            uint32_t dlo[19], dhi[19], lo = 0, hi = 0;
+#pragma unroll
+            for (int q = 0; q < 19; ++q) {
+                const uint2 c = cc[q * P_CWORDS];
+                const uint32_t d4 = __vabsdiffu4(c.x, rr[q * P_RWORDS]) & c.y;
+                dlo[q] = __byte_perm(d4, 0u, 0x4240);
+                dhi[q] = __byte_perm(d4, 0u, 0x4341);
+                lo += dlo[q];
+                hi += dhi[q];
+                if (q >= 9) {
+                    lo -= dlo[q - 9];
+                    hi -= dhi[q - 9];
+                }
+                if (q >= 8) {
+                    const int j = q - 8;                   // output row r0 + j
+                    const uint32_t Q = lo + hi;
+                    const uint32_t Ql = __shfl_up_sync(0xffffffffu, Q, 1);
+                    const uint32_t lol = __shfl_up_sync(0xffffffffu, lo, 1);
+                    const uint32_t Qr = __shfl_down_sync(0xffffffffu, Q, 1);
+                    const uint32_t lor = __shfl_down_sync(0xffffffffu, lo, 1);
+                    const uint32_t A = __byte_perm(Ql, Q, 0x5432), B = __byte_perm(Q, Qr, 0x5432);
+                    const uint32_t h02 = Ql + A + Q + B + lor;
+                    const uint32_t h13 = h02 + Qr - lol - lor;
+                    const uint32_t h[4] = {h02 & 0xffffu, h13 & 0xffffu, h02 >> 16, h13 >> 16};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int y = y0 + r0 + j, x = x0 + 4 * (wi - 1) + c;
+                        const bool ok = inner || ((unsigned)(y + vy) < (unsigned)H &&
+                                                  (unsigned)(x + vx) < (unsigned)W);
+                        if (ok) best[j][c] = min(best[j][c], (h[c] << 9) | rk);
+                    }
+                }
+            }
+        }
+        if (out) {
+#pragma unroll
+            for (int j = 0; j < 11; ++j)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int py = r0 + j, px = 4 * (wi - 1) + c;
+                    if (py < P_TS && sm.cen[py * P_TS + px] == (uint16_t)cstar)
+                        atomicMin(&sm.dkey[py * P_TS + px], best[j][c]);
+                }
+        }
+        __syncthreads();
+    }
+
+    // densely searched pixels are done; the others are listed and searched one per thread
+    char2 *mvk = reinterpret_cast<char2 *>(t.mv[k]);
+    auto store = [&](int pi, uint32_t key) {
+        const int b = sm.tie.bin[key & 511u];
+        mvk[(size_t)(y0 + pi / P_TS) * W + x0 + pi % P_TS] =
+            make_char2((signed char)(b / P_HS - kMaxRadius), (signed char)(b % P_HS - kMaxRadius));
+    };
+    for (int pi = tid; pi < P_TS * P_TS; pi += P_NT) {
+        const int cb = sm.cen[pi];
+        if (cb == 0xffff) continue;                // outside the frame
+        if (cb == cstar) store(pi, sm.dkey[pi]);
+        else sm.plist[atomicAdd(&sm.np, 1)] = (uint16_t)pi;
+    }
+    __syncthreads();
+    const int np = sm.np;
+    for (int e = tid; e < np; e += P_NT) {
+        const int pi = sm.plist[e], py = pi / P_TS, px = pi - py * P_TS, y = y0 + py, x = x0 + px;
+        const int cb = sm.cen[pi];
         uint32_t cs[9][3], cm[9][3];               // template: masked samples and byte masks
 #pragma unroll
         for (int r = 0; r < 9; ++r)
@@ -722,9 +879,7 @@ __global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
                 cs[r][w] = c.x & keep;
                 cm[r][w] = c.y & keep;
             }
-        const char2 p1 = mv1[(size_t)y * W + x];
-        const int cy = min(max((k + 1) * (int)p1.x, max(-R, -y)), min(R, H - 1 - y));
-        const int cx = min(max((k + 1) * (int)p1.y, max(-R, -x)), min(R, W - 1 - x));
+        const int cy = cb / P_HS - kMaxRadius, cx = cb % P_HS - kMaxRadius;
         uint32_t best = 0xffffffffu;               // SAD << 9 | position in the tie order
         for (int vy = max(cy - Rp, -R); vy <= min(cy + Rp, R); ++vy) {
             if ((unsigned)(y + vy) >= (unsigned)H) continue;
@@ -737,13 +892,10 @@ __global__ void __launch_bounds__(P_NT) me_pred_kernel(FrameTask t)
                 for (int r = 0; r < 9; ++r)
 #pragma unroll
                     for (int w = 0; w < 3; ++w) acc = sad4(cs[r][w], rr[r * P_RWORDS + w] & cm[r][w], acc);
-                const uint32_t key = (acc << 9) |
-                    sm.rank[(vy + kMaxRadius) * (2 * kMaxRadius + 1) + vx + kMaxRadius];
-                best = min(best, key);
+                best = min(best, (acc << 9) | sm.tie.rank[(vy + kMaxRadius) * P_HS + vx + kMaxRadius]);
             }
         }
-        const short2 v = sm.vord[best & 511u];
-        mvk[(size_t)y * W + x] = make_char2((signed char)v.x, (signed char)v.y);
+        store(pi, best);
     }
 }
 
