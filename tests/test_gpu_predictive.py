@@ -127,3 +127,51 @@ def test_predictive_config_errors(engine):
             batched.create_stream(height=64, width=64, me_predict_radius=2)
     finally:
         batched.destroy()
+
+
+def test_predictive_stream_resumes_from_export(engine):
+    """The option travels with the stream state: a stream imported from an export made after
+    frame 3 continues bit-identically to the uninterrupted stream."""
+    seq = synth.config2(seed=420, H=96, W=160, F=6)
+    H, W = seq.shape
+    a = engine.create_stream(height=H, width=W, cc_mode="nnc_frmc", me_predict_radius=2)
+    try:
+        for f in range(4):
+            a.push_frame(seq.samples[f], seq.masks[f])
+            a.get_frame(timeout_ms=120000)
+        b = engine.import_stream(a.export_state())
+        try:
+            for f in (4, 5):
+                a.push_frame(seq.samples[f], seq.masks[f])
+                b.push_frame(seq.samples[f], seq.masks[f])
+                np.testing.assert_array_equal(a.get_frame(timeout_ms=120000),
+                                              b.get_frame(timeout_ms=120000))
+                for k in (1, 2, 3):
+                    np.testing.assert_array_equal(a.debug_get(rfsr.DBG_MV, k),
+                                                  b.debug_get(rfsr.DBG_MV, k))
+        finally:
+            b.destroy()
+    finally:
+        a.destroy()
+
+
+def test_predictive_noalloc_matches_stream(engine):
+    """The allocation-free ME + checks + projection call honours the option like a stream."""
+    seq = synth.config2(seed=430, H=80, W=120, F=5)
+    t = 4
+    H, W = seq.shape
+    smp, msk = seq.samples[t], seq.masks[t]
+    hist = _history(seq, t, 3)
+    got = _step(engine, smp, msk, hist, cc_mode="nnc_frmc", me_predict_radius=2)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    refs = [(dev(r), dev(s), dev(m)) for r, s, m in hist]
+    d_psum = torch.zeros((H, W), dtype=torch.int16, device="cuda")
+    d_pcnt = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
+    d_dec = torch.zeros((3, H, W), dtype=torch.uint8, device="cuda")
+    rfsr.me_cc_project_noalloc(dev(smp), dev(msk), refs, d_psum, d_pcnt, H, W, d_dec=d_dec,
+                               cc_mode="nnc_frmc", me_predict_radius=2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d_psum.cpu().numpy().view(np.uint16), got["psum"])
+    np.testing.assert_array_equal(d_pcnt.cpu().numpy(), got["pcnt"])
+    for k in range(3):
+        np.testing.assert_array_equal(d_dec[k].cpu().numpy(), got["dec"][k])
