@@ -92,6 +92,14 @@ def me_byteops(msk, t=T, r=R):
     return int((n * cy[:, None] * cx[None, :]).sum())
 
 
+def me_cost_evaluations(h, w, r=R):
+    """Template costs forward ME evaluates against one past frame: the (p, v) pairs with v in
+    [-R, R]^2 and p + v inside the frame."""
+    cy = np.array([min(y + r, h - 1) - max(y - r, 0) + 1 for y in range(h)], np.int64)
+    cx = np.array([min(x + r, w - 1) - max(x - r, 0) + 1 for x in range(w)], np.int64)
+    return int(cy.sum() * cx.sum())
+
+
 def frmc_source_work(msk, t=T):
     """S(p) = sum over the FRMC offsets d with p + d inside of n(p + d): the masked byte |a-b| of
     one pixel's FRMC check."""
@@ -840,7 +848,11 @@ def run_ours(args, rank, world, local_rank):
             "unit": "T masked byte |a-b| per s", "frac": round(ach / byte_peak, 4),
             "traffic": (tr_me + tr_cc) if tr_me and tr_cc else None,
             "work_per_frame": {"me_byteops": me_ops, "frmc_byteops": cc_ops,
-                               "frmc_checked_pixels": float(np.mean([c.sum() for c in checked]))},
+                               "frmc_checked_pixels": float(np.mean([c.sum() for c in checked])),
+                               "me_cost_evaluations": KREF * me_cost_evaluations(H, W)},
+            "me_cost_evaluations_per_s": round(KREF * me_cost_evaluations(H, W) / me_s, 1),
+            "dram_gbs": (round((tr_me + tr_cc) / (me_s + cc_s) / 1e9, 2) if tr_me and tr_cc
+                         else None),
             "peak_source": f"__vabsdiffu4 (4 byte |a-b| per instruction) measured by rfsr_alu_peak: "
                            f"{vabs_clk:.1f} per clock per SM x 4 bytes x {SMS} SMs x {mhz:.0f} MHz "
                            f"({src} max clock)",
