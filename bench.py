@@ -123,9 +123,9 @@ def fsr_flops_per_block(iters=ITERS):
 # committed ncu summaries: DRAM bytes per launch of a kernel, valid while its sources are unchanged
 CSRC = os.path.join(ROOT, "paper_2203_09200_gb300", "csrc")
 KERNEL_PROFILES = {"fsr_kernel": ("fsr_kernel_1080p.md", ["fsr.cu", "rfsr_internal.h"]),
-                   "me9_kernel": ("me9_kernel_1080p.md", ["me.cu", "rfsr_internal.h"]),
+                   "me9_kernel": ("me9_kernel_1080p.md", ["me.cu", "me9_tile.cuh", "rfsr_internal.h"]),
                    "cc_project_kernel": ("cc_project_kernel_1080p.md", ["cc.cu", "rfsr_internal.h"]),
-                   "rme9_kernel": ("rme9_kernel_1080p.md", ["me.cu", "rfsr_internal.h"])}
+                   "rme9_kernel": ("rme9_kernel_1080p.md", ["me.cu", "me9_tile.cuh", "rfsr_internal.h"])}
 
 
 def kernel_source_sha(kernel):
@@ -446,6 +446,34 @@ def run_me_predictive(rfsr, torch, radii=(0, 2, 4), steps=8):
     out["workload"] = (f"1920x1080 workload, NNC+FRMC, K=3, T=9, R=8, frames 3..{2 + steps} "
                        f"free-running; changed vectors of t-2 / t-3 on frame {t} with the "
                        f"generator's frames as history; rp_0 = the full search")
+    return out
+
+
+def run_fused_me_cc(rfsr, torch, steps=12):
+    """The 1080p workload with ME and the checks as separate launches (the default) and as one
+    fused persistent launch per frame (engine option fuse_me_cc): device time of ME + checks +
+    projection per frame over frames with 3 past frames, L2 not flushed."""
+    seq = synth.config3(seed=1, F=3 + steps)
+    h, w = seq.shape
+    d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
+    out = {}
+    for name, fuse in (("separate", False), ("fused", True)):
+        with rfsr.Engine(device=torch.cuda.current_device(), profile=True, fuse_me_cc=fuse) as eng:
+            st = eng.create_stream(height=h, width=w, cc_mode="nnc_frmc", template_size=T,
+                                   search_radius=R, num_refs=KREF)
+            ph = []
+            for f in range(3 + steps):
+                st.push_frame_device(d_smp[f], d_msk[f])
+                st.get_frame_device(timeout_ms=120000)
+                if f >= 3:
+                    ph.append(st.phase_ms())
+            a = np.array(ph).mean(axis=0)
+            out[name] = {"me_cc_pr_ms": round(float(a[1] + a[2]), 4),
+                         "launches_per_frame": 3 if fuse else 4}
+    out["fused_over_separate"] = round(out["fused"]["me_cc_pr_ms"] / out["separate"]["me_cc_pr_ms"], 3)
+    out["workload"] = (f"1920x1080 workload, NNC+FRMC, K=3, T=9, R=8, frames 3..{2 + steps}, "
+                       f"device-resident inputs, one unbatched stream (launches: ingest, ME, "
+                       f"checks, FSR; fused: ingest, ME + checks, FSR)")
     return out
 
 
@@ -811,7 +839,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = job_rate(args.steps, world, HW, e_s)
     eng.destroy()
     del d_smp, d_msk, flush
-    batching = serving = check_modes = concealed = me_predictive = None
+    batching = serving = check_modes = concealed = me_predictive = fused = None
     if not args.no_serving:
         batching = run_batching(rfsr, torch)
         batching["small_frames"] = run_batching(
@@ -820,6 +848,7 @@ def run_ours(args, rank, world, local_rank):
         check_modes = run_check_modes(rfsr, torch)
         concealed = run_concealed(rfsr, torch)
         me_predictive = run_me_predictive(rfsr, torch)
+        fused = run_fused_me_cc(rfsr, torch)
 
     if rank != 0:
         return
@@ -909,6 +938,7 @@ def run_ours(args, rank, world, local_rank):
         "check_modes": check_modes,
         "concealed_fsr": concealed,
         "me_predictive": me_predictive,
+        "fused_me_cc": fused,
     }
     print(json.dumps(line), flush=True)
 

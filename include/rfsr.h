@@ -100,6 +100,15 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, void *ctx);
     void *alloc_ctx;       /* passed to both callbacks                                          */
+    int fuse_me_cc;        /* 0 (default): ME and the checks + projection are separate launches.
+                              1: an unbatched stream with T = 9, the full ME search and a check
+                              mode other than RME runs them as one persistent launch whose check
+                              tiles wait (bounded) for the ME bands they read; same results, its
+                              phase timing reports ME and checks together.  Measured slower at
+                              1080p (1.23 against 1.13 ms), so it is off by default.            */
+    int wait_test;         /* tests only, leave 0.  1: every wait of the fused launch runs out
+                              (a count no ME tile reaches, a short limit), so the frame ends with
+                              EDEVICE from rfsr_get_frame and the context stays usable.          */
 } rfsr_engine_config;
 
 /* Tile shapes of the batched launches (a performance choice only; no counterpart in the paper,

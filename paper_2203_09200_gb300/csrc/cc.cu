@@ -34,9 +34,11 @@
 // candidate beats d = 0.  The current frame's copies use a row stride of 19 and a copy stride of
 // 12 mod 16 units, and the offsets are dealt to lanes (per column phase, nearest first) so that
 // the 16 lanes of each half-warp read 16 distinct bank pairs for every template word.
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
+#include "me9_tile.cuh"
 #include "rfsr_internal.h"
 
 namespace rfsr {
@@ -911,6 +913,99 @@ __global__ void __launch_bounds__(NT) cc_batched_kernel(BatchDesc *bd)
     });
 }
 
+// ---------------------------------------------------------------------------------------------
+// Fused ME + checks + projection (T = 9): one persistent launch per frame.  The CTAs (8 warps,
+// the checks' shared memory, which also holds an ME strip's staging) claim items in order from a
+// host-built list: ME tiles of 64-row bands (me9_tile with 8 warp strips) and check tiles.  An ME
+// tile ends with a barrier and a release increment of its band's counter; a check tile first
+// waits (one thread, bounded polls with back-off) until the bands it reads -- rows y0 - 2 ..
+// y0 + 33 for the median halo -- are complete, then every thread acquires the counters itself
+// before reading the motion fields.  Items are claimed one at a time and every item's
+// dependencies come earlier in the list, so the lowest unfinished item can always proceed.  A
+// wait that runs out marks the frame (kStatusWaitTimeout) and later tiles skip their work.
+// ---------------------------------------------------------------------------------------------
+constexpr int F_MEW = 8;                          // warps of an ME item (64-row strips)
+constexpr int F_MEROWS = me9k::s_outh<F_MEW>();
+static_assert(sizeof(me9k::Smem9<F_MEW>) <= sizeof(Smem), "an ME strip's staging fits the checks' smem");
+static_assert(me9k::s_nt<F_MEW>() == NT, "ME items use every thread of the CTA");
+
+// item: bit 31 check tile (else ME tile), bits 0..9 tile column, 10..21 tile row, 22..23 past frame
+constexpr uint32_t F_CC = 0x80000000u;
+__host__ __device__ constexpr uint32_t f_item(bool cc, int tx, int ty, int k)
+{
+    return (cc ? F_CC : 0u) | (uint32_t)tx | ((uint32_t)ty << 10) | ((uint32_t)k << 22);
+}
+// ME bands lo..hi that check-tile row ty reads (rows 32 ty - 2 .. 32 ty + 33)
+__host__ __device__ constexpr int f_band_lo(int ty) { return ty == 0 ? 0 : (TP * ty - 2) / F_MEROWS; }
+__host__ __device__ constexpr int f_band_hi(int ty, int nbands)
+{
+    return (TP * ty + TP + 1) / F_MEROWS < nbands - 1 ? (TP * ty + TP + 1) / F_MEROWS : nbands - 1;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// t.status points at a word of m.ctr that stays 0 during the launch: the tiles test it on entry,
+// and a status that another CTA could change meanwhile might split a CTA at its barriers.
+// The frame's own status word is m.status.
+__global__ void __launch_bounds__(NT, 2) mecc_kernel(FrameTask t, MeccPlan m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    me9k::Smem9<F_MEW> &sm9 = *reinterpret_cast<me9k::Smem9<F_MEW> *>(smem_raw);
+    __shared__ int claim, failed, skip;
+    if (threadIdx.x == 0) skip = *(volatile int *)m.status;   // bad mask: nothing to do, nothing waits
+    __syncthreads();
+    if (skip) return;                             // uniform over the CTA
+    for (;;) {
+        if (threadIdx.x == 0) claim = atomicAdd(&m.ctr[0], 1);
+        __syncthreads();
+        const int i = claim;
+        if (i >= m.nitems) break;                 // uniform over the CTA
+        const uint32_t it = m.items[i];
+        const int tx = (int)(it & 0x3ffu), ty = (int)((it >> 10) & 0xfffu), k = (int)((it >> 22) & 3u);
+        if (!(it & F_CC)) {
+            me9k::me9_tile<F_MEW>(sm9, t, tx, ty, k);
+            __syncthreads();                      // every motion vector of the tile is written
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&m.ctr[2 + ty], 1);
+            }
+        } else {
+            const int lo = f_band_lo(ty), hi = f_band_hi(ty, m.nbands);
+            if (threadIdx.x == 0) {
+                int bad = ld_acquire(&m.ctr[1]);
+                for (int b = lo; b <= hi && !bad; ++b) {
+                    int n = 0;
+                    while (ld_acquire(&m.ctr[2 + b]) < m.need + m.bias) {
+                        if (++n > m.limit) {
+                            bad = 1;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                if (bad) {
+                    atomicExch(&m.ctr[1], 1);
+                    atomicOr(m.status, kStatusWaitTimeout);
+                }
+                failed = bad;
+            }
+            __syncthreads();
+            if (!failed) {
+                for (int b = lo; b <= hi; ++b) (void)ld_acquire(&m.ctr[2 + b]);   // this thread's acquire
+                cc_tile<9>(sm, t, tx, ty);
+                cp_wait_all();                    // no copy into shared memory outlives the tile
+            }
+        }
+        __syncthreads();                          // the claim slot and shared memory are reused
+    }
+}
+
 // RME (Sec. 2.2): reverse motion vector at every past-frame pixel q: argmin over w in [-R, R]^2
 // with q + w inside of C(q + w, -w), exact mean-cost order, tie order on w.
 __device__ __forceinline__ void rme_tile(const FrameTask &t, int tbx, int tby, int k)
@@ -997,6 +1092,58 @@ cudaError_t launch_cc_batched_t(BatchDesc *bd, cudaStream_t st)
 }  // namespace
 
 int tiles_cc(const FrameTask &t) { return ((t.W + TP - 1) / TP) * ((t.H + TP - 1) / TP); }
+
+int mecc_bands(int H) { return (H + F_MEROWS - 1) / F_MEROWS; }
+int mecc_need(int W, int K) { return ((W + me9k::S_OUTW - 1) / me9k::S_OUTW) * K; }
+
+// Claim order: the ME bands top to bottom (every column tile and past frame of a band), and each
+// check-tile row once the band holding its last needed row is `lag` bands back, lag being about
+// one wave of the grid, so that a check tile is normally claimed after its bands are done.
+int mecc_schedule(int H, int W, int K, int grid, uint32_t *items)
+{
+    const int nb = mecc_bands(H), nc = (W + me9k::S_OUTW - 1) / me9k::S_OUTW;
+    const int ny = (H + TP - 1) / TP, nx = (W + TP - 1) / TP;
+    const int per_band = std::max(1, nc * K);
+    const int lag = (grid + per_band - 1) / per_band + 1;
+    int n = 0, row = 0;
+    auto emit_rows = [&](int upto_band) {
+        while (row < ny && f_band_hi(row, nb) <= upto_band) {
+            for (int x = 0; x < nx; ++x, ++n)
+                if (items) items[n] = f_item(true, x, row, 0);
+            ++row;
+        }
+    };
+    for (int b = 0; b < nb; ++b) {
+        for (int k = 0; k < K; ++k)
+            for (int c = 0; c < nc; ++c, ++n)
+                if (items) items[n] = f_item(false, c, b, k);
+        emit_rows(b - lag);
+    }
+    emit_rows(nb);
+    return n;
+}
+
+// the shared-memory attribute comes first: the occupancy query counts on it
+static std::atomic<bool> g_mecc_attr[64];
+int mecc_grid()
+{
+    if (set_smem(mecc_kernel, g_mecc_attr) != cudaSuccess) return 0;
+    static std::atomic<int> grids[64];
+    return persistent_grid_cached(mecc_kernel, NT, sizeof(Smem), grids);
+}
+
+cudaError_t launch_me_cc(const FrameTask &t, const MeccPlan &plan, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = init_cc(dev);
+    if (e != cudaSuccess) return e;
+    const int grid = mecc_grid();
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    mecc_kernel<<<grid, NT, sizeof(Smem), st>>>(t, plan);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t init_cc(int dev)
 {

@@ -225,6 +225,11 @@ struct rfsr_stream {
     uint8_t *pcnt = nullptr;
     float *fsr = nullptr;
     uint16_t *fsr_sel = nullptr;   // selection trace (fsr_trace streams)
+    // fused ME + checks launch: claim orders for 1..K past frames, counters
+    uint32_t *mecc_items = nullptr;
+    int mecc_off[kMaxRefs + 1] = {}, mecc_n[kMaxRefs + 1] = {};
+    int *mecc_ctr = nullptr;
+    int mecc_nb = 0;
     float *tables = nullptr;
     int *d_zero = nullptr;
     std::vector<Slot> slots;
@@ -288,15 +293,31 @@ size_t trace_bytes(const rfsr_stream_config *c)
     return std::max<size_t>(2, 2 * nb * (size_t)c->fsr_iterations);
 }
 
+// frame steps of this stream run ME and the checks as one fused launch (engines that ask for it;
+// unbatched, T = 9, full ME search, no RME)
+bool fused_me_cc(const rfsr_engine_config &e, const rfsr_stream_config *c)
+{
+    return !e.batched && !e.serve && e.fuse_me_cc && c->template_size == 9 &&
+           c->cc_mode != RFSR_CC_RME && c->me_predict_radius == 0 && c->num_refs > 0;
+}
+
+// bytes of the fused launch's claim orders (1..K past frames) and counters
+size_t mecc_bytes(const rfsr_stream_config *c)
+{
+    size_t n = 0;
+    for (int k = 1; k <= c->num_refs; ++k) n += (size_t)mecc_schedule(c->height, c->width, k, 1, nullptr);
+    return 4 * n + 4 * (size_t)(mecc_bands(c->height) + 3);
+}
+
 // device bytes a stream will hold (admission against the engine budget)
-size_t stream_need(const rfsr_stream_config *c, int M)
+size_t stream_need(const rfsr_stream_config *c, int M, bool fused)
 {
     const size_t HW = (size_t)c->height * c->width;
     const int K = c->num_refs;
     const bool rme = c->cc_mode == RFSR_CC_RME;
     return (size_t)(K + 1) * 3 * HW + (size_t)K * (2 * HW * (rme ? 3 : 2) + HW) + 3 * HW + 4 * HW +
            sizeof(FsrTables) + 64 + (size_t)M * (3 * HW + (c->keep_f32 ? 4 * HW : 0) + 4) +
-           trace_bytes(c);
+           trace_bytes(c) + (fused ? mecc_bytes(c) : 0);
 }
 
 // allocate a stream's device and pinned state (engine lock held)
@@ -334,6 +355,23 @@ int admit(rfsr_stream *s)
     AL(s->d_zero, 64);
     cudaError_t er = cudaMemset(s->d_zero, 0, 64);
     if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemset"));
+    if (fused_me_cc(e->cfg, &s->cfg)) {                // claim orders of the fused ME + checks launch
+        const int grid = mecc_grid();
+        if (grid <= 0) return bail(fail(RFSR_EDEVICE, "fused ME + checks launch: no resident grid"));
+        std::vector<uint32_t> items;
+        for (int k = 1; k <= s->K; ++k) {
+            const int n = mecc_schedule(s->H, s->W, k, grid, nullptr);
+            s->mecc_off[k] = (int)items.size();
+            s->mecc_n[k] = n;
+            items.resize(items.size() + n);
+            mecc_schedule(s->H, s->W, k, grid, items.data() + s->mecc_off[k]);
+        }
+        s->mecc_nb = mecc_bands(s->H);
+        AL(s->mecc_items, 4 * items.size());
+        AL(s->mecc_ctr, 4 * (size_t)(s->mecc_nb + 3));
+        er = cudaMemcpy(s->mecc_items, items.data(), 4 * items.size(), cudaMemcpyHostToDevice);
+        if (er != cudaSuccess) return bail(cuda_fail(er, "cudaMemcpy claim order"));
+    }
     {
         FsrTables tb;
         fill_fsr_tables(tb, s->cfg.fsr_rho);
@@ -446,15 +484,33 @@ int enqueue_step(rfsr_stream *s, int slot_idx, const uint8_t *in_smp, const uint
     FrameTask t;
     prepare_frame(s, slot_idx, in_smp, in_msk, t);
     const bool prof = e->cfg.profile != 0;
+    const bool fused = s->mecc_items != nullptr && t.K > 0;
     CK(cudaMemsetAsync(sl.d_status, 0, sizeof(int), e->stream));
+    if (fused) CK(cudaMemsetAsync(s->mecc_ctr, 0, sizeof(int) * (size_t)(s->mecc_nb + 3), e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[0], e->stream));
     CK(launch_ingest(t, e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[1], e->stream));
-    CK(launch_me(t, e->stream));
-    if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
-    // the reverse field of RME belongs to the consistency check (Sec. 2.2), so it is timed there
-    if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
-    CK(launch_cc_project(t, e->stream));
+    if (fused) {                                     // ME, checks and projection in one launch
+        MeccPlan m;
+        m.items = s->mecc_items + s->mecc_off[t.K];
+        m.nitems = s->mecc_n[t.K];
+        m.ctr = s->mecc_ctr;
+        m.nbands = s->mecc_nb;
+        m.need = mecc_need(t.W, t.K);
+        m.limit = e->cfg.wait_test ? 4096 : (1 << 21);   // polls of about 0.5 us: 2 ms / 1 s
+        m.bias = e->cfg.wait_test ? 1 : 0;
+        m.status = t.status;
+        FrameTask tf = t;                            // the tiles see a status word that stays 0
+        tf.status = s->mecc_ctr + s->mecc_nb + 2;
+        CK(launch_me_cc(tf, m, e->stream));
+        if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
+    } else {
+        CK(launch_me(t, e->stream));
+        if (prof) CK(cudaEventRecord(sl.phase[2], e->stream));
+        // the reverse field of RME belongs to the consistency check (Sec. 2.2), so it is timed there
+        if (t.cc_mode == RFSR_CC_RME) CK(launch_rme_field(t, e->stream));
+        CK(launch_cc_project(t, e->stream));
+    }
     if (prof) CK(cudaEventRecord(sl.phase[3], e->stream));
     CK(launch_fsr(t, e->stream));
     if (prof) CK(cudaEventRecord(sl.phase[4], e->stream));
@@ -1026,7 +1082,7 @@ int rfsr_create_stream(rfsr_engine *e, const rfsr_stream_config *cfg, rfsr_strea
     s->H = cfg->height;
     s->W = cfg->width;
     s->K = cfg->num_refs;
-    s->need = stream_need(cfg, e->cfg.max_inflight);
+    s->need = stream_need(cfg, e->cfg.max_inflight, fused_me_cc(e->cfg, cfg));
     std::lock_guard<std::mutex> g(e->mu);
     if (s->need > e->budget) {
         delete s;
@@ -1173,6 +1229,11 @@ static int collect(rfsr_stream *s, int timeout_ms, Slot **out)
     if (st & kStatusPoisoned) {
         s->poisoned = true;
         return fail(RFSR_ESTATE, "get_frame: an earlier frame of the stream had a bad mask");
+    }
+    if (st & kStatusWaitTimeout) {                   // the frame's checks and FSR did not run
+        s->poisoned = true;
+        return fail(RFSR_EDEVICE, "get_frame: a wait of the fused ME + checks launch ran out; "
+                                  "reset the stream with rfsr_set_history");
     }
     *out = &sl;
     return RFSR_OK;

@@ -21,6 +21,7 @@ constexpr int kFsrHalf = kFsrN / 2 + 1;   // stored half spectrum: l = 0..16
 // device status bits (per frame, written by kernels, read back by the host)
 constexpr int kStatusBadMask = 1;     // this frame's mask is not a quarter-sampling mask
 constexpr int kStatusPoisoned = 2;    // an earlier frame of the stream had a bad mask
+constexpr int kStatusWaitTimeout = 4; // a wait of the fused ME + checks launch ran out
 
 // One frame step of one stream: every pointer is device memory owned by the stream, except
 // in_smp / in_msk which point at the staged (or caller's device) input.
@@ -205,6 +206,31 @@ cudaError_t launch_ingest(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_me(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_rme_field(const FrameTask &t, cudaStream_t st);
 cudaError_t launch_cc_project(const FrameTask &t, cudaStream_t st);
+
+// Fused ME + checks + projection of one frame (T = 9, no RME, full ME search): one persistent
+// launch whose CTAs claim, in order, ME tiles (64-row strips x 120 columns x past frame) and check
+// tiles (32 x 32); a check tile first waits for the ME bands it reads.  The order is built on the
+// host so that every tile's dependencies come earlier in it.
+struct MeccPlan {
+    const uint32_t *items;     // the frame's tiles in claim order (device)
+    int nitems;
+    int *ctr;                  // [0] claim head, [1] wait ran out, [2 + b] finished ME tiles of band b,
+                               // [2 + nbands] a status word that stays 0 (the tiles' t.status, so
+                               // that every thread of a CTA reads the same); zeroed before the launch
+    int *status;               // the frame's status word (the ingest's verdict; a wait that runs out
+                               // adds kStatusWaitTimeout)
+    int nbands;                // 64-row ME bands
+    int need;                  // ME tiles per band (column tiles x past frames)
+    int limit;                 // polls of a wait before it gives up
+    int bias;                  // 0; 1 makes every wait run out (tests of the timeout path)
+};
+// items of the claim order for an H x W frame with K past frames on a grid of `grid` CTAs
+// (written to `items` unless null; returns the count)
+int mecc_schedule(int H, int W, int K, int grid, uint32_t *items);
+int mecc_bands(int H);
+int mecc_need(int W, int K);
+int mecc_grid();               // the fused kernel's persistent grid on the current device
+cudaError_t launch_me_cc(const FrameTask &t, const MeccPlan &plan, cudaStream_t st);
 cudaError_t launch_fsr(const FrameTask &t, cudaStream_t st);
 // one-time per-device set-up of the FSR kernel (constant twiddles, shared-memory limit)
 cudaError_t init_fsr(int device);

@@ -42,7 +42,8 @@ class rfsr_engine_config(C.Structure):
     _fields_ = [("device", C.c_int), ("memory_budget", C.c_size_t), ("cuda_stream", C.c_void_p),
                 ("max_inflight", C.c_int), ("batched", C.c_int), ("profile", C.c_int),
                 ("serve", C.c_int), ("autotune", C.c_int), ("dev_alloc", ALLOC_FN),
-                ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("fuse_me_cc", C.c_int),
+                ("wait_test", C.c_int)]
 
 
 class rfsr_stream_config(C.Structure):
@@ -211,7 +212,8 @@ class Engine:
 
     def __init__(self, device: int = 0, memory_budget: int = 0, cuda_stream: Optional[int] = None,
                  max_inflight: int = 4, batched: bool = False, profile: bool = False,
-                 serve: bool = False, autotune: bool = True, allocator: Optional[str] = None):
+                 serve: bool = False, autotune: bool = True, allocator: Optional[str] = None,
+                 fuse_me_cc: bool = False, wait_test: bool = False):
         """allocator="torch": the engine's device memory comes from PyTorch's caching allocator
         (through the dev_alloc / dev_free callbacks of the engine config)."""
         lib = load()
@@ -221,6 +223,7 @@ class Engine:
         cfg.cuda_stream = cuda_stream
         cfg.max_inflight, cfg.batched, cfg.profile = max_inflight, int(batched), int(profile)
         cfg.serve, cfg.autotune = int(serve), int(autotune)
+        cfg.fuse_me_cc, cfg.wait_test = int(fuse_me_cc), int(wait_test)
         self._callbacks = None
         if allocator == "torch":
             self._callbacks = _torch_allocator(device)
