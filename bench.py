@@ -972,7 +972,7 @@ def summarize_launches(path):
 def run_ncu_case(args):
     """A short, untimed kernel sequence for an ncu capture: 'frame_step' runs `frames` frames of
     the 1080p workload on one unbatched stream (device-resident inputs, check mode --cc-mode,
-    predictive-centre ME radius --me-predict-radius);
+    predictive-centre ME radius --me-predict-radius, fused ME + checks with --fuse-me-cc);
     'batched' runs `frames` batched steps of --streams streams of the uneven-size mix (default
     tile shape, no autotuning)."""
     import torch
@@ -984,7 +984,7 @@ def run_ncu_case(args):
     if args.ncu_case == "frame_step":
         seq = synth.config3(seed=3, F=nf)
         d_smp, d_msk = torch.from_numpy(seq.samples).cuda(), torch.from_numpy(seq.masks).cuda()
-        with rfsr.Engine(device=0) as eng:
+        with rfsr.Engine(device=0, fuse_me_cc=args.fuse_me_cc) as eng:
             st = eng.create_stream(height=H, width=W, cc_mode=args.cc_mode, template_size=T,
                                    search_radius=R, num_refs=KREF, fsr_iterations=ITERS,
                                    me_predict_radius=args.me_predict_radius)
@@ -1024,6 +1024,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--streams", type=int, default=64, help="streams of --ncu-case batched")
     ap.add_argument("--cc-mode", default="nnc_frmc", choices=list(MODES),
                     help="consistency-check mode of --ncu-case frame_step")
+    ap.add_argument("--fuse-me-cc", action="store_true",
+                    help="--ncu-case frame_step with the fused ME + checks launch")
     ap.add_argument("--me-predict-radius", type=int, default=0,
                     help="predictive-centre ME radius of --ncu-case frame_step (0: full search)")
     ap.add_argument("--serving-full", action="store_true",
