@@ -405,6 +405,17 @@ int rfsr_alu_peak(int device, int kind, int iters, double *ops_per_sec, double *
 /* Kernel launches made by this process so far (all engines), for launch accounting. */
 long long rfsr_kernel_launches(void);
 
+/* Inspection (no counterpart in the paper): the order in which the CTAs of the fused ME + checks
+ * launch (engine option fuse_me_cc) claim the tiles of a height x width frame with num_refs past
+ * frames on a grid of `grid` CTAs.  Item: bit 31 set for a check tile (32 x 32 pixels at tile
+ * column bits 0..9, tile row bits 10..21), clear for an ME tile (64-row band bits 10..21, 120-column
+ * tile bits 0..9, past frame bits 22..23).  A check tile reads the motion fields of rows
+ * 32 row - 2 .. 32 row + 33; the launch relies on every ME tile of those rows' bands coming earlier
+ * in the order.  Pure host code.  Writes up to `capacity` items (items may be NULL) and returns
+ * the count, or EINVAL for bad sizes. */
+int rfsr_fused_schedule(int height, int width, int num_refs, int grid, uint32_t *items,
+                        int capacity);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *rfsr_last_error(void);
 

@@ -791,6 +791,16 @@ const char *rfsr_last_error(void) { return g_err.c_str(); }
 
 long long rfsr_kernel_launches(void) { return rfsr::launches(); }
 
+int rfsr_fused_schedule(int height, int width, int num_refs, int grid, uint32_t *items, int capacity)
+{
+    if (height < 16 || width < 16 || height > 8192 || width > 8192 || num_refs < 1 ||
+        num_refs > kMaxRefs || grid < 1 || capacity < 0)
+        return fail(RFSR_EINVAL, "fused_schedule: bad size, past frames or grid");
+    const int n = mecc_schedule(height, width, num_refs, grid, nullptr);
+    if (items && capacity >= n) mecc_schedule(height, width, num_refs, grid, items);
+    return n;
+}
+
 int rfsr_engine_create(const rfsr_engine_config *cfg, rfsr_engine **out)
 {
     if (!cfg || !out) return fail(RFSR_EINVAL, "engine_create: NULL argument");

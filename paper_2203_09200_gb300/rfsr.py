@@ -115,6 +115,7 @@ SYMBOLS = {
                                     C.POINTER(_VP), C.POINTER(_VP), _VP, _VP, _VP, _VP, _VP], _I),
     "rfsr_alu_peak": ([_I, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_double)], _I),
     "rfsr_kernel_launches": ([], C.c_longlong),
+    "rfsr_fused_schedule": ([_I, _I, _I, _I, _VP, _I], _I),
     "rfsr_last_error": ([], C.c_char_p),
 }
 
@@ -397,6 +398,14 @@ def fsr_device(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, height: int, w
     cfg = stream_config(height, width, **fsr_kw)
     _check(load().rfsr_fsr_device(C.byref(cfg), _ptr(d_smp), _ptr(d_msk), _ptr(d_psum),
                                   _ptr(d_pcnt), _ptr(d_out_f32), _ptr(d_out_u8), cuda_stream))
+
+
+def fused_schedule(height: int, width: int, num_refs: int, grid: int) -> np.ndarray:
+    """rfsr_fused_schedule: the claim order of the fused ME + checks launch (uint32 items)."""
+    n = _check(load().rfsr_fused_schedule(height, width, num_refs, grid, None, 0))
+    out = np.zeros(max(1, n), np.uint32)
+    _check(load().rfsr_fused_schedule(height, width, num_refs, grid, out.ctypes.data, n))
+    return out[:n]
 
 
 def fsr_device_trace(d_smp, d_msk, d_psum, d_pcnt, d_out_f32, d_out_u8, d_sel, height: int,
